@@ -1,0 +1,57 @@
+"""Write ``workloads.json``: the geometry of the synthetic thin-film workloads.
+
+Calls only the oracle (for kappa from the contact angle and for the
+most-unstable wavelength lambda_m = 2 pi / q_m and growth rate sigma_max of
+the flat film, Sec. Linear Stability Analysis).  Run from the repository
+root:  ``python tests/golden/make_workloads.py``.
+
+Workloads (square, cell-centred, no-flux walls; b = 0.1, n = 3, m = 2,
+theta_c = 20 deg, M = 1/2, C = 1, h0 = 1):
+  small     64^2 on 4 lambda_m, noise eps = 0.01, dt0 = 1e-3, T = 5/sigma_max
+  scale2k   2048^2 on 64 lambda_m, noise eps = 0.01 (run to rupture)
+  scale8k   8192^2 on 64 lambda_m, noise eps = 0.01 (200 timed steps)
+  nucl8k    8192^2 on 256 lambda_m, eps = 1e-4 + 64 Gaussian depressions
+            of depth 0.3 h0 and width lambda_m / 4
+  adjoint1k 1024^2 on 16 lambda_m
+Step control: dt_max = 0.01/sigma_max, dt_min = 1e-9, shrink 1/2, grow 5/4
+after 5 accepted steps, K = 10 Newton iterations, tol 1e-10.
+"""
+import json
+import math
+import os
+import sys
+
+sys.path.insert(0, os.path.abspath(os.path.join(os.path.dirname(__file__), "..", "..")))
+import oracle as O  # noqa: E402
+
+
+def main():
+    b, n, m, th = 0.1, 3, 2, math.radians(20.0)
+    kappa = O.kappa_from_contact_angle(th, b, n, m)
+    M = O.Model(nx=1, ny=1, ds=1.0, kappa=kappa, b=b, n=n, m=m)
+    qm, sm = O.lsa(M, 1.0)
+    lam = 2.0 * math.pi / qm
+    common = dict(b=b, n=n, m=m, theta_c=th, kappa=kappa, cap_C=1.0, h0=1.0,
+                  theta=0.5, lambda_m=lam, sigma_max=sm, tol=1e-10, max_iter=10,
+                  dt_min=1e-9, dt_max=0.01 / sm, dt_shrink=0.5, dt_grow=1.25,
+                  grow_after=5, rupture_h=2.0 * b)
+    W = {
+        "small": dict(common, N=64, P=4, eps=0.01, seed=1234, dt0=1e-3, T=5.0 / sm),
+        "scale2k": dict(common, N=2048, P=64, eps=0.01, seed=1235, dt0=1e-3, T=1e30),
+        "scale8k": dict(common, N=8192, P=64, eps=0.01, seed=1235, dt0=1e-3, T=1e30,
+                        steps=200),
+        "nucl8k": dict(common, N=8192, P=256, eps=1e-4, seed=1236, dt0=1e-3, T=1e30,
+                       holes=64, depth=0.3, width=lam / 4.0),
+        "adjoint1k": dict(common, N=1024, P=16, eps=0.01, seed=1238, dt0=1e-3,
+                          T=1e30, dt_fixed=(2.0 / sm) / 400.0, fixed_iter=3),
+    }
+    for w in W.values():
+        w["ds"] = w["P"] * lam / w["N"]
+    out = os.path.join(os.path.dirname(__file__), "workloads.json")
+    with open(out, "w") as f:
+        json.dump(W, f, indent=1, sort_keys=True)
+    print(out)
+
+
+if __name__ == "__main__":
+    main()
