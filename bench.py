@@ -1,0 +1,383 @@
+"""Benchmark: grid cell-updates per second of the Newton--ADI thin-film step.
+
+Workload (default): the 8192^2 spinodal film on a 64 lambda_m square
+(b = 0.1, n = 3, m = 2, contact angle 20 deg, h0 = 1, noise 0.01 U[-1,1]
+from seed 1235), Crank--Nicolson, tol 1e-10, K = 10, adaptive dt from 1e-3.
+W untimed warm-up steps, then K timed steps.  FP64 mode runs the adaptive
+controller and records its step sizes; FP32-bulk mode replays them, so
+both modes do the same steps.  The headline value is FP32-bulk:
+8192^2 * (accepted steps) / (timed seconds), summed over ranks.
+
+One JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead (each step a 512^2 sample of the same workload).
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU (the single-grid step has no data-parallel split without a halo
+exchange), timed with a barrier and the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = os.path.join(ROOT, "tests", "golden", "workloads.json")
+
+
+def load_workload(name: str) -> dict:
+    with open(WORKLOADS) as f:
+        return json.load(f)[name]
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured")
+    return dict(hbm_gbs=6800.0, source="fallback")
+
+
+# Measured on this machine's GB300 with a dependent-FMA throughput probe:
+# 500 G FP64 FMA/s (1.0 TFLOP/s) -- the FP64 pipe runs at 1/62 of FP32.
+FP64_TFLOPS = 1.0
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=mx,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return rank, world, local, dist
+    torch.cuda.set_device(0)
+    return 0, 1, 0, None
+
+
+def barrier(dist):
+    import torch
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_mode(tf, torch, w, h0, mode, warmup, steps, dist, replay=None, e2e_steps=0, clocks=None):
+    """Warm up, then time `steps` step attempts.  Returns a result dict."""
+    N = w["N"]
+    ctx = tf.Context(tf.params_for_workload(w, mode))
+    h = torch.from_numpy(h0).cuda()
+    if replay is None:
+        info_w, rec_w = tf.tf_advance(ctx, h, 0.0, 1e30, w["dt0"], warmup)
+        dt = info_w["dt"]
+        t0 = info_w["t"]
+    else:
+        info_w, rec_w = tf.tf_advance(ctx, h, 0.0, 1e30, 1.0, warmup,
+                                      dt_replay=replay[:warmup])
+        t0 = info_w["t"]
+        dt = 1.0
+    tf.tf_timing_enable(ctx, True)
+    barrier(dist)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    wall0 = time.perf_counter()
+    if clocks:
+        clocks.__enter__()
+    if replay is None:
+        info, recs = tf.tf_advance(ctx, h, t0, 1e30, dt, steps)
+    else:
+        info, recs = tf.tf_advance(ctx, h, t0, 1e30, 1.0, steps,
+                                   dt_replay=replay[warmup:warmup + steps])
+    stop.record()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.__exit__()
+    wall = time.perf_counter() - wall0
+    barrier(dist)
+    ms = start.elapsed_time(stop)
+    timing = tf.tf_timing_get(ctx)
+    tf.tf_timing_enable(ctx, False)
+    ms = max_over_ranks(dist, ms)
+    out = dict(ms=ms, wall_s=wall, info=info, records=recs, timing=timing,
+               warm_records=rec_w, final_mass=float(h.sum().item()))
+    if e2e_steps > 0:
+        # End to end through the public C-ABI call with host buffers: each
+        # step copies the film from pinned host memory, steps it, and copies
+        # the new film back.
+        hh = torch.from_numpy(h.cpu().numpy()).pin_memory()
+        hd = torch.empty_like(h)
+        hn = torch.empty_like(h)
+        out_h = torch.empty_like(hh).pin_memory()
+        dts = [r["dt"] for r in recs if r["accepted"]][:e2e_steps]
+        barrier(dist)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        acc = 0
+        for d in dts:
+            hd.copy_(hh, non_blocking=True)
+            st = tf.tf_newton_adi_step(ctx, hd, hn, d)
+            out_h.copy_(hn, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            hh, out_h = out_h, hh
+            acc += st["status"] == 0
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(dist)
+        out["e2e_ms"] = max_over_ranks(dist, e0.elapsed_time(e1))
+        out["e2e_steps"] = acc
+        out["e2e_bytes"] = N * N * 8
+    ctx.close()
+    return out
+
+
+def roofline_hbm(res, N, lp_bytes, pk):
+    """Dominant kernel's achieved algorithmic HBM bandwidth."""
+    t = res["timing"]
+    xs = t["x_ms"] / max(1, t["x_launches"])
+    ys = t["y_ms"] / max(1, t["y_launches"])
+    # algorithmic bytes per cell: x pass reads u (8) and b^n (8), writes w;
+    # y pass reads u (8) and w, writes u_{k+1} (8).
+    bx = N * N * (16 + lp_bytes)
+    by = N * N * (16 + lp_bytes)
+    if xs >= ys:
+        name, per, b = "x_pass", xs, bx
+    else:
+        name, per, b = "y_pass", ys, by
+    ach = b / (per * 1e-3) / 1e9
+    return dict(bound="hbm", kernel=name, achieved=round(ach, 1), peak=pk["hbm_gbs"],
+                unit="GB/s", frac=round(ach / pk["hbm_gbs"], 4), traffic=None,
+                ms_per_launch=round(per, 4), peak_source=pk["source"])
+
+
+def cpu_baseline_sample(w, h0):
+    """FP64 oracle on the host cores: the first time step of the workload."""
+    import oracle as O
+    O.build()
+    N = w["N"]
+    M = O.Model(nx=N, ny=N, ds=w["ds"], kappa=w["kappa"], b=w["b"], n=w["n"], m=w["m"],
+                cap_C=w["cap_C"], theta=w["theta"])
+    ctl = O.Control(tol=w["tol"], max_iter=w["max_iter"])
+    t = time.perf_counter()
+    _, info = O.step(M, ctl, h0, w["dt0"])
+    el = time.perf_counter() - t
+    return dict(value=N * N / el, unit="cell-updates/s", cores=O.num_threads(), kind="oracle",
+                sample=f"one time step (dt={w['dt0']}, {info['iterations']} Newton iterations) "
+                       f"of the {N}x{N} film on the host cores, {el:.1f} s")
+
+
+def reference_arm(args, w):
+    """The FP64 CPU oracle as the reference arm: each step is one oracle
+    time step of a 512^2 sample of the workload (same spacing, same noise)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1806_10550_gb300 import synthetic as S
+    O.build()
+    n = 512
+    M = O.Model(nx=n, ny=n, ds=w["ds"], kappa=w["kappa"], b=w["b"], n=w["n"], m=w["m"],
+                cap_C=w["cap_C"], theta=w["theta"])
+    ctl = O.Control(tol=w["tol"], max_iter=w["max_iter"], dt_min=w["dt_min"],
+                    dt_max=w["dt_max"], dt_shrink=w["dt_shrink"], dt_grow=w["dt_grow"],
+                    grow_after=w["grow_after"])
+    h = S.spinodal_film(n, n, w["h0"], w["eps"], w["seed"])
+    res = O.advance(M, ctl, h, 0.0, 1e30, w["dt0"], args.warmup)
+    t0 = time.perf_counter()
+    res2 = O.advance(M, ctl, res.h, res.t, 1e30, res.dt, args.steps)
+    el = time.perf_counter() - t0
+    acc = len(res2.accepted())
+    value = n * n * acc / el
+    line = dict(metric="grid cell-updates/s per Newton-ADI step", value=value,
+                unit="cell-updates/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=el * 1e3 / max(1, args.steps), higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                impl="reference",
+                config=dict(workload=f"{n}x{n} sample of the 8192^2 spinodal film, 64 lambda_m "
+                                     f"spacing (ds={w['ds']:.6f})", global_batch=1),
+                cpu_baseline=dict(value=value, unit="cell-updates/s", cores=O.num_threads(),
+                                  kind="oracle", sample=f"{acc} accepted steps of a {n}^2 sample"),
+                e2e=dict(value=value, unit="cell-updates/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale8k")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--modes", default="fp64,f32b")
+    args = ap.parse_args()
+    w = load_workload(args.workload)
+    if args.impl == "reference":
+        reference_arm(args, w)
+        return
+    import torch
+    import paper_1806_10550_gb300 as tf
+    from paper_1806_10550_gb300 import synthetic as S
+    rank, world, local, dist = dist_setup()
+    tf.library(build_if_missing=True)
+    N = w["N"]
+    h0 = S.spinodal_film(N, N, w["h0"], w["eps"], w["seed"])
+    pk = peaks()
+    modes = args.modes.split(",")
+    res = {}
+    clocks = ClockSampler(local)
+    if "fp64" in modes:
+        res["fp64"] = run_mode(tf, torch, w, h0, tf.TF_FP64, args.warmup, args.steps, dist)
+        replay = [r["dt"] for r in res["fp64"]["warm_records"] + res["fp64"]["records"]
+                  if r["accepted"]]
+    else:
+        replay = None
+    if "f32b" in modes:
+        if replay is not None and len(replay) >= args.warmup + args.steps:
+            res["f32b"] = run_mode(tf, torch, w, h0, tf.TF_FP32_BULK, args.warmup, args.steps,
+                                   dist, replay=replay, e2e_steps=args.e2e_steps, clocks=clocks)
+        else:
+            res["f32b"] = run_mode(tf, torch, w, h0, tf.TF_FP32_BULK, args.warmup, args.steps,
+                                   dist, e2e_steps=args.e2e_steps, clocks=clocks)
+    head = "f32b" if "f32b" in res else "fp64"
+    R = res[head]
+    acc_local = R["info"]["accepted"]
+    acc_all = sum_over_ranks(dist, acc_local)
+    value = N * N * acc_all / (R["ms"] * 1e-3)
+    lp = 4 if head == "f32b" else 8
+    line = dict(
+        metric="grid cell-updates/s per Newton-ADI step at 8192^2",
+        value=value, unit="cell-updates/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=R["ms"] / max(1, R["info"]["attempts"]), higher_is_better=True,
+        scaling="weak", vs_baseline=None,
+        dtype=("f32 solves + f32x2 double-float residual, f64 state" if head == "f32b" else "f64"),
+        data="synthetic",
+        config=dict(workload=f"{N}x{N} spinodal film, 64 lambda_m square, seed {w['seed']}",
+                    mode=("FP32-bulk" if head == "f32b" else "FP64"),
+                    dt_sequence=("replayed from the FP64 run" if head == "f32b" and "fp64" in res
+                                 else "adaptive"),
+                    global_batch=world, l2="working set larger than L2 (several 8192^2 grids)",
+                    parallelism=f"replicas x{world}"),
+        accepted_steps=acc_local, attempts=R["info"]["attempts"],
+        newton_iterations=R["info"]["newton_iterations"],
+        cell_iterations_per_s=N * N * R["info"]["newton_iterations"] * world / (R["ms"] * 1e-3),
+        roofline=roofline_hbm(R, N, lp, pk),
+        gpu_launches=R["timing"]["launches"],
+        kernel_ms=dict(explicit=R["timing"]["explicit_ms"], x_pass=R["timing"]["x_ms"],
+                       y_pass=R["timing"]["y_ms"]),
+    )
+    if "e2e_ms" in R:
+        line["e2e"] = dict(value=N * N * R["e2e_steps"] * world / (R["e2e_ms"] * 1e-3),
+                           unit="cell-updates/s", h2d_bytes_per_step=R["e2e_bytes"],
+                           d2h_bytes_per_step=R["e2e_bytes"], steps=R["e2e_steps"])
+    if "fp64" in res:
+        F = res["fp64"]
+        v64 = N * N * sum_over_ranks(dist, F["info"]["accepted"]) / (F["ms"] * 1e-3)
+        t = F["timing"]
+        per = (t["x_ms"] + t["y_ms"]) / max(1, t["x_launches"])
+        line["fp64"] = dict(value=v64, ms_per_step=F["ms"] / max(1, F["info"]["attempts"]),
+                            accepted_steps=F["info"]["accepted"],
+                            newton_iterations=F["info"]["newton_iterations"],
+                            ms_per_iteration_x_plus_y=per,
+                            roofline=dict(bound="alu", unit="TFLOP/s", peak=FP64_TFLOPS,
+                                          peak_source="measured FP64 FMA throughput probe"))
+        if head == "f32b":
+            line["speedup_f32b_vs_fp64"] = value / v64
+    cs = clocks.summary()
+    line["clocks"] = dict(sm_mhz=cs["sm_mhz"], sm_max_mhz=cs["sm_max_mhz"], reasons=cs["reasons"])
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(w, h0)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

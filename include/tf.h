@@ -1,0 +1,208 @@
+/*
+ * tf.h -- C ABI of the GB300 Newton--ADI thin-film solver (libtfadi.so).
+ *
+ * The library advances the two-dimensional thin-film equation
+ *     h_t + div[ f0(h) grad lap h + f1(h) grad h ] = 0,
+ *     f0 = C h^3,  f1 = h^3 Pi'(h),  Pi(h) = kappa[(b/h)^n - (b/h)^m]
+ * (Lam, Cummings & Kondic, eq. GoverningEquation and eq. GeneralDisPreForm,
+ * read with f1 = h^3 Pi' so that the printed stability values hold) on a
+ * uniform cell-centred grid with no-flux walls (eq. BoundaryConditions),
+ * using the conservative flux discretisation (eq. GovEqnCell2 and Sec. Flux
+ * Discretization), the trapezoidal (Crank--Nicolson) rule (eq. TrapRule),
+ * the pseudo-Newton ADI iteration (eqs. JacobianSystem1-3, x-lines first,
+ * then y-lines) and the adaptive time-step state machine (Fig.
+ * FlowChartTime, eq. NewtonError).
+ *
+ * Conventions
+ *   Grids: nx*ny cells, IEEE double, row-major [ny][nx] (x contiguous),
+ *   DEVICE memory owned by the caller, 8-byte aligned.  The library never
+ *   frees caller memory.  Input and output grids of one call must not
+ *   overlap unless stated.
+ *   Streams: all GPU work of a context runs on the stream given to
+ *   tf_init (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *   Calls that return scalars (tf_residual, tf_newton_adi_step,
+ *   tf_advance) synchronise that stream before returning.
+ *   Errors: every call returns an int.  0 = success; negative = API or CUDA
+ *   error (tf_strerror gives text; the context stays usable for TF_ERR_ARG,
+ *   and should be destroyed after TF_ERR_CUDA).  Positive values of
+ *   tf_newton_adi_step are step outcomes (TF_STEP_*).  No call aborts, traps
+ *   or throws across this interface.
+ */
+#ifndef TFADI_TF_H
+#define TFADI_TF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define TF_OK 0
+#define TF_ERR_ARG (-1)   /* invalid argument (sizes, NULL, parameters)    */
+#define TF_ERR_CUDA (-2)  /* a CUDA runtime call failed                    */
+#define TF_ERR_NOMEM (-3) /* device or host allocation failed              */
+
+/* step outcomes (tf_step_info.status, tf_step_record.status) */
+#define TF_STEP_CONVERGED 0     /* max|v/u_k| < newton_tol (eq. NewtonError) */
+#define TF_STEP_NOT_CONVERGED 1 /* K iterations without convergence          */
+#define TF_STEP_NONPOSITIVE 2   /* an iterate had h <= 0 or a non-finite value */
+#define TF_STEP_ZERO_PIVOT 3    /* zero or non-finite pivot in a line solve   */
+
+/* tf_advance_info.status */
+#define TF_ADV_DONE 0        /* reached t_end                              */
+#define TF_ADV_MAX_ATTEMPTS 1/* attempt limit reached before t_end         */
+#define TF_ADV_DT_MIN 2      /* dt fell below dt_min (or a replayed step failed) */
+#define TF_ADV_RUPTURE 3     /* min h fell below rupture_h                 */
+
+/* models (Sec. Thin Film Models) */
+#define TF_MODEL_POWERLAW 0 /* f0 = C h^3, f1 = h^3 Pi'(h), power-law Pi    */
+#define TF_MODEL_LINEAR 1   /* f0 = c0, f1 = c1 (the linear test model)      */
+
+/* precision modes */
+#define TF_FP64 0      /* every operation in IEEE double                       */
+#define TF_FP32_BULK 1 /* residual, explicit part, update and norms in
+                          double-float (FP32 pairs, >= 47-bit significand) on
+                          the FP32 pipes; Jacobian assembly and pentadiagonal
+                          solves in FP32; state stays IEEE double           */
+
+typedef struct {
+  int nx, ny;            /* cells in x and y, 1..65536 each, nx*ny < 2^31       */
+  double ds;             /* grid spacing (both directions), > 0               */
+  int model;             /* TF_MODEL_*                                         */
+  double cap_C;          /* f0 = C h^3                                         */
+  double b;              /* precursor scale of Pi                              */
+  int n, m;              /* exponents of Pi, n > m >= 1                        */
+  double kappa;          /* strength of Pi; if <= 0 it is derived from
+                            contact_angle: kappa = (1 - cos th)/(b M),
+                            M = (n-m)/((m-1)(n-1))  (requires m >= 2)         */
+  double contact_angle;  /* radians                                           */
+  double c0, c1;         /* TF_MODEL_LINEAR coefficients                       */
+  double theta;          /* time weighting, 0.5 = Crank--Nicolson, in [0,1]   */
+  double newton_tol;     /* tolerance on max|v/u_k|                            */
+  int newton_max_iter;   /* K: iterations before a step is rejected (>= 1)    */
+  int newton_fixed_iter; /* > 0: run exactly this many iterations, no test    */
+  double dt_min, dt_max; /* step-size bounds of the controller                 */
+  double dt_shrink;      /* factor on rejection, in (0,1)                     */
+  double dt_grow;        /* factor after grow_after accepted steps, >= 1      */
+  int grow_after;        /* consecutive accepted steps before dt grows        */
+  double rupture_h;      /* tf_advance stops when min h < rupture_h (0 = off) */
+  int precision;         /* TF_FP64 or TF_FP32_BULK                            */
+} tf_params;
+
+typedef struct tf_ctx tf_ctx;
+
+typedef struct {
+  double gnorm; /* max |G| over the grid                                     */
+  double mass;  /* sum of the grid values (of h_k): each value rounded to a
+                   multiple of 2^-36, summed exactly (heights below 16)   */
+  double hmin;  /* min of h_k                                                 */
+} tf_norms;
+
+typedef struct {
+  int status;     /* TF_STEP_*                                               */
+  int iterations; /* Newton iterations run                                   */
+  double err;     /* max|v/u_k| of the last iteration                        */
+  double gnorm;   /* max|G(u_k)| at the start of the last iteration          */
+  double mass;    /* sum of h_new                                            */
+  double hmin;    /* min of h_new                                            */
+} tf_step_info;
+
+typedef struct {
+  double t, dt;   /* time before the attempt and the step size tried        */
+  int accepted, iterations, status;
+  double err, gnorm, mass, hmin;
+} tf_step_record;
+
+typedef struct {
+  int status;            /* TF_ADV_*                                         */
+  int attempts;          /* step attempts made                               */
+  int accepted;          /* accepted steps                                   */
+  int newton_iterations; /* Newton iterations over all attempts              */
+  double t;              /* time reached                                     */
+  double dt;             /* step size the controller would try next          */
+} tf_advance_info;
+
+/* Fill *p with the defaults: power-law model, C = 1, b = 0.1, n = 3, m = 2,
+ * contact angle 20 degrees (kappa derived), theta = 0.5, tol 1e-10, K = 10,
+ * dt_min 1e-9, dt_max 1e30, shrink 0.5, grow 1.25 after 5, no rupture stop,
+ * TF_FP64.  nx, ny, ds are set to 0 and must be filled in.               */
+void tf_params_default(tf_params* p);
+
+/* Create a context: validates *p, allocates the device workspace (about
+ * 10 FP64 grids in TF_FP64, 6 in TF_FP32_BULK) and pinned host scalars.
+ * stream: cudaStream_t (as void*) on which every kernel of this context is
+ * launched.  *out receives the context or NULL on error.                 */
+int tf_init(const tf_params* p, void* stream, tf_ctx** out);
+
+/* Release everything tf_init allocated.  NULL is ignored.                */
+void tf_destroy(tf_ctx* ctx);
+
+/* Text for a return code or step outcome (static storage).              */
+const char* tf_strerror(int code);
+
+/* Kappa actually used by the context (given or derived).                */
+double tf_kappa(const tf_ctx* ctx);
+
+/* Newton residual (Sec. Newton Iterative Scheme):
+ *   b^n = h_old - (1-theta) dt D(h_old),
+ *   G   = h_k + theta dt D(h_k) - b^n,
+ * with D the discrete flux divergence of eq. GovEqnCell2.
+ * h_k, h_old: device grids (may alias).  G: device grid or NULL.
+ * out: host struct or NULL (gnorm = max|G|, mass and hmin of h_k).       */
+int tf_residual(tf_ctx* ctx, const double* h_k, const double* h_old, double dt,
+                double* G, tf_norms* out);
+
+/* One pseudo-Newton ADI iteration from h_k (eqs. JacobianSystem1-3):
+ *   (I + theta dt J_x) w = -G(h_k)   on every row (x-line),
+ *   (I + theta dt J_y) v = w         on every column (y-line),
+ *   h_next = h_k + v.
+ * b^n is formed from h_old inside the call.  w, v: device grids or NULL
+ * (written as double).  h_next must not overlap h_k or h_old.
+ * info: status (TF_STEP_CONVERGED if err < newton_tol, else
+ * TF_STEP_NOT_CONVERGED, or a failure code), err, gnorm, mass, hmin.     */
+int tf_newton_iteration(tf_ctx* ctx, const double* h_k, const double* h_old,
+                        double dt, double* w, double* v, double* h_next,
+                        tf_step_info* info);
+
+/* One time step of size dt from h_old (device) into h_new (device, must not
+ * overlap h_old): iterate from u_0 = h_old until max|v/u_k| < newton_tol,
+ * up to newton_max_iter iterations (or exactly newton_fixed_iter).
+ * Returns the step outcome TF_STEP_* (>= 0) or a negative error.  On a
+ * failed step h_new holds the last iterate; h_old is never modified.     */
+int tf_newton_adi_step(tf_ctx* ctx, const double* h_old, double* h_new, double dt,
+                       tf_step_info* info);
+
+/* Adaptive time stepping (Fig. FlowChartTime) of the device grid h in place
+ * from t0 toward t_end, starting with step size dt0; at most max_attempts
+ * step attempts.  Accepted: t += dt; after grow_after consecutive accepted
+ * steps dt = min(dt * dt_grow, dt_max).  Rejected: dt = (tried dt) *
+ * dt_shrink, failing below dt_min.  The last step is clipped to land on
+ * t_end.  Replay (host arrays, nullable): attempt a uses dt_replay[a] and,
+ * if iter_replay != NULL, exactly iter_replay[a] Newton iterations, with
+ * no controller; a failed replayed step ends the call with TF_ADV_DT_MIN.
+ * records: host array of max_attempts entries or NULL.  info: host, required.
+ * Returns TF_OK or a negative error.                                     */
+int tf_advance(tf_ctx* ctx, double* h, double t0, double t_end, double dt0,
+               int max_attempts, const double* dt_replay, const int* iter_replay,
+               tf_step_record* records, tf_advance_info* info);
+
+/* Kernel timing of a context, for measurement.  While enabled, the library
+ * records CUDA events on its stream around every kernel it launches and
+ * accumulates their durations per kernel kind; the sums are taken at the
+ * synchronisation point that ends each Newton iteration.  Counters reset
+ * when timing is enabled. */
+typedef struct {
+  int enabled;
+  int launches;          /* kernels launched while enabled (all kinds)       */
+  int explicit_launches; /* b^n stencil launches                             */
+  int x_launches;        /* x-line pass launches                             */
+  int y_launches;        /* y-line pass launches                             */
+  double explicit_ms, x_ms, y_ms; /* summed event durations, milliseconds    */
+} tf_timing;
+
+int tf_timing_enable(tf_ctx* ctx, int on);
+int tf_timing_get(const tf_ctx* ctx, tf_timing* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

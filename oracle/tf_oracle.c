@@ -150,7 +150,7 @@ void or_operator_D(const or_model* M, const double* u, double* D) {
           face_flux(M, u[IDX(M, i, j)], u[IDX(M, i + 1, j)],
                     lap[IDX(M, i, j)], lap[IDX(M, i + 1, j)]);
 #pragma omp parallel for schedule(static)
-  for (int j = 0; j + 1 < ny; ++j)
+  for (int j = 0; j < ny - 1; ++j)
     for (int i = 0; i < nx; ++i)
       Fy[(size_t)j * nx + i] =
           face_flux(M, u[IDX(M, i, j)], u[IDX(M, i, j + 1)],

@@ -1,0 +1,409 @@
+// tf_api.cu -- C ABI of the Newton--ADI thin-film solver (see include/tf.h).
+//
+// Host side of the method: workspace management, the Newton iteration loop
+// of one time step (Sec. Newton Iterative Scheme, eq. NewtonError) and the
+// adaptive time-step state machine (Fig. FlowChartTime).  All grid work is
+// done by the kernels of tf_kernels.cuh; the host reads back one small
+// struct of reduced scalars per Newton iteration.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "tf_internal.h"
+
+using tf::Scalars;
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? TF_ERR_NOMEM : TF_ERR_CUDA; }
+
+#define TF_CK(call)                     \
+  do {                                  \
+    cudaError_t e_ = (call);            \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+double mass_of(double fixed) { return fixed * 0x1p-36; }
+
+// Reduce the partials of the last passes into c.hsc (blocking).
+int finalize(tf_ctx& c, int n_px, int n_py) {
+  tf::k_finalize<<<1, 256, 0, c.stream>>>(c.px, n_px, c.py, n_py, c.dsc);
+  TF_CK(cudaGetLastError());
+  TF_CK(cudaMemcpyAsync(c.hsc, c.dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
+  TF_CK(cudaStreamSynchronize(c.stream));
+  return TF_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.0f;
+  return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? ms : 0.0f;
+}
+
+// One pseudo-Newton ADI iteration from u_k (b^n already formed).
+int iterate(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_out, double* v_out,
+            Scalars* s) {
+  const bool tm = c.timing.enabled;
+  if (tm) TF_CK(cudaEventRecord(c.ev[0], c.stream));
+  TF_CK(c.ops->pass_x(c, u_k, dt));
+  if (tm) TF_CK(cudaEventRecord(c.ev[1], c.stream));
+  if (w_out) TF_CK(c.ops->w_to_f64(c, w_out));
+  if (tm) TF_CK(cudaEventRecord(c.ev[2], c.stream));
+  TF_CK(c.ops->pass_y(c, u_k, dt, u_next, v_out));
+  if (tm) TF_CK(cudaEventRecord(c.ev[3], c.stream));
+  int r = finalize(c, c.grid_x, c.grid_y);
+  if (r) return r;
+  if (tm) {
+    c.timing.x_ms += elapsed(c.ev[0], c.ev[1]);
+    c.timing.y_ms += elapsed(c.ev[2], c.ev[3]);
+    c.timing.x_launches++;
+    c.timing.y_launches++;
+    c.timing.launches += 3 + (w_out && c.ops->lp_bytes != sizeof(double) ? 1 : 0);
+  }
+  *s = *c.hsc;
+  return TF_OK;
+}
+
+int explicit_timed(tf_ctx& c, const double* h_old, double dt) {
+  const bool tm = c.timing.enabled;
+  if (tm) TF_CK(cudaEventRecord(c.ev[0], c.stream));
+  TF_CK(c.ops->explicit_part(c, h_old, dt));
+  if (tm) {
+    TF_CK(cudaEventRecord(c.ev[1], c.stream));
+    TF_CK(cudaEventSynchronize(c.ev[1]));
+    c.timing.explicit_ms += elapsed(c.ev[0], c.ev[1]);
+    c.timing.explicit_launches++;
+    c.timing.launches++;
+  }
+  return TF_OK;
+}
+
+// Outcome of an iteration, in the oracle's order: pivot, positivity, test.
+int classify(const tf_ctx& c, const Scalars& s, int it, int fixed_iter) {
+  if (s.pivot) return TF_STEP_ZERO_PIVOT;
+  if (s.nonfinite) return TF_STEP_NONPOSITIVE;
+  if (fixed_iter > 0) return it >= fixed_iter ? TF_STEP_CONVERGED : TF_STEP_NOT_CONVERGED;
+  if (s.err < c.p.newton_tol) return TF_STEP_CONVERGED;
+  return TF_STEP_NOT_CONVERGED;
+}
+
+void fill_info(tf_step_info* info, int status, int it, const Scalars& s) {
+  if (!info) return;
+  info->status = status;
+  info->iterations = it;
+  info->err = s.err;
+  info->gnorm = s.gnorm;
+  info->mass = mass_of(s.mass);
+  info->hmin = s.hmin;
+}
+
+// A time step with an explicit fixed-iteration override (0 = none).
+// The iterate ping-pongs between h_new and c.ubuf; the result is in h_new.
+int step(tf_ctx& c, const double* h_old, double* h_new, double dt, int fixed_iter, tf_step_info* info) {
+  int re = explicit_timed(c, h_old, dt);
+  if (re) return re;
+  const int kmax = fixed_iter > 0 ? fixed_iter : c.p.newton_max_iter;
+  const double* uk = h_old;
+  double* bufs[2] = {h_new, c.ubuf};
+  Scalars s;
+  memset(&s, 0, sizeof(s));
+  int status = TF_STEP_NOT_CONVERGED, it = 0;
+  for (int k = 0; k < kmax; ++k) {
+    double* un = bufs[k & 1];
+    int r = iterate(c, uk, dt, un, nullptr, nullptr, &s);
+    if (r) return r;
+    it = k + 1;
+    uk = un;
+    status = classify(c, s, it, fixed_iter);
+    if (status != TF_STEP_NOT_CONVERGED) break;
+  }
+  if (uk != h_new)
+    TF_CK(cudaMemcpyAsync(h_new, uk, c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  TF_CK(cudaStreamSynchronize(c.stream));
+  fill_info(info, status, it, s);
+  return status;
+}
+
+template <class T> int dalloc(T** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *p = (T*)q;
+  return TF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tf_params_default(tf_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->model = TF_MODEL_POWERLAW;
+  p->cap_C = 1.0;
+  p->b = 0.1;
+  p->n = 3;
+  p->m = 2;
+  p->kappa = 0.0;
+  p->contact_angle = 20.0 * M_PI / 180.0;
+  p->c0 = 1.0;
+  p->c1 = 1.0;
+  p->theta = 0.5;
+  p->newton_tol = 1e-10;
+  p->newton_max_iter = 10;
+  p->newton_fixed_iter = 0;
+  p->dt_min = 1e-9;
+  p->dt_max = 1e30;
+  p->dt_shrink = 0.5;
+  p->dt_grow = 1.25;
+  p->grow_after = 5;
+  p->rupture_h = 0.0;
+  p->precision = TF_FP64;
+}
+
+const char* tf_strerror(int code) {
+  switch (code) {
+    case TF_OK: return "ok (step converged)";
+    case TF_ERR_ARG: return "invalid argument";
+    case TF_ERR_CUDA: return "CUDA runtime error";
+    case TF_ERR_NOMEM: return "out of memory";
+    case TF_STEP_NOT_CONVERGED: return "Newton iteration did not converge";
+    case TF_STEP_NONPOSITIVE: return "non-positive or non-finite film height";
+    case TF_STEP_ZERO_PIVOT: return "zero or non-finite pivot in a line solve";
+    default: return "unknown code";
+  }
+}
+
+void tf_destroy(tf_ctx* c) {
+  if (!c) return;
+  cudaFree(c->bn);
+  cudaFree(c->w);
+  cudaFree(c->fac_x);
+  cudaFree(c->fac_y);
+  cudaFree(c->ubuf);
+  cudaFree(c->ubuf2);
+  cudaFree(c->px);
+  cudaFree(c->py);
+  cudaFree(c->dsc);
+  if (c->hsc) cudaFreeHost(c->hsc);
+  for (int k = 0; k < 4; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  free(c);
+}
+
+double tf_kappa(const tf_ctx* c) { return c ? c->kappa : 0.0; }
+
+int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
+  if (!out) return TF_ERR_ARG;
+  *out = nullptr;
+  if (!p) return TF_ERR_ARG;
+  if (p->nx < 1 || p->ny < 1 || !(p->ds > 0.0) || !isfinite(p->ds)) return TF_ERR_ARG;
+  if ((double)p->nx * (double)p->ny >= 2147483647.0) return TF_ERR_ARG;
+  if (p->nx > 65536 || p->ny > 65536) return TF_ERR_ARG;
+  if (p->model != TF_MODEL_POWERLAW && p->model != TF_MODEL_LINEAR) return TF_ERR_ARG;
+  if (!(p->theta >= 0.0 && p->theta <= 1.0)) return TF_ERR_ARG;
+  if (p->newton_max_iter < 1 || p->newton_fixed_iter < 0) return TF_ERR_ARG;
+  if (!(p->dt_shrink > 0.0 && p->dt_shrink < 1.0) || !(p->dt_grow >= 1.0) || p->grow_after < 1)
+    return TF_ERR_ARG;
+  if (p->precision != TF_FP64 && p->precision != TF_FP32_BULK) return TF_ERR_ARG;
+  double kappa = p->kappa;
+  if (p->model == TF_MODEL_POWERLAW) {
+    if (!(p->b > 0.0) || p->m < 1 || p->n <= p->m || p->n > 12 || !(p->cap_C > 0.0)) return TF_ERR_ARG;
+    if (!(kappa > 0.0)) {
+      if (p->m < 2) return TF_ERR_ARG;
+      double Mf = (double)(p->n - p->m) / ((double)(p->m - 1) * (double)(p->n - 1));
+      kappa = (1.0 - cos(p->contact_angle)) / (p->b * Mf);
+      if (!(kappa > 0.0)) return TF_ERR_ARG;
+    }
+  }
+  tf_ctx* c = (tf_ctx*)calloc(1, sizeof(tf_ctx));
+  if (!c) return TF_ERR_NOMEM;
+  c->p = *p;
+  c->kappa = kappa;
+  c->stream = (cudaStream_t)stream;
+  c->ops = p->precision == TF_FP64 ? &tf::ops_fp64 : &tf::ops_f32b;
+  c->N = (size_t)p->nx * (size_t)p->ny;
+  tf::ModelK& mk = c->mk;
+  mk.nx = p->nx;
+  mk.ny = p->ny;
+  mk.model = p->model;
+  mk.n = p->n;
+  mk.m = p->m;
+  mk.inv_ds = 1.0 / p->ds;
+  mk.inv_ds2 = mk.inv_ds * mk.inv_ds;
+  mk.inv_ds3 = mk.inv_ds2 * mk.inv_ds;
+  mk.C = p->cap_C;
+  mk.A1 = kappa * (double)p->m * pow(p->b, p->m);
+  mk.B1 = kappa * (double)p->n * pow(p->b, p->n);
+  mk.c0 = p->c0;
+  mk.c1 = p->c1;
+  c->grid_x = (p->ny + 31) / 32;
+  c->grid_y = (p->nx + 31) / 32;
+  c->nchunk_x = (p->nx + tf::kTileX - 1) / tf::kTileX;
+  c->grid_st_x = (p->nx + 15) / 16;
+  c->grid_st_y = (p->ny + 15) / 16;
+  c->grid_stats = 304;
+  c->n_px = c->grid_x > c->grid_st_x * c->grid_st_y ? c->grid_x : c->grid_st_x * c->grid_st_y;
+  c->n_py = c->grid_y > c->grid_stats ? c->grid_y : c->grid_stats;
+  const size_t hp = c->ops->hp_bytes, lp = c->ops->lp_bytes;
+  const size_t facx = (size_t)3 * c->grid_x * c->nchunk_x * 32 * tf::kTileX;
+  int r = TF_OK;
+  cudaError_t e = c->ops->prepare();
+  if (e != cudaSuccess) r = cuda_fail(e);
+  if (!r) r = dalloc(&c->bn, c->N * hp);
+  if (!r) r = dalloc(&c->w, c->N * lp);
+  if (!r) r = dalloc(&c->fac_x, facx * lp);
+  if (!r) r = dalloc(&c->fac_y, 3 * c->N * lp);
+  if (!r) r = dalloc(&c->ubuf, c->N * sizeof(double));
+  if (!r) r = dalloc(&c->ubuf2, c->N * sizeof(double));
+  if (!r) r = dalloc(&c->px, (size_t)c->n_px * sizeof(tf::PartX));
+  if (!r) r = dalloc(&c->py, (size_t)c->n_py * sizeof(tf::PartY));
+  if (!r) r = dalloc(&c->dsc, sizeof(Scalars));
+  if (!r) {
+    e = cudaMallocHost((void**)&c->hsc, sizeof(Scalars));
+    if (e != cudaSuccess) r = cuda_fail(e);
+  }
+  for (int k = 0; k < 4 && !r; ++k) {
+    e = cudaEventCreate(&c->ev[k]);
+    if (e != cudaSuccess) r = cuda_fail(e);
+  }
+  if (r) {
+    tf_destroy(c);
+    return r;
+  }
+  *out = c;
+  return TF_OK;
+}
+
+int tf_residual(tf_ctx* c, const double* h_k, const double* h_old, double dt, double* G,
+                tf_norms* out) {
+  if (!c || !h_k || !h_old || !isfinite(dt)) return TF_ERR_ARG;
+  TF_CK(c->ops->explicit_part(*c, h_old, dt));
+  TF_CK(c->ops->residual_g(*c, h_k, dt, G ? G : c->ubuf));
+  tf::k_grid_stats<<<c->grid_stats, 256, 0, c->stream>>>(h_k, c->N, c->py);
+  TF_CK(cudaGetLastError());
+  int r = finalize(*c, c->grid_st_x * c->grid_st_y, c->grid_stats);
+  if (r) return r;
+  if (out) {
+    out->gnorm = c->hsc->gnorm;
+    out->mass = mass_of(c->hsc->mass);
+    out->hmin = c->hsc->hmin;
+  }
+  return TF_OK;
+}
+
+int tf_newton_iteration(tf_ctx* c, const double* h_k, const double* h_old, double dt, double* w,
+                        double* v, double* h_next, tf_step_info* info) {
+  if (!c || !h_k || !h_old || !h_next || !isfinite(dt)) return TF_ERR_ARG;
+  if (h_next == h_k || h_next == h_old) return TF_ERR_ARG;
+  TF_CK(c->ops->explicit_part(*c, h_old, dt));
+  Scalars s;
+  int r = iterate(*c, h_k, dt, h_next, w, v, &s);
+  if (r) return r;
+  int status = classify(*c, s, 1, 0);
+  fill_info(info, status, 1, s);
+  return TF_OK;
+}
+
+int tf_newton_adi_step(tf_ctx* c, const double* h_old, double* h_new, double dt, tf_step_info* info) {
+  if (!c || !h_old || !h_new || h_old == h_new || !(dt > 0.0) || !isfinite(dt)) return TF_ERR_ARG;
+  return step(*c, h_old, h_new, dt, c->p.newton_fixed_iter, info);
+}
+
+int tf_advance(tf_ctx* c, double* h, double t0, double t_end, double dt0, int max_attempts,
+               const double* dt_replay, const int* iter_replay, tf_step_record* records,
+               tf_advance_info* info) {
+  if (!c || !h || !info || max_attempts < 0 || !(dt0 > 0.0) || !isfinite(t0)) return TF_ERR_ARG;
+  memset(info, 0, sizeof(*info));
+  const tf_params& P = c->p;
+  double* cur = h;
+  double* nxt = c->ubuf2;
+  double t = t0, dt = dt0;
+  int streak = 0, a = 0, status = TF_ADV_MAX_ATTEMPTS;
+  while (a < max_attempts) {
+    if (t >= t_end) {
+      status = TF_ADV_DONE;
+      break;
+    }
+    double step_dt;
+    int last = 0, fixed = P.newton_fixed_iter;
+    if (dt_replay) {
+      step_dt = dt_replay[a];
+      if (iter_replay) fixed = iter_replay[a];
+      if (!(step_dt > 0.0)) return TF_ERR_ARG;
+    } else if (t_end - t <= dt) {
+      step_dt = t_end - t;
+      last = 1;
+    } else {
+      step_dt = dt;
+    }
+    tf_step_info si;
+    int s = step(*c, cur, nxt, step_dt, fixed, &si);
+    if (s < 0) return s;
+    if (records) {
+      tf_step_record& rec = records[a];
+      rec.t = t;
+      rec.dt = step_dt;
+      rec.accepted = s == TF_STEP_CONVERGED;
+      rec.iterations = si.iterations;
+      rec.status = s;
+      rec.err = si.err;
+      rec.gnorm = si.gnorm;
+      rec.mass = si.mass;
+      rec.hmin = si.hmin;
+    }
+    ++a;
+    info->newton_iterations += si.iterations;
+    if (s == TF_STEP_CONVERGED) {
+      double* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+      t = last ? t_end : t + step_dt;
+      info->accepted++;
+      if (!dt_replay && ++streak >= P.grow_after) {
+        dt = fmin(dt * P.dt_grow, P.dt_max);
+        streak = 0;
+      }
+      if (P.rupture_h > 0.0 && si.hmin < P.rupture_h) {
+        status = TF_ADV_RUPTURE;
+        break;
+      }
+    } else {
+      if (dt_replay) {
+        status = TF_ADV_DT_MIN;
+        break;
+      }
+      streak = 0;
+      dt = step_dt * P.dt_shrink;
+      if (dt < P.dt_min) {
+        status = TF_ADV_DT_MIN;
+        break;
+      }
+    }
+  }
+  if (status == TF_ADV_MAX_ATTEMPTS && t >= t_end) status = TF_ADV_DONE;
+  if (cur != h) {
+    TF_CK(cudaMemcpyAsync(h, cur, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    TF_CK(cudaStreamSynchronize(c->stream));
+  }
+  info->status = status;
+  info->attempts = a;
+  info->t = t;
+  info->dt = dt;
+  return TF_OK;
+}
+
+int tf_timing_enable(tf_ctx* c, int on) {
+  if (!c) return TF_ERR_ARG;
+  memset(&c->timing, 0, sizeof(c->timing));
+  c->timing.enabled = on ? 1 : 0;
+  return TF_OK;
+}
+
+int tf_timing_get(const tf_ctx* c, tf_timing* out) {
+  if (!c || !out) return TF_ERR_ARG;
+  *out = c->timing;
+  return TF_OK;
+}
+
+}  // extern "C"

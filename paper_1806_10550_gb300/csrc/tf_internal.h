@@ -1,0 +1,62 @@
+// tf_internal.h -- context and per-mode launch table shared by the C-ABI
+// layer (tf_api.cu) and the two precision instantiations (tf_mode_*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/tf.h"
+#include "tf_kernels.cuh"
+
+namespace tf {
+
+constexpr int kTileX = 16;  // columns per chunk of the x pass
+constexpr int kRowsY = 32;  // rows per chunk of the y pass
+
+}  // namespace tf
+
+struct tf_ctx;
+
+namespace tf {
+
+struct Ops {
+  size_t hp_bytes, lp_bytes;
+  cudaError_t (*prepare)();
+  cudaError_t (*explicit_part)(tf_ctx& c, const double* u_old, double dt);
+  cudaError_t (*residual_g)(tf_ctx& c, const double* u_k, double dt, double* G);
+  cudaError_t (*pass_x)(tf_ctx& c, const double* u_k, double dt);
+  cudaError_t (*pass_y)(tf_ctx& c, const double* u_k, double dt, double* u_next, double* v_out);
+  cudaError_t (*w_to_f64)(tf_ctx& c, double* out);
+};
+
+extern const Ops ops_fp64;
+extern const Ops ops_f32b;
+
+}  // namespace tf
+
+struct tf_ctx {
+  tf_params p;
+  tf::ModelK mk;
+  double kappa;
+  const tf::Ops* ops;
+  cudaStream_t stream;
+  size_t N;
+  int grid_x;      // blocks of the x pass (32 rows each)
+  int grid_y;      // blocks of the y pass (32 columns each)
+  int nchunk_x;    // column chunks of the x pass
+  int grid_st_x, grid_st_y;  // 2-D stencil grid
+  int grid_stats;  // blocks of k_grid_stats
+  void* bn;        // explicit part b^n, HP storage
+  void* w;         // x-pass output, LP
+  void* fac_x;     // x-pass LU factors, LP
+  void* fac_y;     // y-pass LU factors, LP
+  double* ubuf;    // iterate buffer
+  double* ubuf2;   // state buffer of tf_advance
+  tf::PartX* px;
+  tf::PartY* py;
+  int n_px, n_py;
+  tf::Scalars* dsc;
+  tf::Scalars* hsc;  // pinned
+  tf_timing timing;
+  cudaEvent_t ev[4];
+};

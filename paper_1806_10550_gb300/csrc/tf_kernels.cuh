@@ -1,0 +1,738 @@
+// tf_kernels.cuh -- CUDA kernels of the Newton--ADI thin-film time step.
+//
+// One templated kernel set serves both precision modes (Mode = ModeFP64 or
+// ModeF32B, see tf_numeric.cuh for the double-float arithmetic):
+//   HP  precision of the explicit part b^n, the residual G and the update;
+//   LP  precision of the Jacobian assembly and the pentadiagonal solves.
+//
+// Discretisation (Lam, Cummings & Kondic):
+//   Lap_c  = sum over existing neighbours nb of (u_nb - u_c) / ds^2
+//            (five points; a wall neighbour is the cell itself: even
+//            reflection, eq. BoundaryConditions)
+//   F(p,q) = fbar0 (Lap_q - Lap_p)/ds + fbar1 (u_q - u_p)/ds through each
+//            interior face, fbar = mean of the two cell values (Sec. Flux
+//            Discretization); wall faces carry no flux
+//   D_c    = [F_east - F_west + F_north - F_south] / ds     (eq. GovEqnCell2)
+//   b^n    = u^n - (1-theta) dt D(u^n);  G(u_k) = u_k + theta dt D(u_k) - b^n
+//   J_x    = d(x-face fluxes)/du without the derivative through the y part
+//            of the Laplacian (the neglected mixed term of eq.
+//            DirectionSplit); J_y likewise.
+//   (I + theta dt J_x) w = -G on rows, (I + theta dt J_y) v = w on columns,
+//   u_{k+1} = u_k + v                                (eqs. JacobianSystem1-3)
+// Pentadiagonal systems are solved by LU without pivoting (eq.
+// LUFactorization), one thread per line; factors go to global scratch
+// between the forward and the backward sweep.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tf_numeric.cuh"
+
+namespace tf {
+
+// ---------------------------------------------------------------------------
+// constants
+
+struct ModelK {
+  int nx, ny;
+  int model;  // 0 power law, 1 linear
+  int n, m;
+  double inv_ds, inv_ds2, inv_ds3;
+  double C;       // f0 = C h^3
+  double A1, B1;  // f1 = A1 s^(m-2) - B1 s^(n-2), s = 1/h
+  double c0, c1;  // linear model
+};
+
+struct StepK {
+  double theta_dt;  // theta dt
+  double expl_dt;   // (1 - theta) dt
+};
+
+struct PartX {  // per-block partial results of the x pass
+  double gnorm;
+  int pivot;
+  int pad;
+};
+struct PartY {  // per-block partial results of the y pass
+  double err, hmin;
+  long long mass;
+  int nonfinite, pivot;
+};
+struct Scalars {
+  double err, gnorm, hmin;
+  double mass;  // sum of the 2^-36 fixed-point images of the grid values
+  int nonfinite, pivot;
+};
+
+struct ModeFP64 {
+  typedef double HP;
+  typedef double LP;
+};
+struct ModeF32B {
+  typedef df64 HP;
+  typedef float LP;
+};
+
+// ---------------------------------------------------------------------------
+// precision helpers
+
+template <class T> TF_HD T from_f64(double d);
+template <> TF_HD double from_f64<double>(double d) { return d; }
+template <> TF_HD df64 from_f64<df64>(double d) { return df_of_f64(d); }
+template <> TF_HD float from_f64<float>(double d) { return f32_trunc_of_f64(d); }
+
+template <class LP, class HP> TF_HD LP to_lp(HP x);
+template <> TF_HD double to_lp<double, double>(double x) { return x; }
+template <> TF_HD float to_lp<float, df64>(df64 x) { return x.hi + x.lo; }
+
+TF_HD double to_f64(double x) { return x; }
+TF_HD double to_f64(df64 x) { return f64_of_df(x); }
+TF_HD double to_f64(float x) { return f64_of_f32(x); }
+
+TF_HD double rcp(double x) { return 1.0 / x; }
+TF_HD float rcp(float x) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(x);
+#else
+  return 1.0f / x;
+#endif
+}
+TF_HD df64 rcp(df64 x) { return df_rcp(x); }
+
+template <class T> TF_HD T one();
+template <> TF_HD double one<double>() { return 1.0; }
+template <> TF_HD float one<float>() { return 1.0f; }
+template <> TF_HD df64 one<df64>() { return df_make(1.0f, 0.0f); }
+template <class T> TF_HD T zero();
+template <> TF_HD double zero<double>() { return 0.0; }
+template <> TF_HD float zero<float>() { return 0.0f; }
+template <> TF_HD df64 zero<df64>() { return df_make(0.0f, 0.0f); }
+
+template <class T> TF_HD T ipow(T x, int k) {
+  T r = x;
+  for (int i = 1; i < k; ++i) r = r * x;
+  return r;
+}
+// h^(-k) written through s = 1/h for k >= 0 and through h for k < 0.
+template <class T> TF_HD T hpow_neg(const T& h, const T& s, int k) {
+  if (k > 0) return ipow(s, k);
+  if (k < 0) return ipow(h, -k);
+  return one<T>();
+}
+
+template <class T> struct MobC {
+  T C, A1, B1, c0, c1, three, half;
+  int model, n, m;
+};
+template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
+  MobC<T> c;
+  c.C = from_f64<T>(M.C);
+  c.A1 = from_f64<T>(M.A1);
+  c.B1 = from_f64<T>(M.B1);
+  c.c0 = from_f64<T>(M.c0);
+  c.c1 = from_f64<T>(M.c1);
+  c.three = from_f64<T>(3.0);
+  c.half = from_f64<T>(0.5);
+  c.model = M.model;
+  c.n = M.n;
+  c.m = M.m;
+  return c;
+}
+
+// f0 = C h^3 and f1 = h^3 Pi'(h) = A1 h^(2-m) - B1 h^(2-n)
+// (Sec. Thin Film Models, eq. GeneralDisPreForm).
+template <class T>
+TF_HD void mobility(const MobC<T>& c, const T& h, const T& s, T& f0, T& f1) {
+  if (c.model == 1) {
+    f0 = c.c0;
+    f1 = c.c1;
+    return;
+  }
+  f0 = c.C * (h * h) * h;
+  T a = c.m == 2 ? c.A1 : c.A1 * hpow_neg(h, s, c.m - 2);
+  T b = c.n == 2 ? c.B1 : c.B1 * hpow_neg(h, s, c.n - 2);
+  f1 = a - b;
+}
+// f0' = 3 C h^2, f1' = -(m-2) A1 h^(1-m) + (n-2) B1 h^(1-n).
+template <class T>
+TF_HD void mobility_d(const MobC<T>& c, const T& h, const T& s, T& d0, T& d1) {
+  if (c.model == 1) {
+    d0 = zero<T>();
+    d1 = zero<T>();
+    return;
+  }
+  d0 = c.three * c.C * (h * h);
+  T a = from_f64<T>((double)(c.m - 2)) * c.A1 * hpow_neg(h, s, c.m - 1);
+  T b = from_f64<T>((double)(c.n - 2)) * c.B1 * hpow_neg(h, s, c.n - 1);
+  d1 = b - a;
+}
+
+TF_HD int reflect_index(int i, int n) {
+  // Even reflection about the walls: -1 -> 0, -2 -> 1, n -> n-1, n+1 -> n-2
+  // (repeated for lines shorter than two cells).
+  for (int k = 0; k < 3; ++k) {
+    if (i < 0) i = -1 - i;
+    if (i >= n) i = 2 * n - 1 - i;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// ---------------------------------------------------------------------------
+// Tile stencil: per-cell quantities, face fluxes and D' on a TR x TC tile
+// of cells whose first cell is (j0, x0).  D = (1/2) inv_ds^2 D'.
+
+template <class HP, int TR, int TC> struct StencilSmem {
+  HP u[TR + 4][TC + 4];              // u on rows j0-2.., cols x0-2..
+  HP lap[TR + 2][TC + 2];            // on rows j0-1.., cols x0-1..
+  HP f0[TR + 2][TC + 2], f1[TR + 2][TC + 2], s[TR + 2][TC + 2];
+  HP fx[TR][TC + 1];                 // face between cols x0-1+c and x0+c
+  HP fy[TR + 1][TC];                 // face between rows j0-1+r and j0+r
+};
+
+template <class HP, int TR, int TC>
+__device__ __forceinline__ void stencil_load(StencilSmem<HP, TR, TC>& S, const double* __restrict__ u,
+                                             const ModelK& M, int j0, int x0, int tid, int nt) {
+  for (int k = tid; k < (TR + 4) * (TC + 4); k += nt) {
+    int r = k / (TC + 4), c = k - r * (TC + 4);
+    int gj = reflect_index(j0 - 2 + r, M.ny), gi = reflect_index(x0 - 2 + c, M.nx);
+    S.u[r][c] = from_f64<HP>(__ldg(u + (size_t)gj * M.nx + gi));
+  }
+}
+
+template <class HP, int TR, int TC>
+__device__ __forceinline__ void stencil_cells(StencilSmem<HP, TR, TC>& S, const MobC<HP>& mc,
+                                              const HP& inv_ds2, int tid, int nt) {
+  for (int k = tid; k < (TR + 2) * (TC + 2); k += nt) {
+    int r = k / (TC + 2), c = k - r * (TC + 2);
+    HP uc = S.u[r + 1][c + 1];
+    HP d = ((S.u[r + 1][c + 2] - uc) + (S.u[r + 1][c] - uc)) +
+           ((S.u[r + 2][c + 1] - uc) + (S.u[r][c + 1] - uc));
+    S.lap[r][c] = d * inv_ds2;
+    HP s = rcp(uc);
+    HP f0, f1;
+    mobility(mc, uc, s, f0, f1);
+    S.s[r][c] = s;
+    S.f0[r][c] = f0;
+    S.f1[r][c] = f1;
+  }
+}
+
+// Unscaled face flux F' = (f0p + f0q)(Lq - Lp) + (f1p + f1q)(uq - up);
+// F = F' / (2 ds).  Zero through the walls.
+template <class HP, int TR, int TC>
+__device__ __forceinline__ void stencil_faces(StencilSmem<HP, TR, TC>& S, const ModelK& M, int j0,
+                                              int x0, int tid, int nt) {
+  for (int k = tid; k < TR * (TC + 1); k += nt) {
+    int r = k / (TC + 1), c = k - r * (TC + 1);
+    int gp = x0 - 1 + c;  // left cell of the face
+    HP F = zero<HP>();
+    if (gp >= 0 && gp + 1 < M.nx) {
+      int rr = r + 1;  // region row of cell row j0 + r
+      F = (S.f0[rr][c] + S.f0[rr][c + 1]) * (S.lap[rr][c + 1] - S.lap[rr][c]) +
+          (S.f1[rr][c] + S.f1[rr][c + 1]) * (S.u[rr + 1][c + 2] - S.u[rr + 1][c + 1]);
+    }
+    S.fx[r][c] = F;
+  }
+  for (int k = tid; k < (TR + 1) * TC; k += nt) {
+    int r = k / TC, c = k - r * TC;
+    int gp = j0 - 1 + r;  // lower cell of the face
+    HP F = zero<HP>();
+    if (gp >= 0 && gp + 1 < M.ny) {
+      int cc = c + 1;  // region col of cell col x0 + c
+      F = (S.f0[r][cc] + S.f0[r + 1][cc]) * (S.lap[r + 1][cc] - S.lap[r][cc]) +
+          (S.f1[r][cc] + S.f1[r + 1][cc]) * (S.u[r + 2][cc + 1] - S.u[r + 1][cc + 1]);
+    }
+    S.fy[r][c] = F;
+  }
+}
+
+template <class HP, int TR, int TC>
+__device__ __forceinline__ HP stencil_dprime(const StencilSmem<HP, TR, TC>& S, int r, int c) {
+  return (S.fx[r][c + 1] - S.fx[r][c]) + (S.fy[r + 1][c] - S.fy[r][c]);
+}
+
+// ---------------------------------------------------------------------------
+// 2-D stencil kernel: explicit part b^n (OUT_B) or residual G (OUT_G).
+
+template <class Mode, int OUT_G>
+__global__ void __launch_bounds__(256)
+    k_stencil(ModelK M, StepK K, const double* __restrict__ u, typename Mode::HP* __restrict__ bn,
+              double* __restrict__ G, PartX* __restrict__ part) {
+  typedef typename Mode::HP HP;
+  constexpr int T = 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StencilSmem<HP, T, T>& S = *reinterpret_cast<StencilSmem<HP, T, T>*>(smem_raw);
+  const int tid = threadIdx.y * T + threadIdx.x, nt = T * T;
+  const int x0 = blockIdx.x * T, j0 = blockIdx.y * T;
+  const MobC<HP> mc = mob_consts<HP>(M);
+  const HP inv_ds2 = from_f64<HP>(M.inv_ds2);
+  stencil_load(S, u, M, j0, x0, tid, nt);
+  __syncthreads();
+  stencil_cells(S, mc, inv_ds2, tid, nt);
+  __syncthreads();
+  stencil_faces(S, M, j0, x0, tid, nt);
+  __syncthreads();
+  const int r = threadIdx.y, c = threadIdx.x;
+  const int gj = j0 + r, gi = x0 + c;
+  double g = 0.0;
+  if (gj < M.ny && gi < M.nx) {
+    const size_t idx = (size_t)gj * M.nx + gi;
+    HP dp = stencil_dprime(S, r, c);
+    HP uc = S.u[r + 2][c + 2];
+    if (OUT_G) {
+      HP scale = from_f64<HP>(0.5 * M.inv_ds2 * K.theta_dt);
+      HP Gv = (uc - bn[idx]) + scale * dp;
+      G[idx] = to_f64(Gv);
+      g = fabs(to_f64(Gv));
+    } else {
+      HP scale = from_f64<HP>(0.5 * M.inv_ds2 * K.expl_dt);
+      bn[idx] = uc - scale * dp;
+    }
+  }
+  if (OUT_G) {
+    for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+    __shared__ double red[8];
+    if ((tid & 31) == 0) red[tid >> 5] = g;
+    __syncthreads();
+    if (tid == 0) {
+      double mx = red[0];
+      for (int k = 1; k < 8; ++k) mx = fmax(mx, red[k]);
+      part[blockIdx.y * gridDim.x + blockIdx.x].gnorm = mx;
+      part[blockIdx.y * gridDim.x + blockIdx.x].pivot = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Line band assembly and LU
+
+template <class LP> struct CellLP {
+  LP u, lap, f0, f1, d0, d1;
+};
+
+// dF of one interior face between line cells p and q = p+1, scaled by
+// sc = theta dt / ds, for the columns p-1, p, q, q+1.  pl: p has a left
+// neighbour; qr: q has a right neighbour.
+template <class LP>
+__device__ __forceinline__ void face_dF(const CellLP<LP>& P, const CellLP<LP>& Q, bool pl, bool qr,
+                                        LP inv_ds, LP inv_ds3, LP sc, LP dF[4]) {
+  const LP h = LP(0.5);
+  LP gL = (Q.lap - P.lap) * inv_ds;
+  LP gU = (Q.u - P.u) * inv_ds;
+  LP c3 = h * (P.f0 + Q.f0) * inv_ds3 * sc;
+  LP Bd = h * (P.f1 + Q.f1) * inv_ds * sc;
+  LP wp = pl ? LP(1) : LP(0), wq = qr ? LP(1) : LP(0);
+  dF[0] = -wp * c3;
+  dF[1] = (LP(2) + wp) * c3 + h * sc * (P.d0 * gL + P.d1 * gU) - Bd;
+  dF[2] = -(LP(2) + wq) * c3 + h * sc * (Q.d0 * gL + Q.d1 * gU) + Bd;
+  dF[3] = wq * c3;
+}
+
+template <class LP> struct LUState {
+  LP g1, d1, z1, g2, d2, z2;  // (gamma, delta, z) of rows i-1 and i-2
+  __device__ __forceinline__ void reset() { g1 = d1 = z1 = g2 = d2 = z2 = LP(0); }
+  // Eliminate row i (a x_{i-2} + b x_{i-1} + c x_i + d x_{i+1} + e x_{i+2} = r);
+  // returns false on a zero or non-finite pivot.
+  __device__ __forceinline__ bool step(LP a, LP b, LP c, LP d, LP e, LP r, LP& g, LP& dl, LP& z) {
+    LP beta = b - a * g2;
+    LP mu = c - a * d2 - beta * g1;
+    LP inv = rcp(mu);
+    g = (d - beta * d1) * inv;
+    dl = e * inv;
+    z = (r - a * z2 - beta * z1) * inv;
+    g2 = g1;
+    d2 = d1;
+    z2 = z1;
+    g1 = g;
+    d1 = dl;
+    z1 = z;
+    return (mu != LP(0)) && isfinite(mu);
+  }
+};
+
+template <class LP>
+__device__ __forceinline__ void band_row(const LP L[4], const LP R[4], LP& a, LP& b, LP& c, LP& d,
+                                         LP& e) {
+  a = -L[0];
+  b = R[0] - L[1];
+  c = LP(1) + R[1] - L[2];
+  d = R[2] - L[3];
+  e = R[3];
+}
+
+// ---------------------------------------------------------------------------
+// x pass: residual, J_x assembly and row solves.  One block = 32 rows, one
+// thread per row; the row is walked in chunks of TC columns staged through
+// shared memory.  Output: w (LP).  fac: LP scratch of
+// 3 * gridDim.x * nchunks * 32 * TC.
+
+template <class HP, class LP, int TC> struct PassXSmem {
+  StencilSmem<HP, 32, TC> st;
+  LP rhs[32][TC + 1];
+  LP fac[3][32][TC + 1];
+};
+
+template <class Mode, int TC>
+__global__ void __launch_bounds__(32)
+    k_pass_x(ModelK M, StepK K, const double* __restrict__ u, const typename Mode::HP* __restrict__ bn,
+             typename Mode::LP* __restrict__ w, typename Mode::LP* __restrict__ fac,
+             PartX* __restrict__ part) {
+  typedef typename Mode::HP HP;
+  typedef typename Mode::LP LP;
+  constexpr int TR = 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PassXSmem<HP, LP, TC>& S = *reinterpret_cast<PassXSmem<HP, LP, TC>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int j0 = blockIdx.x * TR;
+  const int row = j0 + tid;
+  const bool active = row < M.ny;
+  const int nchunk = (M.nx + TC - 1) / TC;
+  const MobC<HP> mc = mob_consts<HP>(M);
+  const MobC<LP> ml = mob_consts<LP>(M);
+  const HP inv_ds2 = from_f64<HP>(M.inv_ds2);
+  const HP gscale = from_f64<HP>(0.5 * M.inv_ds2 * K.theta_dt);
+  const LP inv_ds = (LP)M.inv_ds, inv_ds3 = (LP)M.inv_ds3, sc = (LP)(K.theta_dt * M.inv_ds);
+  LP* facblk = fac + (size_t)blockIdx.x * nchunk * 3 * TR * TC;
+
+  double gmax = 0.0;
+  int pivot_bad = 0;
+  LUState<LP> lu;
+  lu.reset();
+  LP Lf[4] = {LP(0), LP(0), LP(0), LP(0)};
+  CellLP<LP> P;
+
+  for (int q = 0; q < nchunk; ++q) {
+    const int x0 = q * TC;
+    stencil_load(S.st, u, M, j0, x0, tid, 32);
+    __syncthreads();
+    stencil_cells(S.st, mc, inv_ds2, tid, 32);
+    __syncthreads();
+    stencil_faces(S.st, M, j0, x0, tid, 32);
+    __syncthreads();
+    for (int k = tid; k < TR * TC; k += 32) {
+      int r = k / TC, c = k - r * TC;
+      int gj = j0 + r, gi = x0 + c;
+      LP rv = LP(0);
+      if (gj < M.ny && gi < M.nx) {
+        HP Gv = (S.st.u[r + 2][c + 2] - bn[(size_t)gj * M.nx + gi]) + gscale * stencil_dprime(S.st, r, c);
+        rv = -to_lp<LP, HP>(Gv);
+        double ag = fabs(to_f64(Gv));
+        if (!(ag <= gmax)) gmax = ag;
+      }
+      S.rhs[r][c] = rv;
+    }
+    __syncthreads();
+    // sequential sweep of this thread's row over the chunk
+    if (active) {
+      auto cell = [&](int c) {  // region col of cell x0 + c is c + 1
+        CellLP<LP> X;
+        int rr = tid + 1, cc = c + 1;
+        X.u = to_lp<LP, HP>(S.st.u[rr + 1][cc + 1]);
+        X.lap = to_lp<LP, HP>(S.st.lap[rr][cc]);
+        X.f0 = to_lp<LP, HP>(S.st.f0[rr][cc]);
+        X.f1 = to_lp<LP, HP>(S.st.f1[rr][cc]);
+        LP s = to_lp<LP, HP>(S.st.s[rr][cc]);
+        mobility_d(ml, X.u, s, X.d0, X.d1);
+        return X;
+      };
+      if (q == 0) P = cell(0);
+      for (int c = 0; c < TC; ++c) {
+        const int i = x0 + c;
+        if (i >= M.nx) break;
+        LP Rf[4] = {LP(0), LP(0), LP(0), LP(0)};
+        CellLP<LP> Q;
+        if (i + 1 < M.nx) {
+          Q = cell(c + 1);
+          face_dF(P, Q, i > 0, i + 2 < M.nx, inv_ds, inv_ds3, sc, Rf);
+        }
+        LP a, b, cc, d, e, g, dl, z;
+        band_row(Lf, Rf, a, b, cc, d, e);
+        if (!lu.step(a, b, cc, d, e, S.rhs[tid][c], g, dl, z)) pivot_bad = 1;
+        S.fac[0][tid][c] = g;
+        S.fac[1][tid][c] = dl;
+        S.fac[2][tid][c] = z;
+        for (int t = 0; t < 4; ++t) Lf[t] = Rf[t];
+        P = Q;
+      }
+    }
+    __syncthreads();
+    LP* fq = facblk + (size_t)q * 3 * TR * TC;
+    for (int k = tid; k < 3 * TR * TC; k += 32) {
+      int f = k / (TR * TC), rem = k - f * TR * TC, r = rem / TC, c = rem - r * TC;
+      fq[k] = S.fac[f][r][c];
+    }
+    __syncthreads();
+  }
+  // backward sweep
+  LP x1 = LP(0), x2 = LP(0);
+  for (int q = nchunk - 1; q >= 0; --q) {
+    const int x0 = q * TC;
+    const LP* fq = facblk + (size_t)q * 3 * TR * TC;
+    for (int k = tid; k < 3 * TR * TC; k += 32) {
+      int f = k / (TR * TC), rem = k - f * TR * TC, r = rem / TC, c = rem - r * TC;
+      S.fac[f][r][c] = fq[k];
+    }
+    __syncthreads();
+    if (active) {
+      for (int c = TC - 1; c >= 0; --c) {
+        if (x0 + c >= M.nx) continue;
+        LP x = S.fac[2][tid][c] - S.fac[0][tid][c] * x1 - S.fac[1][tid][c] * x2;
+        S.rhs[tid][c] = x;
+        x2 = x1;
+        x1 = x;
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < TR * TC; k += 32) {
+      int r = k / TC, c = k - r * TC;
+      int gj = j0 + r, gi = x0 + c;
+      if (gj < M.ny && gi < M.nx) w[(size_t)gj * M.nx + gi] = S.rhs[r][c];
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    pivot_bad |= __shfl_xor_sync(0xffffffffu, pivot_bad, o);
+  }
+  if (tid == 0) {
+    part[blockIdx.x].gnorm = gmax;
+    part[blockIdx.x].pivot = pivot_bad;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y pass: J_y assembly, column solves, update and reductions.  One block =
+// 32 columns, one thread per column; rows walked in chunks of RY staged in
+// shared memory (u in LP with a two-cell halo).  fac: LP scratch 3 * nx*ny.
+
+template <class LP, int RY> struct PassYSmem {
+  LP u[RY + 4][34];  // rows y0-2.., cols i0-1..i0+32
+};
+
+template <class Mode> __device__ __forceinline__ double update_u(double uk, double v);
+template <> __device__ __forceinline__ double update_u<ModeFP64>(double uk, double v) { return uk + v; }
+template <class Mode> __device__ __forceinline__ double update_uf(double uk, float v);
+template <> __device__ __forceinline__ double update_uf<ModeF32B>(double uk, float v) {
+  return f64_add_f32(uk, v);
+}
+
+__device__ __forceinline__ double rel_update(double v, double uk) { return fabs(v / uk); }
+__device__ __forceinline__ double rel_update(float v, double uk) {
+  return (double)(fabsf(v) / fabsf(f32_trunc_of_f64(uk)));
+}
+
+template <class Mode, int RY>
+__global__ void __launch_bounds__(32)
+    k_pass_y(ModelK M, StepK K, const double* __restrict__ u, const typename Mode::LP* __restrict__ w,
+             typename Mode::LP* __restrict__ fac, double* __restrict__ unew, double* __restrict__ vout,
+             PartY* __restrict__ part) {
+  typedef typename Mode::LP LP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PassYSmem<LP, RY>& S = *reinterpret_cast<PassYSmem<LP, RY>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * 32;
+  const int col = i0 + tid;
+  const bool active = col < M.nx;
+  const size_t N = (size_t)M.nx * M.ny;
+  const MobC<LP> ml = mob_consts<LP>(M);
+  const LP inv_ds = (LP)M.inv_ds, inv_ds2 = (LP)M.inv_ds2, inv_ds3 = (LP)M.inv_ds3;
+  const LP sc = (LP)(K.theta_dt * M.inv_ds);
+  LP* fg = fac;
+  LP* fd = fac + N;
+  LP* fz = fac + 2 * N;
+  int pivot_bad = 0;
+  LUState<LP> lu;
+  lu.reset();
+  LP Lf[4] = {LP(0), LP(0), LP(0), LP(0)};
+  CellLP<LP> P;
+  for (int y0 = 0; y0 < M.ny; y0 += RY) {
+    for (int k = tid; k < (RY + 4) * 34; k += 32) {
+      int r = k / 34, c = k - r * 34;
+      int gj = reflect_index(y0 - 2 + r, M.ny), gi = reflect_index(i0 - 1 + c, M.nx);
+      S.u[r][c] = from_f64<LP>(__ldg(u + (size_t)gj * M.nx + gi));
+    }
+    __syncthreads();
+    if (active) {
+      auto cell = [&](int r) {  // cell (col, y0 + r) sits at S.u[r + 2][tid + 1]
+        CellLP<LP> X;
+        int rr = r + 2, cc = tid + 1;
+        LP uc = S.u[rr][cc];
+        X.u = uc;
+        X.lap = (((S.u[rr][cc + 1] - uc) + (S.u[rr][cc - 1] - uc)) +
+                 ((S.u[rr + 1][cc] - uc) + (S.u[rr - 1][cc] - uc))) * inv_ds2;
+        LP s = rcp(uc);
+        mobility(ml, uc, s, X.f0, X.f1);
+        mobility_d(ml, uc, s, X.d0, X.d1);
+        return X;
+      };
+      if (y0 == 0) P = cell(0);
+      for (int r = 0; r < RY; ++r) {
+        const int j = y0 + r;
+        if (j >= M.ny) break;
+        LP Rf[4] = {LP(0), LP(0), LP(0), LP(0)};
+        CellLP<LP> Q;
+        if (j + 1 < M.ny) {
+          Q = cell(r + 1);
+          face_dF(P, Q, j > 0, j + 2 < M.ny, inv_ds, inv_ds3, sc, Rf);
+        }
+        LP a, b, c, d, e, g, dl, z;
+        band_row(Lf, Rf, a, b, c, d, e);
+        const size_t idx = (size_t)j * M.nx + col;
+        if (!lu.step(a, b, c, d, e, w[idx], g, dl, z)) pivot_bad = 1;
+        fg[idx] = g;
+        fd[idx] = dl;
+        fz[idx] = z;
+        for (int t = 0; t < 4; ++t) Lf[t] = Rf[t];
+        P = Q;
+      }
+    }
+    __syncthreads();
+  }
+  double err = 0.0, hmin = INFINITY;
+  long long mass = 0;
+  int nonfinite = 0;
+  if (active) {
+    LP x1 = LP(0), x2 = LP(0);
+    for (int j = M.ny - 1; j >= 0; --j) {
+      const size_t idx = (size_t)j * M.nx + col;
+      LP x = fz[idx] - fg[idx] * x1 - fd[idx] * x2;
+      x2 = x1;
+      x1 = x;
+      const double uk = u[idx];
+      double un;
+      if constexpr (sizeof(LP) == 8)
+        un = update_u<Mode>(uk, (double)x);
+      else
+        un = update_uf<Mode>(uk, (float)x);
+      unew[idx] = un;
+      if (vout) vout[idx] = to_f64(x);
+      double ru = rel_update(x, uk);
+      if (!(ru <= err)) err = ru;
+      if (!(un > 0.0) || !isfinite(un)) nonfinite = 1;
+      hmin = fmin(hmin, un);
+      mass += fixed36_of_f64(un);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double e2 = __shfl_xor_sync(0xffffffffu, err, o);
+    if (!(e2 <= err)) err = e2;
+    hmin = fmin(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+    mass += __shfl_xor_sync(0xffffffffu, mass, o);
+    nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, o);
+    pivot_bad |= __shfl_xor_sync(0xffffffffu, pivot_bad, o);
+  }
+  if (tid == 0) {
+    PartY p;
+    p.err = err;
+    p.hmin = hmin;
+    p.mass = mass;
+    p.nonfinite = nonfinite;
+    p.pivot = pivot_bad;
+    part[blockIdx.x] = p;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions over the per-block partials (one block, fixed order).
+
+static __global__ void __launch_bounds__(256)
+    k_finalize(const PartX* __restrict__ px, int nx_part, const PartY* __restrict__ py, int ny_part,
+               Scalars* __restrict__ out) {
+  __shared__ double s_err[256], s_g[256], s_h[256], s_m[256];
+  __shared__ int s_nf[256], s_pv[256];
+  const int t = threadIdx.x;
+  double err = 0.0, g = 0.0, h = INFINITY, m = 0.0;
+  int nf = 0, pv = 0;
+  for (int k = t; k < nx_part; k += 256) {
+    if (!(px[k].gnorm <= g)) g = px[k].gnorm;
+    pv |= px[k].pivot;
+  }
+  for (int k = t; k < ny_part; k += 256) {
+    if (!(py[k].err <= err)) err = py[k].err;
+    h = fmin(h, py[k].hmin);
+    m += (double)py[k].mass;
+    nf |= py[k].nonfinite;
+    pv |= py[k].pivot;
+  }
+  s_err[t] = err;
+  s_g[t] = g;
+  s_h[t] = h;
+  s_m[t] = m;
+  s_nf[t] = nf;
+  s_pv[t] = pv;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (t < o) {
+      if (!(s_err[t + o] <= s_err[t])) s_err[t] = s_err[t + o];
+      if (!(s_g[t + o] <= s_g[t])) s_g[t] = s_g[t + o];
+      s_h[t] = fmin(s_h[t], s_h[t + o]);
+      s_m[t] += s_m[t + o];
+      s_nf[t] |= s_nf[t + o];
+      s_pv[t] |= s_pv[t + o];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    Scalars s;
+    s.err = s_err[0];
+    s.gnorm = s_g[0];
+    s.hmin = s_h[0];
+    s.mass = s_m[0];
+    s.nonfinite = s_nf[0];
+    s.pivot = s_pv[0];
+    *out = s;
+  }
+}
+
+// Mass and minimum of a grid (for tf_residual's norms).
+static __global__ void __launch_bounds__(256)
+    k_grid_stats(const double* __restrict__ u, size_t N, PartY* __restrict__ part) {
+  double h = INFINITY;
+  long long m = 0;
+  int nf = 0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+    double v = u[k];
+    h = fmin(h, v);
+    m += fixed36_of_f64(v);
+    if (!(v > 0.0) || !isfinite(v)) nf = 1;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    h = fmin(h, __shfl_xor_sync(0xffffffffu, h, o));
+    m += __shfl_xor_sync(0xffffffffu, m, o);
+    nf |= __shfl_xor_sync(0xffffffffu, nf, o);
+  }
+  __shared__ double sh[8];
+  __shared__ long long sm[8];
+  __shared__ int sn[8];
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = h;
+    sm[threadIdx.x >> 5] = m;
+    sn[threadIdx.x >> 5] = nf;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double hb = sh[0];
+    long long mb = sm[0];
+    int nb = sn[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      hb = fmin(hb, sh[k]);
+      mb += sm[k];
+      nb |= sn[k];
+    }
+    PartY p;
+    p.err = 0.0;
+    p.hmin = hb;
+    p.mass = mb;
+    p.nonfinite = nb;
+    p.pivot = 0;
+    part[blockIdx.x] = p;
+  }
+}
+
+template <class T>
+__global__ void k_to_f64(const T* __restrict__ x, double* __restrict__ y, size_t N) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
+    y[k] = to_f64(x[k]);
+}
+
+}  // namespace tf

@@ -1,0 +1,83 @@
+// tf_mode.cuh -- launchers of one precision mode; included once by
+// tf_mode_fp64.cu and once by tf_mode_f32b.cu.
+#pragma once
+
+#include "tf_internal.h"
+
+namespace tf {
+
+template <class Mode> struct Launch {
+  typedef typename Mode::HP HP;
+  typedef typename Mode::LP LP;
+  static constexpr size_t smem_stencil = sizeof(StencilSmem<HP, 16, 16>);
+  static constexpr size_t smem_x = sizeof(PassXSmem<HP, LP, kTileX>);
+  static constexpr size_t smem_y = sizeof(PassYSmem<LP, kRowsY>);
+
+  static StepK step(const tf_ctx& c, double dt) {
+    StepK k;
+    k.theta_dt = c.p.theta * dt;
+    k.expl_dt = (1.0 - c.p.theta) * dt;
+    return k;
+  }
+
+  static cudaError_t prepare() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_stencil<Mode, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_stencil)))
+      return e;
+    if ((e = cudaFuncSetAttribute(k_stencil<Mode, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_stencil)))
+      return e;
+    if ((e = cudaFuncSetAttribute(k_pass_x<Mode, kTileX>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x)))
+      return e;
+    return cudaFuncSetAttribute(k_pass_y<Mode, kRowsY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_y);
+  }
+
+  static cudaError_t explicit_part_c(tf_ctx& c, const double* u_old, double dt) {
+    dim3 grid(c.grid_st_x, c.grid_st_y), block(16, 16);
+    k_stencil<Mode, 0><<<grid, block, smem_stencil, c.stream>>>(c.mk, step(c, dt), u_old, (HP*)c.bn,
+                                                                nullptr, nullptr);
+    return cudaGetLastError();
+  }
+  static cudaError_t residual_c(tf_ctx& c, const double* u_k, double dt, double* G) {
+    dim3 grid(c.grid_st_x, c.grid_st_y), block(16, 16);
+    k_stencil<Mode, 1><<<grid, block, smem_stencil, c.stream>>>(c.mk, step(c, dt), u_k, (HP*)c.bn,
+                                                                G, c.px);
+    return cudaGetLastError();
+  }
+  static cudaError_t pass_x_c(tf_ctx& c, const double* u_k, double dt) {
+    k_pass_x<Mode, kTileX><<<c.grid_x, 32, smem_x, c.stream>>>(c.mk, step(c, dt), u_k, (const HP*)c.bn,
+                                                               (LP*)c.w, (LP*)c.fac_x, c.px);
+    return cudaGetLastError();
+  }
+  static cudaError_t pass_y_c(tf_ctx& c, const double* u_k, double dt, double* u_next,
+                              double* v_out) {
+    k_pass_y<Mode, kRowsY><<<c.grid_y, 32, smem_y, c.stream>>>(c.mk, step(c, dt), u_k, (const LP*)c.w,
+                                                               (LP*)c.fac_y, u_next, v_out, c.py);
+    return cudaGetLastError();
+  }
+  static cudaError_t w_to_f64_c(tf_ctx& c, double* out) {
+    if (sizeof(LP) == sizeof(double))
+      return cudaMemcpyAsync(out, c.w, c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+    k_to_f64<LP><<<1024, 256, 0, c.stream>>>((const LP*)c.w, out, c.N);
+    return cudaGetLastError();
+  }
+};
+
+template <class Mode> Ops make_ops() {
+  typedef Launch<Mode> L;
+  Ops o;
+  o.hp_bytes = sizeof(typename Mode::HP);
+  o.lp_bytes = sizeof(typename Mode::LP);
+  o.prepare = &L::prepare;
+  o.explicit_part = &L::explicit_part_c;
+  o.residual_g = &L::residual_c;
+  o.pass_x = &L::pass_x_c;
+  o.pass_y = &L::pass_y_c;
+  o.w_to_f64 = &L::w_to_f64_c;
+  return o;
+}
+
+}  // namespace tf

@@ -1,0 +1,111 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+function that include/tf.h declares; ctypes structs match the C layout;
+argument validation rejects bad input before any GPU work."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1806_10550_gb300 as tf
+
+ROOT = os.path.abspath(os.path.join(os.path.dirname(__file__), ".."))
+HDR = os.path.join(ROOT, "include", "tf.h")
+
+
+def declared_functions():
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tf_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_functions_exported():
+    L = tf.library()
+    names = declared_functions()
+    assert "tf_init" in names and "tf_advance" in names
+    for n in names:
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", tf._LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r" T (tf_\w+)", out))
+    assert set(names) <= exported, set(names) - exported
+
+
+def _c_layout():
+    prog = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "tf.h"
+#define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("tf_params %zu\ntf_step_info %zu\ntf_step_record %zu\ntf_advance_info %zu\ntf_norms %zu\n",
+         sizeof(tf_params), sizeof(tf_step_info), sizeof(tf_step_record), sizeof(tf_advance_info),
+         sizeof(tf_norms));
+  O(tf_params, ds); O(tf_params, kappa); O(tf_params, theta); O(tf_params, newton_fixed_iter);
+  O(tf_params, grow_after); O(tf_params, rupture_h); O(tf_params, precision);
+  O(tf_step_record, accepted); O(tf_step_record, hmin); O(tf_advance_info, dt);
+  return 0;
+}
+'''
+    d = os.path.join(ROOT, "paper_1806_10550_gb300", "_build")
+    os.makedirs(d, exist_ok=True)
+    src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+    open(src, "w").write(prog)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    return dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+
+
+def test_struct_layouts_match_header():
+    lay = {k: int(v) for k, v in _c_layout().items()}
+    assert lay["tf_params"] == C.sizeof(tf.TfParams)
+    assert lay["tf_step_info"] == C.sizeof(tf.TfStepInfo)
+    assert lay["tf_step_record"] == C.sizeof(tf.TfStepRecord)
+    assert lay["tf_advance_info"] == C.sizeof(tf.TfAdvanceInfo)
+    assert lay["tf_norms"] == C.sizeof(tf.TfNorms)
+    for key, v in lay.items():
+        if "." in key:
+            T, f = key.split(".")
+            cls = {"tf_params": tf.TfParams, "tf_step_record": tf.TfStepRecord,
+                   "tf_advance_info": tf.TfAdvanceInfo}[T]
+            assert getattr(cls, f).offset == v, key
+
+
+def test_params_default():
+    p = tf.tf_params_default()
+    assert p.model == tf.TF_MODEL_POWERLAW and p.n == 3 and p.m == 2 and p.b == 0.1
+    assert p.theta == 0.5 and p.newton_tol == 1e-10 and p.newton_max_iter == 10
+    assert p.precision == tf.TF_FP64 and p.nx == 0
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-3), dict(ds=0.0), dict(theta=1.5),
+                                 dict(newton_max_iter=0), dict(precision=7), dict(model=9),
+                                 dict(n=2, m=2), dict(b=-1.0), dict(dt_shrink=1.0),
+                                 dict(nx=70000, ny=70000)])
+def test_init_rejects_bad_parameters(bad):
+    p = tf.tf_params_default(nx=16, ny=16, ds=1.0)
+    for k, v in bad.items():
+        setattr(p, k, v)
+    h = C.c_void_p(123)
+    rc = tf.library().tf_init(C.byref(p), None, C.byref(h))
+    assert rc == tf.TF_ERR_ARG
+    assert h.value is None
+
+
+def test_null_arguments_rejected():
+    L = tf.library()
+    assert L.tf_init(None, None, None) == tf.TF_ERR_ARG
+    assert L.tf_newton_adi_step(None, None, None, 1.0, None) == tf.TF_ERR_ARG
+    assert L.tf_residual(None, None, None, 1.0, None, None) == tf.TF_ERR_ARG
+    assert L.tf_advance(None, None, 0.0, 1.0, 1.0, 1, None, None, None, None) == tf.TF_ERR_ARG
+    assert tf.tf_strerror(tf.TF_ERR_ARG) == "invalid argument"
+    L.tf_destroy(None)
+
+
+def test_no_cpu_fallback_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(RuntimeError, match="CUDA device is required"):
+        tf.Context(tf.tf_params_default(nx=8, ny=8, ds=1.0))
