@@ -202,6 +202,31 @@ typedef struct {
 int tf_timing_enable(tf_ctx* ctx, int on);
 int tf_timing_get(const tf_ctx* ctx, tf_timing* out);
 
+/* ---- residual without allocation ----------------------------------------
+ * The paper has no counterpart to this entry point: it is a service to
+ * callers that may not allocate device memory (a host framework that owns
+ * every allocation, a latency-bounded loop, a plugin handed buffers but no
+ * right to create a context).  It computes what tf_residual computes,
+ *   G = h_k + theta dt D(h_k) - [h_old - (1-theta) dt D(h_old)],
+ * for the parameters *p (validated as tf_init does; workspace-free) on the
+ * given stream (cudaStream_t as void*, NULL = legacy default stream).
+ * h_k, h_old: device grids [ny][nx]; G: device output grid (required);
+ * out: host struct or NULL (gnorm = max|G|, mass and hmin of h_k; when
+ * given, the call synchronises the stream).
+ * Scratch: one fixed device array of this library (TF_NOALLOC_MAX_CELLS
+ * cells plus partial results, about 16.3 MiB), present on every GPU that
+ * loads the library until the process exits; grids larger than
+ * TF_NOALLOC_MAX_CELLS cells return TF_ERR_ARG.  The call makes no
+ * cudaMalloc, cudaFree or other allocating call.  The first call on each
+ * device looks up the array's device address (with that device current);
+ * make that first call before any stream capture.  Calls share the array,
+ * which keeps the last call's contents (each call writes every element it
+ * reads before reading it), so calls that overlap on the GPU race: the
+ * caller must serialise them.  Returns TF_OK, TF_ERR_ARG or TF_ERR_CUDA. */
+#define TF_NOALLOC_MAX_CELLS (1 << 21)
+int tf_residual_noalloc(const tf_params* p, void* stream, const double* h_k,
+                        const double* h_old, double dt, double* G, tf_norms* out);
+
 #ifdef __cplusplus
 }
 #endif
