@@ -194,9 +194,10 @@ typedef struct {
   int enabled;
   int launches;          /* kernels launched while enabled (all kinds)       */
   int explicit_launches; /* b^n stencil launches                             */
-  int x_launches;        /* x-line pass launches                             */
-  int y_launches;        /* y-line pass launches                             */
-  double explicit_ms, x_ms, y_ms; /* summed event durations, milliseconds    */
+  int rhs_launches;      /* residual (right side of the x solve) launches    */
+  int x_launches;        /* x-line sweep launches                            */
+  int y_launches;        /* y-line sweep launches                            */
+  double explicit_ms, rhs_ms, x_ms, y_ms; /* summed event durations, ms      */
 } tf_timing;
 
 int tf_timing_enable(tf_ctx* ctx, int on);

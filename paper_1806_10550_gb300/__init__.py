@@ -71,8 +71,9 @@ class TfAdvanceInfo(C.Structure):
 
 class TfTiming(C.Structure):
     _fields_ = [("enabled", C.c_int), ("launches", C.c_int), ("explicit_launches", C.c_int),
-                ("x_launches", C.c_int), ("y_launches", C.c_int), ("explicit_ms", C.c_double),
-                ("x_ms", C.c_double), ("y_ms", C.c_double)]
+                ("rhs_launches", C.c_int), ("x_launches", C.c_int), ("y_launches", C.c_int),
+                ("explicit_ms", C.c_double), ("rhs_ms", C.c_double), ("x_ms", C.c_double),
+                ("y_ms", C.c_double)]
 
 
 _lib = None

@@ -40,25 +40,30 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
   return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? ms : 0.0f;
 }
 
-// One pseudo-Newton ADI iteration from u_k (b^n already formed).
+// One pseudo-Newton ADI iteration from u_k (b^n already formed):
+// residual -> x sweep -> y sweep -> reductions.
 int iterate(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_out, double* v_out,
             Scalars* s) {
   const bool tm = c.timing.enabled;
   if (tm) TF_CK(cudaEventRecord(c.ev[0], c.stream));
-  TF_CK(c.ops->pass_x(c, u_k, dt));
+  TF_CK(c.ops->rhs(c, u_k, dt));
   if (tm) TF_CK(cudaEventRecord(c.ev[1], c.stream));
-  if (w_out) TF_CK(c.ops->w_to_f64(c, w_out));
+  TF_CK(c.ops->xsweep(c, dt, u_k));
   if (tm) TF_CK(cudaEventRecord(c.ev[2], c.stream));
-  TF_CK(c.ops->pass_y(c, u_k, dt, u_next, v_out));
+  if (w_out) TF_CK(c.ops->w_to_f64(c, w_out));
   if (tm) TF_CK(cudaEventRecord(c.ev[3], c.stream));
-  int r = finalize(c, c.grid_x, c.grid_y);
+  TF_CK(c.ops->ysweep(c, u_k, dt, u_next, v_out));
+  if (tm) TF_CK(cudaEventRecord(c.ev[4], c.stream));
+  int r = finalize(c, c.grid_rx * c.grid_ry + c.grid_x, c.grid_y);
   if (r) return r;
   if (tm) {
-    c.timing.x_ms += elapsed(c.ev[0], c.ev[1]);
-    c.timing.y_ms += elapsed(c.ev[2], c.ev[3]);
+    c.timing.rhs_ms += elapsed(c.ev[0], c.ev[1]);
+    c.timing.x_ms += elapsed(c.ev[1], c.ev[2]);
+    c.timing.y_ms += elapsed(c.ev[3], c.ev[4]);
+    c.timing.rhs_launches++;
     c.timing.x_launches++;
     c.timing.y_launches++;
-    c.timing.launches += 3 + (w_out && c.ops->lp_bytes != sizeof(double) ? 1 : 0);
+    c.timing.launches += 4 + (w_out && c.ops->lp_bytes != sizeof(double) ? 1 : 0);
   }
   *s = *c.hsc;
   return TF_OK;
@@ -186,7 +191,7 @@ void tf_destroy(tf_ctx* c) {
   cudaFree(c->py);
   cudaFree(c->dsc);
   if (c->hsc) cudaFreeHost(c->hsc);
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 5; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   free(c);
 }
@@ -239,14 +244,18 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   mk.c1 = p->c1;
   c->grid_x = (p->ny + 31) / 32;
   c->grid_y = (p->nx + 31) / 32;
-  c->nchunk_x = (p->nx + tf::kTileX - 1) / tf::kTileX;
+  c->grid_rx = (p->nx + 31) / 32;
+  c->grid_ry = (p->ny + 31) / 32;
   c->grid_st_x = (p->nx + 15) / 16;
   c->grid_st_y = (p->ny + 15) / 16;
   c->grid_stats = 304;
-  c->n_px = c->grid_x > c->grid_st_x * c->grid_st_y ? c->grid_x : c->grid_st_x * c->grid_st_y;
+  {
+    int a = c->grid_rx * c->grid_ry + c->grid_x, b = c->grid_st_x * c->grid_st_y;
+    c->n_px = a > b ? a : b;
+  }
   c->n_py = c->grid_y > c->grid_stats ? c->grid_y : c->grid_stats;
   const size_t hp = c->ops->hp_bytes, lp = c->ops->lp_bytes;
-  const size_t facx = (size_t)3 * c->grid_x * c->nchunk_x * 32 * tf::kTileX;
+  const size_t facx = (size_t)3 * c->grid_x * 32 * (size_t)p->nx;
   int r = TF_OK;
   cudaError_t e = c->ops->prepare();
   if (e != cudaSuccess) r = cuda_fail(e);
@@ -263,7 +272,7 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
     e = cudaMallocHost((void**)&c->hsc, sizeof(Scalars));
     if (e != cudaSuccess) r = cuda_fail(e);
   }
-  for (int k = 0; k < 4 && !r; ++k) {
+  for (int k = 0; k < 5 && !r; ++k) {
     e = cudaEventCreate(&c->ev[k]);
     if (e != cudaSuccess) r = cuda_fail(e);
   }

@@ -6,12 +6,10 @@
 #include <stddef.h>
 
 #include "../../include/tf.h"
-#include "tf_kernels.cuh"
+#include "tf_sweeps.cuh"
 
 namespace tf {
 
-constexpr int kTileX = 16;  // columns per chunk of the x pass
-constexpr int kRowsY = 32;  // rows per chunk of the y pass
 
 }  // namespace tf
 
@@ -24,8 +22,9 @@ struct Ops {
   cudaError_t (*prepare)();
   cudaError_t (*explicit_part)(tf_ctx& c, const double* u_old, double dt);
   cudaError_t (*residual_g)(tf_ctx& c, const double* u_k, double dt, double* G);
-  cudaError_t (*pass_x)(tf_ctx& c, const double* u_k, double dt);
-  cudaError_t (*pass_y)(tf_ctx& c, const double* u_k, double dt, double* u_next, double* v_out);
+  cudaError_t (*rhs)(tf_ctx& c, const double* u_k, double dt);
+  cudaError_t (*xsweep)(tf_ctx& c, double dt, const double* u_k);
+  cudaError_t (*ysweep)(tf_ctx& c, const double* u_k, double dt, double* u_next, double* v_out);
   cudaError_t (*w_to_f64)(tf_ctx& c, double* out);
 };
 
@@ -41,15 +40,15 @@ struct tf_ctx {
   const tf::Ops* ops;
   cudaStream_t stream;
   size_t N;
-  int grid_x;      // blocks of the x pass (32 rows each)
-  int grid_y;      // blocks of the y pass (32 columns each)
-  int nchunk_x;    // column chunks of the x pass
-  int grid_st_x, grid_st_y;  // 2-D stencil grid
+  int grid_x;      // blocks of the x sweep (32 rows each)
+  int grid_y;      // blocks of the y sweep (32 columns each)
+  int grid_rx, grid_ry;      // 2-D residual grid (32 x 32 tiles)
+  int grid_st_x, grid_st_y;  // 2-D stencil grid (16 x 16 tiles)
   int grid_stats;  // blocks of k_grid_stats
   void* bn;        // explicit part b^n, HP storage
-  void* w;         // x-pass output, LP
-  void* fac_x;     // x-pass LU factors, LP
-  void* fac_y;     // y-pass LU factors, LP
+  void* w;         // right side of the x solve, overwritten by its solution w, LP
+  void* fac_x;     // x-sweep LU factors, LP
+  void* fac_y;     // y-sweep LU factors, LP
   double* ubuf;    // iterate buffer
   double* ubuf2;   // state buffer of tf_advance
   tf::PartX* px;
@@ -58,5 +57,5 @@ struct tf_ctx {
   tf::Scalars* dsc;
   tf::Scalars* hsc;  // pinned
   tf_timing timing;
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[5];
 };

@@ -92,7 +92,7 @@ TF_HD double to_f64(float x) { return f64_of_f32(x); }
 TF_HD double rcp(double x) { return 1.0 / x; }
 TF_HD float rcp(float x) {
 #ifdef __CUDA_ARCH__
-  return __frcp_rn(x);
+  return __fdividef(1.0f, x);  // MUFU reciprocal, about 2 ulp: FP32 solves only
 #else
   return 1.0f / x;
 #endif
@@ -122,6 +122,7 @@ template <class T> TF_HD T hpow_neg(const T& h, const T& s, int k) {
 
 template <class T> struct MobC {
   T C, A1, B1, c0, c1, three, half;
+  T dA1, dB1;  // (m-2) A1 and (n-2) B1
   int model, n, m;
 };
 template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
@@ -133,6 +134,8 @@ template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
   c.c1 = from_f64<T>(M.c1);
   c.three = from_f64<T>(3.0);
   c.half = from_f64<T>(0.5);
+  c.dA1 = from_f64<T>((double)(M.m - 2) * M.A1);
+  c.dB1 = from_f64<T>((double)(M.n - 2) * M.B1);
   c.model = M.model;
   c.n = M.n;
   c.m = M.m;
@@ -162,9 +165,8 @@ TF_HD void mobility_d(const MobC<T>& c, const T& h, const T& s, T& d0, T& d1) {
     return;
   }
   d0 = c.three * c.C * (h * h);
-  T a = from_f64<T>((double)(c.m - 2)) * c.A1 * hpow_neg(h, s, c.m - 1);
-  T b = from_f64<T>((double)(c.n - 2)) * c.B1 * hpow_neg(h, s, c.n - 1);
-  d1 = b - a;
+  T b = c.dB1 * hpow_neg(h, s, c.n - 1);
+  d1 = c.m == 2 ? b : b - c.dA1 * hpow_neg(h, s, c.m - 1);
 }
 
 TF_HD int reflect_index(int i, int n) {
@@ -517,8 +519,14 @@ template <> __device__ __forceinline__ double update_uf<ModeF32B>(double uk, flo
 }
 
 __device__ __forceinline__ double rel_update(double v, double uk) { return fabs(v / uk); }
-__device__ __forceinline__ double rel_update(float v, double uk) {
-  return (double)(fabsf(v) / fabsf(f32_trunc_of_f64(uk)));
+__device__ __forceinline__ float rel_update(float v, double uk) {
+  return __fdividef(fabsf(v), fabsf(f32_trunc_of_f64(uk)));
+}
+// Order-preserving integer key of a non-negative double (bit pattern);
+// negative values, zero, NaN and infinities are reported separately.
+__device__ __forceinline__ bool positive_finite_bits(double u) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+  return (b >> 63) == 0 && b != 0ull && ((b >> 52) & 0x7ff) != 0x7ff;
 }
 
 template <class Mode, int RY>

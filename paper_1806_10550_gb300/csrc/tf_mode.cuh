@@ -10,8 +10,9 @@ template <class Mode> struct Launch {
   typedef typename Mode::HP HP;
   typedef typename Mode::LP LP;
   static constexpr size_t smem_stencil = sizeof(StencilSmem<HP, 16, 16>);
-  static constexpr size_t smem_x = sizeof(PassXSmem<HP, LP, kTileX>);
-  static constexpr size_t smem_y = sizeof(PassYSmem<LP, kRowsY>);
+  static constexpr size_t smem_rhs = sizeof(RhsSmem<HP, 32>);
+  static constexpr size_t smem_x = sizeof(XSweepSmem<LP>);
+  static constexpr size_t smem_y = sizeof(YSweepSmem<LP>);
 
   static StepK step(const tf_ctx& c, double dt) {
     StepK k;
@@ -22,17 +23,12 @@ template <class Mode> struct Launch {
 
   static cudaError_t prepare() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_stencil<Mode, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_stencil)))
-      return e;
-    if ((e = cudaFuncSetAttribute(k_stencil<Mode, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_stencil)))
-      return e;
-    if ((e = cudaFuncSetAttribute(k_pass_x<Mode, kTileX>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x)))
-      return e;
-    return cudaFuncSetAttribute(k_pass_y<Mode, kRowsY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_y);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(k_stencil<Mode, 0>, A, (int)smem_stencil))) return e;
+    if ((e = cudaFuncSetAttribute(k_stencil<Mode, 1>, A, (int)smem_stencil))) return e;
+    if ((e = cudaFuncSetAttribute(k_rhs<Mode>, A, (int)smem_rhs))) return e;
+    if ((e = cudaFuncSetAttribute(k_xsweep<Mode>, A, (int)smem_x))) return e;
+    return cudaFuncSetAttribute(k_ysweep<Mode>, A, (int)smem_y);
   }
 
   static cudaError_t explicit_part_c(tf_ctx& c, const double* u_old, double dt) {
@@ -47,15 +43,21 @@ template <class Mode> struct Launch {
                                                                 G, c.px);
     return cudaGetLastError();
   }
-  static cudaError_t pass_x_c(tf_ctx& c, const double* u_k, double dt) {
-    k_pass_x<Mode, kTileX><<<c.grid_x, 32, smem_x, c.stream>>>(c.mk, step(c, dt), u_k, (const HP*)c.bn,
-                                                               (LP*)c.w, (LP*)c.fac_x, c.px);
+  static cudaError_t rhs_c(tf_ctx& c, const double* u_k, double dt) {
+    dim3 grid(c.grid_rx, c.grid_ry);
+    k_rhs<Mode><<<grid, 256, smem_rhs, c.stream>>>(c.mk, step(c, dt), u_k, (const HP*)c.bn, (LP*)c.w,
+                                                   c.px);
     return cudaGetLastError();
   }
-  static cudaError_t pass_y_c(tf_ctx& c, const double* u_k, double dt, double* u_next,
+  static cudaError_t xsweep_c(tf_ctx& c, double dt, const double* u_k) {
+    k_xsweep<Mode><<<c.grid_x, 64, smem_x, c.stream>>>(c.mk, step(c, dt), u_k, (LP*)c.w,
+                                                       (LP*)c.fac_x, c.px + c.grid_rx * c.grid_ry);
+    return cudaGetLastError();
+  }
+  static cudaError_t ysweep_c(tf_ctx& c, const double* u_k, double dt, double* u_next,
                               double* v_out) {
-    k_pass_y<Mode, kRowsY><<<c.grid_y, 32, smem_y, c.stream>>>(c.mk, step(c, dt), u_k, (const LP*)c.w,
-                                                               (LP*)c.fac_y, u_next, v_out, c.py);
+    k_ysweep<Mode><<<c.grid_y, 64, smem_y, c.stream>>>(c.mk, step(c, dt), u_k, (const LP*)c.w,
+                                                       (LP*)c.fac_y, u_next, v_out, c.py);
     return cudaGetLastError();
   }
   static cudaError_t w_to_f64_c(tf_ctx& c, double* out) {
@@ -74,8 +76,9 @@ template <class Mode> Ops make_ops() {
   o.prepare = &L::prepare;
   o.explicit_part = &L::explicit_part_c;
   o.residual_g = &L::residual_c;
-  o.pass_x = &L::pass_x_c;
-  o.pass_y = &L::pass_y_c;
+  o.rhs = &L::rhs_c;
+  o.xsweep = &L::xsweep_c;
+  o.ysweep = &L::ysweep_c;
   o.w_to_f64 = &L::w_to_f64_c;
   return o;
 }

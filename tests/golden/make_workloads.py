@@ -10,6 +10,7 @@ theta_c = 20 deg, M = 1/2, C = 1, h0 = 1):
   small     64^2 on 4 lambda_m, noise eps = 0.01, dt0 = 1e-3, T = 5/sigma_max
   scale2k   2048^2 on 64 lambda_m, noise eps = 0.01 (run to rupture)
   scale8k   8192^2 on 64 lambda_m, noise eps = 0.01 (200 timed steps)
+  prof4k    4096^2 on 64 lambda_m (profiling captures: inputs larger than L2)
   nucl8k    8192^2 on 256 lambda_m, eps = 1e-4 + 64 Gaussian depressions
             of depth 0.3 h0 and width lambda_m / 4
   adjoint1k 1024^2 on 16 lambda_m
@@ -40,6 +41,7 @@ def main():
         "scale2k": dict(common, N=2048, P=64, eps=0.01, seed=1235, dt0=1e-3, T=1e30),
         "scale8k": dict(common, N=8192, P=64, eps=0.01, seed=1235, dt0=1e-3, T=1e30,
                         steps=200),
+        "prof4k": dict(common, N=4096, P=64, eps=0.01, seed=1237, dt0=1e-3, T=1e30),
         "nucl8k": dict(common, N=8192, P=256, eps=1e-4, seed=1236, dt0=1e-3, T=1e30,
                        holes=64, depth=0.3, width=lam / 4.0),
         "adjoint1k": dict(common, N=1024, P=16, eps=0.01, seed=1238, dt0=1e-3,
