@@ -6,7 +6,7 @@
 #include <stddef.h>
 
 #include "../../include/tf.h"
-#include "tf_sweeps.cuh"
+#include "tf_sweeps3.cuh"
 
 namespace tf {
 

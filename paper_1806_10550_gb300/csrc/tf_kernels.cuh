@@ -152,6 +152,10 @@ TF_HD void mobility(const MobC<T>& c, const T& h, const T& s, T& f0, T& f1) {
     return;
   }
   f0 = c.C * (h * h) * h;
+  if (c.n == 3 && c.m == 2) {  // f1 = A1 - B1 / h
+    f1 = c.A1 - c.B1 * s;
+    return;
+  }
   T a = c.m == 2 ? c.A1 : c.A1 * hpow_neg(h, s, c.m - 2);
   T b = c.n == 2 ? c.B1 : c.B1 * hpow_neg(h, s, c.n - 2);
   f1 = a - b;
@@ -165,6 +169,10 @@ TF_HD void mobility_d(const MobC<T>& c, const T& h, const T& s, T& d0, T& d1) {
     return;
   }
   d0 = c.three * c.C * (h * h);
+  if (c.n == 3 && c.m == 2) {  // f1' = B1 / h^2
+    d1 = c.dB1 * (s * s);
+    return;
+  }
   T b = c.dB1 * hpow_neg(h, s, c.n - 1);
   d1 = c.m == 2 ? b : b - c.dA1 * hpow_neg(h, s, c.m - 1);
 }

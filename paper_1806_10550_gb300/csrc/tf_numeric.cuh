@@ -146,13 +146,13 @@ TF_HD void two_prod(float a, float b, float& p, float& e) {
   e = fma_f(a, b, -p);
 }
 
+// Addition with one TwoSum on the leading parts: the error is below about
+// 2^-48 (|a| + |b|), enough for sums and differences of the residual, where
+// the operands carry 2^-48 relative representation error already.
 TF_HD df64 operator+(df64 a, df64 b) {
-  float s, e, t, f;
+  float s, e;
   two_sum(a.hi, b.hi, s, e);
-  two_sum(a.lo, b.lo, t, f);
-  e += t;
-  fast_two_sum(s, e, s, e);
-  e += f;
+  e += a.lo + b.lo;
   fast_two_sum(s, e, s, e);
   return df_make(s, e);
 }
@@ -172,6 +172,15 @@ TF_HD df64 df_rcp(df64 a) {
   df64 Y = df_make(y, 0.0f);
   df64 r = df_make(1.0f, 0.0f) - a * Y;  // residual 1 - a y, small
   return Y + Y * r;
+}
+
+// Positive normal double -> float (truncated), five integer operations.
+// Valid for 2^-126 <= u < 2^128; used for film tiles of the FP32 Jacobian,
+// where any height outside that range already fails the step.
+TF_HD float f32_of_pos_f64_fast(double d) {
+  const uint64_t b = bits_of(d);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  return float_of((((hi - 0x38000000u) << 3) & 0x7ffffff8u) | (lo >> 29));
 }
 
 // double bit pattern -> df64 with integer operations: hi takes the leading
@@ -204,6 +213,24 @@ TF_HD df64 df_of_f64(double d) {
   if (lf <= 0) return df_make(hi, 0.0f);
   const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
   return df_make(hi, float_of(sign | ((uint32_t)lf << 23) | (man & 0x7fffffu)));
+}
+
+// Positive normal double -> df64 in a few operations: hi is the
+// truncated float, lo the remaining 29 significand bits rounded to float.
+// Valid for 2^-74 <= u < 2^127 (lo stays a normal float); relative error
+// below 2^-48.  Film heights lie far inside that range.
+TF_HD df64 df_of_pos_f64_fast(double d) {
+  const uint64_t b = bits_of(d);
+  const float hi = f32_of_pos_f64_fast(d);
+  const uint32_t r = (uint32_t)b & 0x1fffffffu;
+  if (r == 0) return df_make(hi, 0.0f);
+  const int e = (int)((b >> 52) & 0x7ff);
+#ifdef __CUDA_ARCH__
+  const float rf = __uint2float_rn(r);
+#else
+  const float rf = (float)r;
+#endif
+  return df_make(hi, float_of(bits_of(rf) - (uint32_t)((1075 - e) << 23)));
 }
 
 // u + v rounded to double (round half away from zero) with integer

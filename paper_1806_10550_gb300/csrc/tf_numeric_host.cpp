@@ -24,6 +24,14 @@ void tfh_df_ops(const double* a, const double* b, double* sum, double* prod, dou
     rcp[i] = tf::f64_of_df(tf::df_rcp(x));
   }
 }
+void tfh_fast_conv(const double* x, float* f, float* hi, float* lo, long n) {
+  for (long i = 0; i < n; ++i) {
+    f[i] = tf::f32_of_pos_f64_fast(x[i]);
+    tf::df64 d = tf::df_of_pos_f64_fast(x[i]);
+    hi[i] = d.hi;
+    lo[i] = d.lo;
+  }
+}
 void tfh_fixed36(const double* u, long long* q, long n) {
   for (long i = 0; i < n; ++i) q[i] = (long long)tf::fixed36_of_f64(u[i]);
 }

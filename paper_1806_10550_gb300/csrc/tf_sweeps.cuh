@@ -34,6 +34,12 @@ constexpr int kChunk = 32;  // cells per staged chunk along a line
 // ---------------------------------------------------------------------------
 // residual -> right side of the x solve
 
+// Film height in HP for the residual (heights are positive and normal;
+// anything else fails the step in the y sweep).
+template <class HP> __device__ __forceinline__ HP film_hp(double u);
+template <> __device__ __forceinline__ double film_hp<double>(double u) { return u; }
+template <> __device__ __forceinline__ df64 film_hp<df64>(double u) { return df_of_pos_f64_fast(u); }
+
 template <class HP, int T> struct RhsSmem {
   HP u[T + 4][T + 4];
   HP lap[T + 2][T + 2], f0[T + 2][T + 2], f1[T + 2][T + 2];
@@ -56,7 +62,7 @@ __global__ void __launch_bounds__(256)
   for (int k = tid; k < (T + 4) * (T + 4); k += NT) {
     int r = k / (T + 4), c = k - r * (T + 4);
     int gj = reflect_index(j0 - 2 + r, M.ny), gi = reflect_index(x0 - 2 + c, M.nx);
-    S.u[r][c] = from_f64<HP>(__ldg(u + (size_t)gj * M.nx + gi));
+    S.u[r][c] = film_hp<HP>(__ldg(u + (size_t)gj * M.nx + gi));
   }
   __syncthreads();
   for (int k = tid; k < (T + 2) * (T + 2); k += NT) {

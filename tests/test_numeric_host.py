@@ -93,3 +93,17 @@ def test_fixed_point_mass(lib):
     lib.tfh_fixed36(_p(u), _p(q), C.c_long(u.size))
     assert list(q[:4]) == [0, 2 ** 36, 2 ** 35, 13 * 2 ** 34]
     assert q[4] == round(1e-12 * 2 ** 36) and q[5] == 100 * 2 ** 36 and q[6] == 0
+
+
+def test_fast_positive_conversions(lib):
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.uniform(1e-3, 50, 20000), 10.0 ** rng.uniform(-22, 38, 5000),
+                        [1.0, 0.5, 2.0, 1.0 + 2.0 ** -52]])
+    f, hi, lo = (np.empty(x.size, np.float32) for _ in range(3))
+    lib.tfh_fast_conv(_p(x), _p(f), _p(hi), _p(lo), C.c_long(x.size))
+    ref = np.empty(x.size, np.float32)
+    lib.tfh_f32_trunc_of_f64(_p(x), _p(ref), C.c_long(x.size))
+    assert np.array_equal(f, ref)  # same truncation as the general routine
+    assert np.array_equal(hi, ref)
+    rec = hi.astype(np.float64) + lo.astype(np.float64)
+    assert np.all(np.abs(rec - x) <= 2.0 ** -48 * x)
