@@ -129,22 +129,27 @@ def barrier(dist):
         dist.barrier()
 
 
-def max_over_ranks(dist, x: float) -> float:
+def _reduce(dist, x: float, op) -> float:
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(dist, x: float) -> float:
+    return _reduce(dist, x, dist.ReduceOp.MAX) if dist is not None else x
 
 
 def sum_over_ranks(dist, x: float) -> float:
-    if dist is None:
-        return x
-    import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(dist, x, dist.ReduceOp.SUM) if dist is not None else x
+
+
+def job_rate(dist, local_units: float, local_ms: float) -> float:
+    """Whole-job throughput: units of all ranks / the slowest rank's time."""
+    return sum_over_ranks(dist, local_units) / (max_over_ranks(dist, local_ms) * 1e-3)
 
 
 def run_mode(tf, torch, w, h0, mode, warmup, steps, dist, replay=None, e2e_steps=0, clocks=None):
@@ -161,6 +166,7 @@ def run_mode(tf, torch, w, h0, mode, warmup, steps, dist, replay=None, e2e_steps
                                       dt_replay=replay[:warmup])
         t0 = info_w["t"]
         dt = 1.0
+    h_start = h.clone()  # the e2e pass repeats the timed steps from here
     tf.tf_timing_enable(ctx, True)
     barrier(dist)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -186,10 +192,11 @@ def run_mode(tf, torch, w, h0, mode, warmup, steps, dist, replay=None, e2e_steps
     out = dict(ms=ms, wall_s=wall, info=info, records=recs, timing=timing,
                warm_records=rec_w, final_mass=float(h.sum().item()))
     if e2e_steps > 0:
-        # End to end through the public C-ABI call with host buffers: each
+        # End to end through the public C-ABI call with host buffers: the
+        # same accepted steps as the timed region, from the same film; each
         # step copies the film from pinned host memory, steps it, and copies
         # the new film back.
-        hh = torch.from_numpy(h.cpu().numpy()).pin_memory()
+        hh = h_start.cpu().pin_memory()
         hd = torch.empty_like(h)
         hn = torch.empty_like(h)
         out_h = torch.empty_like(hh).pin_memory()
@@ -233,15 +240,24 @@ def kernel_table(res, N, lp):
     }
 
 
-def roofline_hbm(res, N, lp_bytes, pk):
+# DRAM bytes (read + write) per cell per launch of each FP32-bulk kernel,
+# from the ncu capture summarised in profiles/iteration_kernels_f32b_prof4k.md
+# (4096^2; traffic scales with the cells).  Valid for the kernels as
+# captured; set an entry to None when that kernel changes.
+TRAFFIC_PER_CELL_F32B = {"rhs": 19.2, "x_sweep": 36.0, "y_sweep": 47.2}
+
+
+def roofline_hbm(res, N, lp_bytes, pk, traffic_per_cell=None):
     """Dominant kernel (largest total time): achieved algorithmic GB/s."""
     tab = kernel_table(res, N, lp_bytes)
     name = max(tab, key=lambda k: tab[k][1])
     n, ms, b = tab[name]
     per = ms / max(1, n)
     ach = b / (per * 1e-3) / 1e9
+    tpc = (traffic_per_cell or {}).get(name)
+    traffic = None if tpc is None else round(tpc * N * N)
     return dict(bound="hbm", kernel=name, achieved=round(ach, 1), peak=pk["hbm_gbs"],
-                unit="GB/s", frac=round(ach / pk["hbm_gbs"], 4), traffic=None,
+                unit="GB/s", frac=round(ach / pk["hbm_gbs"], 4), traffic=traffic,
                 ms_per_launch=round(per, 4), algorithmic_bytes_per_launch=b,
                 peak_source=pk["source"])
 
@@ -305,7 +321,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale8k")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="steps of the end-to-end pass (default: all timed steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--modes", default="fp64,f32b")
     args = ap.parse_args()
@@ -317,6 +334,8 @@ def main():
     import paper_1806_10550_gb300 as tf
     from paper_1806_10550_gb300 import synthetic as S
     rank, world, local, dist = dist_setup()
+    if args.e2e_steps < 0:
+        args.e2e_steps = args.steps
     tf.library(build_if_missing=True)
     N = w["N"]
     h0 = S.spinodal_film(N, N, w["h0"], w["eps"], w["seed"])
@@ -359,7 +378,7 @@ def main():
         accepted_steps=acc_local, attempts=R["info"]["attempts"],
         newton_iterations=R["info"]["newton_iterations"],
         cell_iterations_per_s=N * N * R["info"]["newton_iterations"] * world / (R["ms"] * 1e-3),
-        roofline=roofline_hbm(R, N, lp, pk),
+        roofline=roofline_hbm(R, N, lp, pk, TRAFFIC_PER_CELL_F32B if head == "f32b" else None),
         gpu_launches=R["timing"]["launches"],
         kernel_ms=dict(explicit=R["timing"]["explicit_ms"], rhs=R["timing"]["rhs_ms"],
                        x_sweep=R["timing"]["x_ms"], y_sweep=R["timing"]["y_ms"]),

@@ -83,6 +83,20 @@ int explicit_timed(tf_ctx& c, const double* h_old, double dt) {
   return TF_OK;
 }
 
+// Mass and min h of a film (once per step), into s->mass and s->hmin.
+int film_stats(tf_ctx& c, const double* h, Scalars* s) {
+  tf::k_grid_stats<<<c.grid_stats, 256, 0, c.stream>>>(h, c.N, c.py);
+  TF_CK(cudaGetLastError());
+  if (c.timing.enabled) c.timing.launches += 2;
+  tf::k_finalize<<<1, 256, 0, c.stream>>>(c.px, 0, c.py, c.grid_stats, c.dsc);
+  TF_CK(cudaGetLastError());
+  TF_CK(cudaMemcpyAsync(c.hsc, c.dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
+  TF_CK(cudaStreamSynchronize(c.stream));
+  s->mass = c.hsc->mass;
+  s->hmin = c.hsc->hmin;
+  return TF_OK;
+}
+
 // Outcome of an iteration, in the oracle's order: pivot, positivity, test.
 int classify(const tf_ctx& c, const Scalars& s, int it, int fixed_iter) {
   if (s.pivot) return TF_STEP_ZERO_PIVOT;
@@ -124,7 +138,8 @@ int step(tf_ctx& c, const double* h_old, double* h_new, double dt, int fixed_ite
   }
   if (uk != h_new)
     TF_CK(cudaMemcpyAsync(h_new, uk, c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-  TF_CK(cudaStreamSynchronize(c.stream));
+  int rs = film_stats(c, h_new, &s);
+  if (rs) return rs;
   fill_info(info, status, it, s);
   return status;
 }
@@ -310,6 +325,8 @@ int tf_newton_iteration(tf_ctx* c, const double* h_k, const double* h_old, doubl
   int r = iterate(*c, h_k, dt, h_next, w, v, &s);
   if (r) return r;
   int status = classify(*c, s, 1, 0);
+  r = film_stats(*c, h_next, &s);
+  if (r) return r;
   fill_info(info, status, 1, s);
   return TF_OK;
 }

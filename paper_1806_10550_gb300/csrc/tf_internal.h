@@ -6,7 +6,7 @@
 #include <stddef.h>
 
 #include "../../include/tf.h"
-#include "tf_sweeps3.cuh"
+#include "tf_line_sweeps.cuh"
 
 namespace tf {
 

@@ -19,9 +19,8 @@
 //            DirectionSplit); J_y likewise.
 //   (I + theta dt J_x) w = -G on rows, (I + theta dt J_y) v = w on columns,
 //   u_{k+1} = u_k + v                                (eqs. JacobianSystem1-3)
-// Pentadiagonal systems are solved by LU without pivoting (eq.
-// LUFactorization), one thread per line; factors go to global scratch
-// between the forward and the backward sweep.
+// The line solves themselves live in tf_sweeps.cuh (residual kernel and
+// shared line machinery) and tf_line_sweeps.cuh (the x and y sweeps).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -124,6 +123,7 @@ template <class T> struct MobC {
   T C, A1, B1, c0, c1, three, half;
   T dA1, dB1;  // (m-2) A1 and (n-2) B1
   int model, n, m;
+  bool unitC;  // C == 1
 };
 template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
   MobC<T> c;
@@ -139,6 +139,7 @@ template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
   c.model = M.model;
   c.n = M.n;
   c.m = M.m;
+  c.unitC = M.C == 1.0;
   return c;
 }
 
@@ -151,7 +152,7 @@ TF_HD void mobility(const MobC<T>& c, const T& h, const T& s, T& f0, T& f1) {
     f1 = c.c1;
     return;
   }
-  f0 = c.C * (h * h) * h;
+  f0 = c.unitC ? (h * h) * h : c.C * (h * h) * h;
   if (c.n == 3 && c.m == 2) {  // f1 = A1 - B1 / h
     f1 = c.A1 - c.B1 * s;
     return;
@@ -371,281 +372,17 @@ __device__ __forceinline__ void band_row(const LP L[4], const LP R[4], LP& a, LP
 }
 
 // ---------------------------------------------------------------------------
-// x pass: residual, J_x assembly and row solves.  One block = 32 rows, one
-// thread per row; the row is walked in chunks of TC columns staged through
-// shared memory.  Output: w (LP).  fac: LP scratch of
-// 3 * gridDim.x * nchunks * 32 * TC.
-
-template <class HP, class LP, int TC> struct PassXSmem {
-  StencilSmem<HP, 32, TC> st;
-  LP rhs[32][TC + 1];
-  LP fac[3][32][TC + 1];
-};
-
-template <class Mode, int TC>
-__global__ void __launch_bounds__(32)
-    k_pass_x(ModelK M, StepK K, const double* __restrict__ u, const typename Mode::HP* __restrict__ bn,
-             typename Mode::LP* __restrict__ w, typename Mode::LP* __restrict__ fac,
-             PartX* __restrict__ part) {
-  typedef typename Mode::HP HP;
-  typedef typename Mode::LP LP;
-  constexpr int TR = 32;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PassXSmem<HP, LP, TC>& S = *reinterpret_cast<PassXSmem<HP, LP, TC>*>(smem_raw);
-  const int tid = threadIdx.x;
-  const int j0 = blockIdx.x * TR;
-  const int row = j0 + tid;
-  const bool active = row < M.ny;
-  const int nchunk = (M.nx + TC - 1) / TC;
-  const MobC<HP> mc = mob_consts<HP>(M);
-  const MobC<LP> ml = mob_consts<LP>(M);
-  const HP inv_ds2 = from_f64<HP>(M.inv_ds2);
-  const HP gscale = from_f64<HP>(0.5 * M.inv_ds2 * K.theta_dt);
-  const LP inv_ds = (LP)M.inv_ds, inv_ds3 = (LP)M.inv_ds3, sc = (LP)(K.theta_dt * M.inv_ds);
-  LP* facblk = fac + (size_t)blockIdx.x * nchunk * 3 * TR * TC;
-
-  double gmax = 0.0;
-  int pivot_bad = 0;
-  LUState<LP> lu;
-  lu.reset();
-  LP Lf[4] = {LP(0), LP(0), LP(0), LP(0)};
-  CellLP<LP> P;
-
-  for (int q = 0; q < nchunk; ++q) {
-    const int x0 = q * TC;
-    stencil_load(S.st, u, M, j0, x0, tid, 32);
-    __syncthreads();
-    stencil_cells(S.st, mc, inv_ds2, tid, 32);
-    __syncthreads();
-    stencil_faces(S.st, M, j0, x0, tid, 32);
-    __syncthreads();
-    for (int k = tid; k < TR * TC; k += 32) {
-      int r = k / TC, c = k - r * TC;
-      int gj = j0 + r, gi = x0 + c;
-      LP rv = LP(0);
-      if (gj < M.ny && gi < M.nx) {
-        HP Gv = (S.st.u[r + 2][c + 2] - bn[(size_t)gj * M.nx + gi]) + gscale * stencil_dprime(S.st, r, c);
-        rv = -to_lp<LP, HP>(Gv);
-        double ag = fabs(to_f64(Gv));
-        if (!(ag <= gmax)) gmax = ag;
-      }
-      S.rhs[r][c] = rv;
-    }
-    __syncthreads();
-    // sequential sweep of this thread's row over the chunk
-    if (active) {
-      auto cell = [&](int c) {  // region col of cell x0 + c is c + 1
-        CellLP<LP> X;
-        int rr = tid + 1, cc = c + 1;
-        X.u = to_lp<LP, HP>(S.st.u[rr + 1][cc + 1]);
-        X.lap = to_lp<LP, HP>(S.st.lap[rr][cc]);
-        X.f0 = to_lp<LP, HP>(S.st.f0[rr][cc]);
-        X.f1 = to_lp<LP, HP>(S.st.f1[rr][cc]);
-        LP s = to_lp<LP, HP>(S.st.s[rr][cc]);
-        mobility_d(ml, X.u, s, X.d0, X.d1);
-        return X;
-      };
-      if (q == 0) P = cell(0);
-      for (int c = 0; c < TC; ++c) {
-        const int i = x0 + c;
-        if (i >= M.nx) break;
-        LP Rf[4] = {LP(0), LP(0), LP(0), LP(0)};
-        CellLP<LP> Q;
-        if (i + 1 < M.nx) {
-          Q = cell(c + 1);
-          face_dF(P, Q, i > 0, i + 2 < M.nx, inv_ds, inv_ds3, sc, Rf);
-        }
-        LP a, b, cc, d, e, g, dl, z;
-        band_row(Lf, Rf, a, b, cc, d, e);
-        if (!lu.step(a, b, cc, d, e, S.rhs[tid][c], g, dl, z)) pivot_bad = 1;
-        S.fac[0][tid][c] = g;
-        S.fac[1][tid][c] = dl;
-        S.fac[2][tid][c] = z;
-        for (int t = 0; t < 4; ++t) Lf[t] = Rf[t];
-        P = Q;
-      }
-    }
-    __syncthreads();
-    LP* fq = facblk + (size_t)q * 3 * TR * TC;
-    for (int k = tid; k < 3 * TR * TC; k += 32) {
-      int f = k / (TR * TC), rem = k - f * TR * TC, r = rem / TC, c = rem - r * TC;
-      fq[k] = S.fac[f][r][c];
-    }
-    __syncthreads();
-  }
-  // backward sweep
-  LP x1 = LP(0), x2 = LP(0);
-  for (int q = nchunk - 1; q >= 0; --q) {
-    const int x0 = q * TC;
-    const LP* fq = facblk + (size_t)q * 3 * TR * TC;
-    for (int k = tid; k < 3 * TR * TC; k += 32) {
-      int f = k / (TR * TC), rem = k - f * TR * TC, r = rem / TC, c = rem - r * TC;
-      S.fac[f][r][c] = fq[k];
-    }
-    __syncthreads();
-    if (active) {
-      for (int c = TC - 1; c >= 0; --c) {
-        if (x0 + c >= M.nx) continue;
-        LP x = S.fac[2][tid][c] - S.fac[0][tid][c] * x1 - S.fac[1][tid][c] * x2;
-        S.rhs[tid][c] = x;
-        x2 = x1;
-        x1 = x;
-      }
-    }
-    __syncthreads();
-    for (int k = tid; k < TR * TC; k += 32) {
-      int r = k / TC, c = k - r * TC;
-      int gj = j0 + r, gi = x0 + c;
-      if (gj < M.ny && gi < M.nx) w[(size_t)gj * M.nx + gi] = S.rhs[r][c];
-    }
-    __syncthreads();
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-    pivot_bad |= __shfl_xor_sync(0xffffffffu, pivot_bad, o);
-  }
-  if (tid == 0) {
-    part[blockIdx.x].gnorm = gmax;
-    part[blockIdx.x].pivot = pivot_bad;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// y pass: J_y assembly, column solves, update and reductions.  One block =
-// 32 columns, one thread per column; rows walked in chunks of RY staged in
-// shared memory (u in LP with a two-cell halo).  fac: LP scratch 3 * nx*ny.
-
-template <class LP, int RY> struct PassYSmem {
-  LP u[RY + 4][34];  // rows y0-2.., cols i0-1..i0+32
-};
-
-template <class Mode> __device__ __forceinline__ double update_u(double uk, double v);
-template <> __device__ __forceinline__ double update_u<ModeFP64>(double uk, double v) { return uk + v; }
-template <class Mode> __device__ __forceinline__ double update_uf(double uk, float v);
-template <> __device__ __forceinline__ double update_uf<ModeF32B>(double uk, float v) {
-  return f64_add_f32(uk, v);
-}
+// per-cell helpers of the update and the Newton test
 
 __device__ __forceinline__ double rel_update(double v, double uk) { return fabs(v / uk); }
 __device__ __forceinline__ float rel_update(float v, double uk) {
-  return __fdividef(fabsf(v), fabsf(f32_trunc_of_f64(uk)));
+  return __fdividef(fabsf(v), f32_of_pos_f64_fast(uk));  // uk > 0 or the step fails anyway
 }
 // Order-preserving integer key of a non-negative double (bit pattern);
 // negative values, zero, NaN and infinities are reported separately.
 __device__ __forceinline__ bool positive_finite_bits(double u) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(u);
   return (b >> 63) == 0 && b != 0ull && ((b >> 52) & 0x7ff) != 0x7ff;
-}
-
-template <class Mode, int RY>
-__global__ void __launch_bounds__(32)
-    k_pass_y(ModelK M, StepK K, const double* __restrict__ u, const typename Mode::LP* __restrict__ w,
-             typename Mode::LP* __restrict__ fac, double* __restrict__ unew, double* __restrict__ vout,
-             PartY* __restrict__ part) {
-  typedef typename Mode::LP LP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PassYSmem<LP, RY>& S = *reinterpret_cast<PassYSmem<LP, RY>*>(smem_raw);
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * 32;
-  const int col = i0 + tid;
-  const bool active = col < M.nx;
-  const size_t N = (size_t)M.nx * M.ny;
-  const MobC<LP> ml = mob_consts<LP>(M);
-  const LP inv_ds = (LP)M.inv_ds, inv_ds2 = (LP)M.inv_ds2, inv_ds3 = (LP)M.inv_ds3;
-  const LP sc = (LP)(K.theta_dt * M.inv_ds);
-  LP* fg = fac;
-  LP* fd = fac + N;
-  LP* fz = fac + 2 * N;
-  int pivot_bad = 0;
-  LUState<LP> lu;
-  lu.reset();
-  LP Lf[4] = {LP(0), LP(0), LP(0), LP(0)};
-  CellLP<LP> P;
-  for (int y0 = 0; y0 < M.ny; y0 += RY) {
-    for (int k = tid; k < (RY + 4) * 34; k += 32) {
-      int r = k / 34, c = k - r * 34;
-      int gj = reflect_index(y0 - 2 + r, M.ny), gi = reflect_index(i0 - 1 + c, M.nx);
-      S.u[r][c] = from_f64<LP>(__ldg(u + (size_t)gj * M.nx + gi));
-    }
-    __syncthreads();
-    if (active) {
-      auto cell = [&](int r) {  // cell (col, y0 + r) sits at S.u[r + 2][tid + 1]
-        CellLP<LP> X;
-        int rr = r + 2, cc = tid + 1;
-        LP uc = S.u[rr][cc];
-        X.u = uc;
-        X.lap = (((S.u[rr][cc + 1] - uc) + (S.u[rr][cc - 1] - uc)) +
-                 ((S.u[rr + 1][cc] - uc) + (S.u[rr - 1][cc] - uc))) * inv_ds2;
-        LP s = rcp(uc);
-        mobility(ml, uc, s, X.f0, X.f1);
-        mobility_d(ml, uc, s, X.d0, X.d1);
-        return X;
-      };
-      if (y0 == 0) P = cell(0);
-      for (int r = 0; r < RY; ++r) {
-        const int j = y0 + r;
-        if (j >= M.ny) break;
-        LP Rf[4] = {LP(0), LP(0), LP(0), LP(0)};
-        CellLP<LP> Q;
-        if (j + 1 < M.ny) {
-          Q = cell(r + 1);
-          face_dF(P, Q, j > 0, j + 2 < M.ny, inv_ds, inv_ds3, sc, Rf);
-        }
-        LP a, b, c, d, e, g, dl, z;
-        band_row(Lf, Rf, a, b, c, d, e);
-        const size_t idx = (size_t)j * M.nx + col;
-        if (!lu.step(a, b, c, d, e, w[idx], g, dl, z)) pivot_bad = 1;
-        fg[idx] = g;
-        fd[idx] = dl;
-        fz[idx] = z;
-        for (int t = 0; t < 4; ++t) Lf[t] = Rf[t];
-        P = Q;
-      }
-    }
-    __syncthreads();
-  }
-  double err = 0.0, hmin = INFINITY;
-  long long mass = 0;
-  int nonfinite = 0;
-  if (active) {
-    LP x1 = LP(0), x2 = LP(0);
-    for (int j = M.ny - 1; j >= 0; --j) {
-      const size_t idx = (size_t)j * M.nx + col;
-      LP x = fz[idx] - fg[idx] * x1 - fd[idx] * x2;
-      x2 = x1;
-      x1 = x;
-      const double uk = u[idx];
-      double un;
-      if constexpr (sizeof(LP) == 8)
-        un = update_u<Mode>(uk, (double)x);
-      else
-        un = update_uf<Mode>(uk, (float)x);
-      unew[idx] = un;
-      if (vout) vout[idx] = to_f64(x);
-      double ru = rel_update(x, uk);
-      if (!(ru <= err)) err = ru;
-      if (!(un > 0.0) || !isfinite(un)) nonfinite = 1;
-      hmin = fmin(hmin, un);
-      mass += fixed36_of_f64(un);
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    double e2 = __shfl_xor_sync(0xffffffffu, err, o);
-    if (!(e2 <= err)) err = e2;
-    hmin = fmin(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
-    mass += __shfl_xor_sync(0xffffffffu, mass, o);
-    nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, o);
-    pivot_bad |= __shfl_xor_sync(0xffffffffu, pivot_bad, o);
-  }
-  if (tid == 0) {
-    PartY p;
-    p.err = err;
-    p.hmin = hmin;
-    p.mass = mass;
-    p.nonfinite = nonfinite;
-    p.pivot = pivot_bad;
-    part[blockIdx.x] = p;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -703,41 +440,44 @@ static __global__ void __launch_bounds__(256)
 // Mass and minimum of a grid (for tf_residual's norms).
 static __global__ void __launch_bounds__(256)
     k_grid_stats(const double* __restrict__ u, size_t N, PartY* __restrict__ part) {
-  double h = INFINITY;
+  // min over positive values through their bit patterns (integer compares)
+  unsigned long long hb = 0x7ff0000000000000ull;
   long long m = 0;
   int nf = 0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-    double v = u[k];
-    h = fmin(h, v);
+    const double v = u[k];
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if (!positive_finite_bits(v)) nf = 1;
+    else if (b < hb) hb = b;
     m += fixed36_of_f64(v);
-    if (!(v > 0.0) || !isfinite(v)) nf = 1;
   }
   for (int o = 16; o > 0; o >>= 1) {
-    h = fmin(h, __shfl_xor_sync(0xffffffffu, h, o));
+    unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hb, o);
+    if (h2 < hb) hb = h2;
     m += __shfl_xor_sync(0xffffffffu, m, o);
     nf |= __shfl_xor_sync(0xffffffffu, nf, o);
   }
-  __shared__ double sh[8];
+  __shared__ unsigned long long sh[8];
   __shared__ long long sm[8];
   __shared__ int sn[8];
   if ((threadIdx.x & 31) == 0) {
-    sh[threadIdx.x >> 5] = h;
+    sh[threadIdx.x >> 5] = hb;
     sm[threadIdx.x >> 5] = m;
     sn[threadIdx.x >> 5] = nf;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double hb = sh[0];
+    unsigned long long hbb = sh[0];
     long long mb = sm[0];
     int nb = sn[0];
     for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
-      hb = fmin(hb, sh[k]);
+      if (sh[k] < hbb) hbb = sh[k];
       mb += sm[k];
       nb |= sn[k];
     }
     PartY p;
     p.err = 0.0;
-    p.hmin = hb;
+    p.hmin = __longlong_as_double((long long)hbb);
     p.mass = mb;
     p.nonfinite = nb;
     p.pivot = 0;

@@ -1,4 +1,4 @@
-// tf_sweeps3.cuh -- warp-specialised line sweeps.
+// tf_line_sweeps.cuh -- warp-specialised line sweeps.
 //
 // The exact twisted LU solve of every line (see tf_sweeps.cuh) has a short
 // sequential recurrence per cell; everything else per cell (the film values,
@@ -19,7 +19,7 @@ namespace tf {
 constexpr int kRY = 12;      // rows per chunk of the y sweep
 constexpr int kCX = 12;      // columns per chunk of the x sweep
 constexpr int kProd = 8;     // producer warps per block
-constexpr int kThreads3 = 32 * (2 + kProd);
+constexpr int kSweepThreads = 32 * (2 + kProd);
 
 // Band of line cell j from its two faces (natural orientation):
 // a..e multiply x_{j-2}..x_{j+2}.
@@ -117,36 +117,36 @@ __device__ __forceinline__ void band_group(const CellBuf<LP, L>& cb, int line, i
 // halves; warps 2..5 produce.  Producer thread p: half = p >> 6,
 // col = p & 31, row group = (p >> 5) & 1 (8 rows of a 16-row chunk).
 
-template <class LP> struct Y3Fwd {
+template <class LP> struct YFwd {
   double ut[2][2][kRY + 4][34];  // raw film tiles (rows r0-2.., cols i0-1..)
   LP wt[2][2][kRY][32];          // right sides w
   LP lt[2][kRY + 4][35];         // film tile in LP (current producer chunk)
   LP band[2][2][6][kRY][32];     // [stage][half][a..e, r][row][col]
   CellBuf<LP, kRY> cb[2];        // film values of the chunk's cells
 };
-template <class LP> struct Y3Bwd {
+template <class LP> struct YBwd {
   LP ft[3][2][3][kRY][32];       // factor tiles
   double ukt[3][2][kRY][32];     // u_k tiles for the update
   LP xb[2][2][kRY][32];          // solved corrections
 };
-template <class LP> struct Y3Smem {
+template <class LP> struct YSmem {
   union {
-    Y3Fwd<LP> f;
-    Y3Bwd<LP> b;
+    YFwd<LP> f;
+    YBwd<LP> b;
   } s;
   LUState<LP> seamS[32], seamR[32];
   LP xs[32][4];
-  PartY part[kThreads3 / 32];
+  PartY part[kSweepThreads / 32];
 };
 
 template <class Mode>
-__global__ void __launch_bounds__(kThreads3)
-    k_ysweep3(ModelK M, StepK K, const double* __restrict__ u, const typename Mode::LP* __restrict__ w,
+__global__ void __launch_bounds__(kSweepThreads)
+    k_ysweep(ModelK M, StepK K, const double* __restrict__ u, const typename Mode::LP* __restrict__ w,
               typename Mode::LP* __restrict__ fac, double* __restrict__ unew,
               double* __restrict__ vout, PartY* __restrict__ part) {
   typedef typename Mode::LP LP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Y3Smem<LP>& S = *reinterpret_cast<Y3Smem<LP>*>(smem_raw);
+  YSmem<LP>& S = *reinterpret_cast<YSmem<LP>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool solver = warp < 2;
   const int p = threadIdx.x - 64;  // producer index (valid when !solver)
@@ -315,9 +315,9 @@ __global__ void __launch_bounds__(kThreads3)
       x2 = S.xs[lane][0];
     }
   }
+  // per-iteration reductions: the Newton test and positivity (mass and min h
+  // of the accepted film are reduced once per step by k_grid_stats)
   LP err = LP(0);
-  unsigned long long hmin_bits = 0x7ff0000000000000ull;
-  long long mass = 0;
   int nonfinite = 0;
   // cp.async groups: before the ticks {f0, u0} and {f1}; tick t issues
   // {f(t+2), u(t+1)} and then waits for everything older, so the solvers
@@ -389,9 +389,6 @@ __global__ void __launch_bounds__(kThreads3)
             LP ru = rel_update(x, uk);
             if (!(ru <= err)) err = ru;
             if (!positive_finite_bits(un)) nonfinite = 1;
-            const unsigned long long ub = (unsigned long long)__double_as_longlong(un);
-            if (!(ub >> 63) && ub < hmin_bits) hmin_bits = ub;
-            mass += fixed36_of_f64(un);
           }
         }
       }
@@ -407,17 +404,14 @@ __global__ void __launch_bounds__(kThreads3)
   for (int o = 16; o > 0; o >>= 1) {
     LP e2 = __shfl_xor_sync(0xffffffffu, err, o);
     if (!(e2 <= err)) err = e2;
-    unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hmin_bits, o);
-    if (h2 < hmin_bits) hmin_bits = h2;
-    mass += __shfl_xor_sync(0xffffffffu, mass, o);
     nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, o);
     pivot_bad |= __shfl_xor_sync(0xffffffffu, pivot_bad, o);
   }
   if (lane == 0) {
     PartY pp;
     pp.err = (double)err;
-    pp.hmin = __longlong_as_double((long long)hmin_bits);
-    pp.mass = mass;
+    pp.hmin = INFINITY;
+    pp.mass = 0;
     pp.nonfinite = nonfinite;
     pp.pivot = pivot_bad;
     S.part[warp] = pp;
@@ -425,7 +419,7 @@ __global__ void __launch_bounds__(kThreads3)
   __syncthreads();
   if (threadIdx.x == 0) {
     PartY a = S.part[0];
-    for (int k = 1; k < kThreads3 / 32; ++k) {
+    for (int k = 1; k < kSweepThreads / 32; ++k) {
       const PartY& b = S.part[k];
       if (!(b.err <= a.err)) a.err = b.err;
       if (b.hmin < a.hmin) a.hmin = b.hmin;
@@ -443,34 +437,34 @@ __global__ void __launch_bounds__(kThreads3)
 // half = p >> 6, row = p & 31, column group = (p >> 5) & 1 (8 columns of a
 // 16-column chunk).  Factor scratch per block: fac[((blk*3 + f)*nx + col)*32 + row].
 
-template <class LP> struct X3Fwd {
+template <class LP> struct XFwd {
   double ut[2][2][34][kCX + 4];  // raw film tiles (rows j0-1.., cols c0-2..)
   LP rt[2][2][32][kCX + 1];      // right sides
   LP lt[2][34][kCX + 5];         // film tile in LP
   LP band[2][2][6][kCX][32];     // [stage][half][a..e, r][col][row]
   CellBuf<LP, kCX> cb[2];        // film values of the chunk's cells
 };
-template <class LP> struct X3Bwd {
+template <class LP> struct XBwd {
   LP ft[3][2][3][kCX][32];       // factor tiles [f][col][row]
   LP xb[2][2][kCX][33];          // solved w [col][row]
 };
-template <class LP> struct X3Smem {
+template <class LP> struct XSmem {
   union {
-    X3Fwd<LP> f;
-    X3Bwd<LP> b;
+    XFwd<LP> f;
+    XBwd<LP> b;
   } s;
   LUState<LP> seamS[32], seamR[32];
   LP xs[32][4];
-  int piv[kThreads3 / 32];
+  int piv[kSweepThreads / 32];
 };
 
 template <class Mode>
-__global__ void __launch_bounds__(kThreads3)
-    k_xsweep3(ModelK M, StepK K, const double* __restrict__ u, typename Mode::LP* __restrict__ rw,
+__global__ void __launch_bounds__(kSweepThreads)
+    k_xsweep(ModelK M, StepK K, const double* __restrict__ u, typename Mode::LP* __restrict__ rw,
               typename Mode::LP* __restrict__ fac, PartX* __restrict__ part) {
   typedef typename Mode::LP LP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  X3Smem<LP>& S = *reinterpret_cast<X3Smem<LP>*>(smem_raw);
+  XSmem<LP>& S = *reinterpret_cast<XSmem<LP>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool solver = warp < 2;
   const int p = threadIdx.x - 64;
@@ -678,7 +672,7 @@ __global__ void __launch_bounds__(kThreads3)
   __syncthreads();
   if (threadIdx.x == 0) {
     int a = 0;
-    for (int k = 0; k < kThreads3 / 32; ++k) a |= S.piv[k];
+    for (int k = 0; k < kSweepThreads / 32; ++k) a |= S.piv[k];
     PartX pp;
     pp.gnorm = 0.0;
     pp.pivot = a;

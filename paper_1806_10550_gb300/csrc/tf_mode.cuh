@@ -11,8 +11,8 @@ template <class Mode> struct Launch {
   typedef typename Mode::LP LP;
   static constexpr size_t smem_stencil = sizeof(StencilSmem<HP, 16, 16>);
   static constexpr size_t smem_rhs = sizeof(RhsSmem<HP, 32>);
-  static constexpr size_t smem_x = sizeof(X3Smem<LP>);
-  static constexpr size_t smem_y = sizeof(Y3Smem<LP>);
+  static constexpr size_t smem_x = sizeof(XSmem<LP>);
+  static constexpr size_t smem_y = sizeof(YSmem<LP>);
 
   static StepK step(const tf_ctx& c, double dt) {
     StepK k;
@@ -27,12 +27,12 @@ template <class Mode> struct Launch {
     if ((e = cudaFuncSetAttribute(k_stencil<Mode, 0>, A, (int)smem_stencil))) return e;
     if ((e = cudaFuncSetAttribute(k_stencil<Mode, 1>, A, (int)smem_stencil))) return e;
     if ((e = cudaFuncSetAttribute(k_rhs<Mode>, A, (int)smem_rhs))) return e;
-    if ((e = cudaFuncSetAttribute(k_xsweep3<Mode>, A, (int)smem_x))) return e;
-    if ((e = cudaFuncSetAttribute(k_ysweep3<Mode>, A, (int)smem_y))) return e;
+    if ((e = cudaFuncSetAttribute(k_xsweep<Mode>, A, (int)smem_x))) return e;
+    if ((e = cudaFuncSetAttribute(k_ysweep<Mode>, A, (int)smem_y))) return e;
     // the sweeps run two blocks per SM only with the largest shared carveout
     const cudaFuncAttribute C = cudaFuncAttributePreferredSharedMemoryCarveout;
-    if ((e = cudaFuncSetAttribute(k_xsweep3<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
-    if ((e = cudaFuncSetAttribute(k_ysweep3<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+    if ((e = cudaFuncSetAttribute(k_xsweep<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+    if ((e = cudaFuncSetAttribute(k_ysweep<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     return cudaFuncSetAttribute(k_rhs<Mode>, C, (int)cudaSharedmemCarveoutMaxShared);
   }
 
@@ -55,13 +55,13 @@ template <class Mode> struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t xsweep_c(tf_ctx& c, double dt, const double* u_k) {
-    k_xsweep3<Mode><<<c.grid_x, kThreads3, smem_x, c.stream>>>(c.mk, step(c, dt), u_k, (LP*)c.w,
+    k_xsweep<Mode><<<c.grid_x, kSweepThreads, smem_x, c.stream>>>(c.mk, step(c, dt), u_k, (LP*)c.w,
                                                        (LP*)c.fac_x, c.px + c.grid_rx * c.grid_ry);
     return cudaGetLastError();
   }
   static cudaError_t ysweep_c(tf_ctx& c, const double* u_k, double dt, double* u_next,
                               double* v_out) {
-    k_ysweep3<Mode><<<c.grid_y, kThreads3, smem_y, c.stream>>>(c.mk, step(c, dt), u_k, (const LP*)c.w,
+    k_ysweep<Mode><<<c.grid_y, kSweepThreads, smem_y, c.stream>>>(c.mk, step(c, dt), u_k, (const LP*)c.w,
                                                        (LP*)c.fac_y, u_next, v_out, c.py);
     return cudaGetLastError();
   }

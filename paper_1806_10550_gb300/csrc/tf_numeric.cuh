@@ -166,6 +166,27 @@ TF_HD df64 operator*(df64 a, df64 b) {
   fast_two_sum(p, e, p, e);
   return df_make(p, e);
 }
+// Unnormalised ("lazy") variants for chains of operations: the result pair
+// (hi, lo) is exact to about 2^-47 of the operands but lo is not folded into
+// hi; fold with df_norm before storing or comparing.
+TF_HD df64 df_add_u(df64 a, df64 b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df_make(s, e + (a.lo + b.lo));
+}
+TF_HD df64 df_mul_u(df64 a, df64 b) {
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  e = fma_f(a.hi, b.lo, e);
+  e = fma_f(a.lo, b.hi, e);
+  return df_make(p, e);
+}
+TF_HD df64 df_norm(df64 a) {
+  float s, e;
+  fast_two_sum(a.hi, a.lo, s, e);
+  return df_make(s, e);
+}
+
 // 1/a: float reciprocal refined by one Newton step in double-float.
 TF_HD df64 df_rcp(df64 a) {
   float y = 1.0f / a.hi;
