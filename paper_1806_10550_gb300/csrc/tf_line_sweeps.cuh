@@ -16,16 +16,13 @@
 
 namespace tf {
 
-constexpr int kRY = 12;      // rows per chunk of the y sweep
+constexpr int kRY = 12;      // rows per chunk of the y sweep (4 groups of 3)
 constexpr int kCX = 12;      // columns per chunk of the x sweep
 constexpr int kProd = 8;     // producer warps per block
 constexpr int kSweepThreads = 32 * (2 + kProd);
 
 // Band of line cell j from its two faces (natural orientation):
 // a..e multiply x_{j-2}..x_{j+2}.
-template <class LP> struct Band {
-  LP a, b, c, d, e;
-};
 
 constexpr int kNP = 32 * kProd;  // producer threads
 
@@ -56,26 +53,74 @@ __device__ __forceinline__ void copy_tile_f64(double* dst, const double* __restr
   }
 }
 
-// Struct-of-arrays cell buffer: film values of the cells of one chunk plus
-// one halo cell at each end, for 32 lines: [field][cell][line].
+// Per-cell film values, pre-scaled for the band: with k3 = theta dt/(2 ds^4)
+// and k1 = theta dt/(2 ds^2),
+//   F0 = k3 f0, F1 = k1 f1, D0 = k1 f0', D1 = k1 f1',
+// so that for the face between line cells p and q (the scaled dF of
+// face_dF): c3 = F0_p + F0_q, Bd = F1_p + F1_q,
+//   t_p = D0_p (lap_q - lap_p) + D1_p (u_q - u_p), t_q likewise, and
+//   dF = (-w_p c3, (2 + w_p) c3 + t_p - Bd, -(2 + w_q) c3 + t_q + Bd, w_q c3).
+template <class LP> struct CellS {
+  LP u, lap, F0, F1, D0, D1;
+};
+
+template <class LP, class Acc>
+__device__ __forceinline__ CellS<LP> cell_scaled(const MobC<LP>& ml, LP inv_ds2, LP k3, LP k1, Acc U) {
+  CellS<LP> X;
+  const LP uc = U(0, 0);
+  X.u = uc;
+  X.lap = (((U(0, 1) - uc) + (U(0, -1) - uc)) + ((U(1, 0) - uc) + (U(-1, 0) - uc))) * inv_ds2;
+  const LP s = rcp(uc);
+  LP f0, f1, d0, d1;
+  mobility(ml, uc, s, f0, f1);
+  mobility_d(ml, uc, s, d0, d1);
+  X.F0 = k3 * f0;
+  X.F1 = k1 * f1;
+  X.D0 = k1 * d0;
+  X.D1 = k1 * d1;
+  return X;
+}
+
+template <class LP>
+__device__ __forceinline__ void face_scaled(const CellS<LP>& P, const CellS<LP>& Q, bool pl, bool qr,
+                                            LP dF[4]) {
+  const LP dl = Q.lap - P.lap, du = Q.u - P.u;
+  const LP c3 = P.F0 + Q.F0, Bd = P.F1 + Q.F1;
+  const LP tp = P.D0 * dl + P.D1 * du, tq = Q.D0 * dl + Q.D1 * du;
+  if (pl && qr) {
+    dF[0] = -c3;
+    dF[1] = LP(3) * c3 + (tp - Bd);
+    dF[2] = LP(-3) * c3 + (tq + Bd);
+    dF[3] = c3;
+  } else {
+    const LP wp = pl ? LP(1) : LP(0), wq = qr ? LP(1) : LP(0);
+    dF[0] = -wp * c3;
+    dF[1] = (LP(2) + wp) * c3 + (tp - Bd);
+    dF[2] = -(LP(2) + wq) * c3 + (tq + Bd);
+    dF[3] = wq * c3;
+  }
+}
+
+// Struct-of-arrays cell buffer: scaled film values of the cells of one chunk
+// plus one halo cell at each end, for 32 lines: [field][cell][line].
 template <class LP, int L> struct CellBuf {
   LP v[6][L + 2][32];
-  __device__ __forceinline__ void put(int cell, int line, const CellLP<LP>& X) {
+  __device__ __forceinline__ void put(int cell, int line, const CellS<LP>& X) {
     v[0][cell][line] = X.u;
     v[1][cell][line] = X.lap;
-    v[2][cell][line] = X.f0;
-    v[3][cell][line] = X.f1;
-    v[4][cell][line] = X.d0;
-    v[5][cell][line] = X.d1;
+    v[2][cell][line] = X.F0;
+    v[3][cell][line] = X.F1;
+    v[4][cell][line] = X.D0;
+    v[5][cell][line] = X.D1;
   }
-  __device__ __forceinline__ CellLP<LP> get(int cell, int line) const {
-    CellLP<LP> X;
+  __device__ __forceinline__ CellS<LP> get(int cell, int line) const {
+    CellS<LP> X;
     X.u = v[0][cell][line];
     X.lap = v[1][cell][line];
-    X.f0 = v[2][cell][line];
-    X.f1 = v[3][cell][line];
-    X.d0 = v[4][cell][line];
-    X.d1 = v[5][cell][line];
+    X.F0 = v[2][cell][line];
+    X.F1 = v[3][cell][line];
+    X.D0 = v[4][cell][line];
+    X.D1 = v[5][cell][line];
     return X;
   }
 };
@@ -85,28 +130,23 @@ template <class LP, int L> struct CellBuf {
 // with the right side r taken from R(i).
 template <class LP, int L, class RhsF>
 __device__ __forceinline__ void band_group(const CellBuf<LP, L>& cb, int line, int c0, int ia, int ib,
-                                           int n, LP inv_ds, LP inv_ds3, LP sc, LP* B, RhsF R) {
-  CellLP<LP> P = cb.get(ia - c0 + 1, line);
+                                           int n, LP* B, RhsF R) {
+  CellS<LP> P = cb.get(ia - c0 + 1, line);
   LP Lf[4] = {LP(0), LP(0), LP(0), LP(0)};
-  if (ia > 0) {
-    CellLP<LP> Pm = cb.get(ia - c0, line);
-    face_dF(Pm, P, ia - 1 > 0, ia + 1 < n, inv_ds, inv_ds3, sc, Lf);
-  }
+  if (ia > 0) face_scaled(cb.get(ia - c0, line), P, ia - 1 > 0, ia + 1 < n, Lf);
   for (int i = ia; i < ib; ++i) {
     LP Rf[4] = {LP(0), LP(0), LP(0), LP(0)};
     if (i + 1 < n) {
-      CellLP<LP> Q = cb.get(i - c0 + 2, line);
-      face_dF(P, Q, i > 0, i + 2 < n, inv_ds, inv_ds3, sc, Rf);
+      CellS<LP> Q = cb.get(i - c0 + 2, line);
+      face_scaled(P, Q, i > 0, i + 2 < n, Rf);
       P = Q;
     }
-    LP a, b, c, d, e;
-    band_row(Lf, Rf, a, b, c, d, e);
     const int k = (i - c0) * 32 + line;
-    B[0 * L * 32 + k] = a;
-    B[1 * L * 32 + k] = b;
-    B[2 * L * 32 + k] = c;
-    B[3 * L * 32 + k] = d;
-    B[4 * L * 32 + k] = e;
+    B[0 * L * 32 + k] = -Lf[0];
+    B[1 * L * 32 + k] = Rf[0] - Lf[1];
+    B[2 * L * 32 + k] = LP(1) + (Rf[1] - Lf[2]);
+    B[3 * L * 32 + k] = Rf[2] - Lf[3];
+    B[4 * L * 32 + k] = Rf[3];
     B[5 * L * 32 + k] = R(i);
     for (int q = 0; q < 4; ++q) Lf[q] = Rf[q];
   }
@@ -160,8 +200,9 @@ __global__ void __launch_bounds__(kSweepThreads)
   auto r0_of = [&](int h, int q) { return h == 0 ? q * kRY : max(m, ny - (q + 1) * kRY); };
   auto r1_of = [&](int h, int q) { return h == 0 ? min(m, (q + 1) * kRY) : ny - q * kRY; };
   const MobC<LP> ml = mob_consts<LP>(M);
-  const LP inv_ds = (LP)M.inv_ds, inv_ds2 = (LP)M.inv_ds2, inv_ds3 = (LP)M.inv_ds3;
-  const LP sc = (LP)(K.theta_dt * M.inv_ds);
+  const LP inv_ds2 = (LP)M.inv_ds2;
+  const LP k3 = (LP)(0.5 * K.theta_dt * M.inv_ds3 * M.inv_ds);
+  const LP k1 = (LP)(0.5 * K.theta_dt * M.inv_ds2);
   LP* fg = fac;
   LP* fd = fac + N;
   LP* fz = fac + 2 * N;
@@ -212,21 +253,20 @@ __global__ void __launch_bounds__(kSweepThreads)
             const int cr = k >> 5, c = k & 31;  // cell row index: global row r0 - 1 + cr
             if (r0 - 1 + cr > r1 || i0 + c >= nx) continue;
             const int rr = cr + 1, cc = c + 1;  // tile position of the cell
-            S.s.f.cb[h].put(cr, c, cell_values<LP>(ml, inv_ds2, [&](int dr, int dc) {
+            S.s.f.cb[h].put(cr, c, cell_scaled<LP>(ml, inv_ds2, k3, k1, [&](int dr, int dc) {
                               return S.s.f.lt[h][rr + dr][cc + dc];
                             }));
           }
         }
         pbar();
-        // phase B: band rows; thread p covers (half, column, 4 rows)
+        // phase B: band rows; thread p covers (half, column, 3 rows)
         {
           const int h = p >> 7, g = (p >> 5) & 3, c = p & 31;
           if (t < nchh[h] && i0 + c < nx) {
             const int r0 = r0_of(h, t), r1 = r1_of(h, t);
-            const int ja = r0 + 4 * g, jb = min(r1, ja + 4);
+            const int ja = r0 + 3 * g, jb = min(r1, ja + 3);
             if (ja < jb)
-              band_group<LP, kRY>(S.s.f.cb[h], c, r0, ja, jb, ny, inv_ds, inv_ds3, sc,
-                                  &S.s.f.band[t & 1][h][0][0][0],
+              band_group<LP, kRY>(S.s.f.cb[h], c, r0, ja, jb, ny, &S.s.f.band[t & 1][h][0][0][0],
                                   [&](int j) { return S.s.f.wt[slot][h][j - r0][c]; });
           }
         }
@@ -477,8 +517,9 @@ __global__ void __launch_bounds__(kSweepThreads)
   auto c0_of = [&](int h, int q) { return h == 0 ? q * kCX : max(m, nx - (q + 1) * kCX); };
   auto c1_of = [&](int h, int q) { return h == 0 ? min(m, (q + 1) * kCX) : nx - q * kCX; };
   const MobC<LP> ml = mob_consts<LP>(M);
-  const LP inv_ds = (LP)M.inv_ds, inv_ds2 = (LP)M.inv_ds2, inv_ds3 = (LP)M.inv_ds3;
-  const LP sc = (LP)(K.theta_dt * M.inv_ds);
+  const LP inv_ds2 = (LP)M.inv_ds2;
+  const LP k3 = (LP)(0.5 * K.theta_dt * M.inv_ds3 * M.inv_ds);
+  const LP k1 = (LP)(0.5 * K.theta_dt * M.inv_ds2);
   LP* facb = fac + (size_t)blockIdx.x * 3 * nx * 32;
   int pivot_bad = 0;
 
@@ -523,21 +564,20 @@ __global__ void __launch_bounds__(kSweepThreads)
             const int ci = k >> 5, r = k & 31;  // cell col index: global col c0 - 1 + ci
             if (c0 - 1 + ci > c1 || j0 + r >= ny) continue;
             const int rr = r + 1, cc = ci + 1;
-            S.s.f.cb[h].put(ci, r, cell_values<LP>(ml, inv_ds2, [&](int dr, int dc) {
+            S.s.f.cb[h].put(ci, r, cell_scaled<LP>(ml, inv_ds2, k3, k1, [&](int dr, int dc) {
                               return S.s.f.lt[h][rr + dr][cc + dc];
                             }));
           }
         }
         pbar();
-        // phase B: band rows; thread p covers (half, row, 4 columns)
+        // phase B: band rows; thread p covers (half, row, 3 columns)
         {
           const int h = p >> 7, g = (p >> 5) & 3, r = p & 31;
           if (t < nchh[h] && j0 + r < ny) {
             const int c0 = c0_of(h, t), c1 = c1_of(h, t);
-            const int ia = c0 + 4 * g, ib = min(c1, ia + 4);
+            const int ia = c0 + 3 * g, ib = min(c1, ia + 3);
             if (ia < ib)
-              band_group<LP, kCX>(S.s.f.cb[h], r, c0, ia, ib, nx, inv_ds, inv_ds3, sc,
-                                  &S.s.f.band[t & 1][h][0][0][0],
+              band_group<LP, kCX>(S.s.f.cb[h], r, c0, ia, ib, nx, &S.s.f.band[t & 1][h][0][0][0],
                                   [&](int i) { return S.s.f.rt[slot][h][r][i - c0]; });
           }
         }
