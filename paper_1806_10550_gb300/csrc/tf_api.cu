@@ -198,6 +198,7 @@ void tf_destroy(tf_ctx* c) {
   if (!c) return;
   cudaFree(c->bn);
   cudaFree(c->w);
+  cudaFree(c->ulp);
   cudaFree(c->fac_x);
   cudaFree(c->fac_y);
   cudaFree(c->ubuf);
@@ -276,6 +277,7 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   if (e != cudaSuccess) r = cuda_fail(e);
   if (!r) r = dalloc(&c->bn, c->N * hp);
   if (!r) r = dalloc(&c->w, c->N * lp);
+  if (!r && lp != sizeof(double)) r = dalloc(&c->ulp, c->N * lp);
   if (!r) r = dalloc(&c->fac_x, facx * lp);
   if (!r) r = dalloc(&c->fac_y, 3 * c->N * lp);
   if (!r) r = dalloc(&c->ubuf, c->N * sizeof(double));

@@ -47,6 +47,7 @@ struct tf_ctx {
   int grid_stats;  // blocks of k_grid_stats
   void* bn;        // explicit part b^n, HP storage
   void* w;         // right side of the x solve, overwritten by its solution w, LP
+  void* ulp;       // FP32 copy of the iterate u_k (FP32-bulk only), written by k_rhs
   void* fac_x;     // x-sweep LU factors, LP
   void* fac_y;     // y-sweep LU factors, LP
   double* ubuf;    // iterate buffer

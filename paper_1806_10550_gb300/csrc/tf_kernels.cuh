@@ -66,10 +66,12 @@ struct Scalars {
 struct ModeFP64 {
   typedef double HP;
   typedef double LP;
+  static constexpr int kSweepBlocks = 1;  // sweep blocks per SM (shared memory)
 };
 struct ModeF32B {
   typedef df64 HP;
   typedef float LP;
+  static constexpr int kSweepBlocks = 2;
 };
 
 // ---------------------------------------------------------------------------
@@ -141,6 +143,36 @@ template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
   c.m = M.m;
   c.unitC = M.C == 1.0;
   return c;
+}
+
+// Per-launch constants of the line sweeps and of the residual, converted once
+// on the host: kernels read them from the parameter space and never convert
+// or recompute them per cell.
+template <class T> struct LineK {
+  MobC<T> ml;
+  T inv_ds2;  // 1/ds^2
+  T k3, k1;   // theta dt/(2 ds^4) and theta dt/(2 ds^2): the band's face scales
+};
+template <class T> inline LineK<T> line_consts(const ModelK& M, const StepK& K) {
+  LineK<T> L;
+  L.ml = mob_consts<T>(M);
+  L.inv_ds2 = (T)M.inv_ds2;
+  L.k3 = (T)(0.5 * K.theta_dt * M.inv_ds3 * M.inv_ds);
+  L.k1 = (T)(0.5 * K.theta_dt * M.inv_ds2);
+  return L;
+}
+template <class T> struct RhsK {
+  MobC<T> mc;
+  T inv_ds2, four;
+  T gscale;  // theta dt/(2 ds^2)
+};
+template <class T> inline RhsK<T> rhs_consts(const ModelK& M, const StepK& K) {
+  RhsK<T> R;
+  R.mc = mob_consts<T>(M);
+  R.inv_ds2 = from_f64<T>(M.inv_ds2);
+  R.four = from_f64<T>(4.0);
+  R.gscale = from_f64<T>(0.5 * M.inv_ds2 * K.theta_dt);
+  return R;
 }
 
 // f0 = C h^3 and f1 = h^3 Pi'(h) = A1 h^(2-m) - B1 h^(2-n)

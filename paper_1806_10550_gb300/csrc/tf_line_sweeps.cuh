@@ -16,8 +16,9 @@
 
 namespace tf {
 
-constexpr int kRY = 12;      // rows per chunk of the y sweep (4 groups of 3)
-constexpr int kCX = 12;      // columns per chunk of the x sweep
+constexpr int kRY = 24;      // rows per chunk of the y sweep
+constexpr int kCX = 24;      // columns per chunk of the x sweep
+constexpr int kG = 6;        // cells of a chunk whose band rows one producer thread builds
 constexpr int kProd = 8;     // producer warps per block
 constexpr int kSweepThreads = 32 * (2 + kProd);
 
@@ -25,31 +26,74 @@ constexpr int kSweepThreads = 32 * (2 + kProd);
 // a..e multiply x_{j-2}..x_{j+2}.
 
 constexpr int kNP = 32 * kProd;  // producer threads
+static_assert(2 * 4 * 32 == kNP && 4 * kG == kRY && 4 * kG == kCX,
+              "each producer thread owns one group of kG cells of one line half");
 
-// Film value of a tile in LP (the FP32 Jacobian needs the truncated height).
-template <class LP> __device__ __forceinline__ LP tile_lp(double u);
-template <> __device__ __forceinline__ double tile_lp<double>(double u) { return u; }
-template <> __device__ __forceinline__ float tile_lp<float>(double u) { return f32_of_pos_f64_fast(u); }
-
-// Copy an R x C tile of u with top-left corner (row0, col0) into shared
-// memory (row pitch DP), reflecting indices at the walls; tiles that touch
-// no wall take the plain path.  Executed by the producer threads.
-template <int R, int C, int DP>
-__device__ __forceinline__ void copy_tile_f64(double* dst, const double* __restrict__ u, int row0,
-                                              int col0, int ny, int nx, int p) {
+// Copy an R x C tile of a row-major [ny][nx] array with top-left corner
+// (row0, col0) into shared memory (row pitch DP elements), reflecting indices
+// at the walls.  Interior tiles whose rows are 16-byte aligned move in
+// 16-byte cp.async vectors; other tiles element by element.  Executed by the
+// producer threads.
+template <class T, int R, int C, int DP>
+__device__ __forceinline__ void copy_tile(T* dst, const T* __restrict__ src, int row0, int col0, int ny,
+                                          int nx, int p) {
+  constexpr int V = 16 / sizeof(T);  // elements per vector
   const bool inner = row0 >= 0 && row0 + R <= ny && col0 >= 0 && col0 + C <= nx;
-  if (inner) {
-    const double* base = u + (size_t)row0 * nx + col0;
+  const T* base = src + (size_t)row0 * nx + col0;
+  if (inner && (C % V) == 0 && (DP % V) == 0 && (nx % V) == 0 &&
+      (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+    constexpr int CV = C / V;
+    for (int k = p; k < R * CV; k += kNP) {
+      const int r = k / CV, c = (k - r * CV) * V;
+      __pipeline_memcpy_async(dst + r * DP + c, base + (size_t)r * nx + c, 16);
+    }
+  } else if (inner) {
     for (int k = p; k < R * C; k += kNP) {
       const int r = k / C, c = k - r * C;
-      cp8(dst + r * DP + c, base + (size_t)r * nx + c);
+      cpT(dst + r * DP + c, base + (size_t)r * nx + c);
     }
   } else {
     for (int k = p; k < R * C; k += kNP) {
       const int r = k / C, c = k - r * C;
       const int gj = reflect_index(row0 + r, ny), gi = reflect_index(col0 + c, nx);
-      cp8(dst + r * DP + c, u + (size_t)gj * nx + gi);
+      cpT(dst + r * DP + c, src + (size_t)gj * nx + gi);
     }
+  }
+}
+
+// Copy rows [0, nr) x columns [0, C) of a row-major array (row stride nx)
+// from (row0, col0) into shared memory (row pitch DP), without reflection;
+// columns at or beyond nx are skipped.  Full aligned rows move in 16-byte
+// vectors.
+template <class T, int R, int C, int DP>
+__device__ __forceinline__ void copy_rows(T* dst, const T* __restrict__ src, int row0, int col0, int nr,
+                                          int nx, int p) {
+  constexpr int V = 16 / sizeof(T);
+  const T* base = src + (size_t)row0 * nx + col0;
+  if ((C % V) == 0 && (DP % V) == 0 && col0 + C <= nx && (nx % V) == 0 &&
+      (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+    constexpr int CV = C / V;
+    for (int k = p; k < nr * CV; k += kNP) {
+      const int r = k / CV, c = (k - r * CV) * V;
+      __pipeline_memcpy_async(dst + r * DP + c, base + (size_t)r * nx + c, 16);
+    }
+  } else {
+    for (int k = p; k < nr * C; k += kNP) {
+      const int r = k / C, c = k - r * C;
+      if (col0 + c < nx) cpT(dst + r * DP + c, base + (size_t)r * nx + c);
+    }
+  }
+}
+
+// Copy n contiguous elements (both ends 16-byte aligned when n * sizeof(T)
+// is a multiple of 16).
+template <class T>
+__device__ __forceinline__ void copy_span(T* dst, const T* __restrict__ src, int n, int p) {
+  constexpr int V = 16 / sizeof(T);
+  if ((n % V) == 0 && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+    for (int k = p; k < n / V; k += kNP) __pipeline_memcpy_async(dst + k * V, src + k * V, 16);
+  } else {
+    for (int k = p; k < n; k += kNP) cpT(dst + k, src + k);
   }
 }
 
@@ -101,68 +145,100 @@ __device__ __forceinline__ void face_scaled(const CellS<LP>& P, const CellS<LP>&
   }
 }
 
-// Struct-of-arrays cell buffer: scaled film values of the cells of one chunk
-// plus one halo cell at each end, for 32 lines: [field][cell][line].
-template <class LP, int L> struct CellBuf {
-  LP v[6][L + 2][32];
-  __device__ __forceinline__ void put(int cell, int line, const CellS<LP>& X) {
-    v[0][cell][line] = X.u;
-    v[1][cell][line] = X.lap;
-    v[2][cell][line] = X.F0;
-    v[3][cell][line] = X.F1;
-    v[4][cell][line] = X.D0;
-    v[5][cell][line] = X.D1;
-  }
-  __device__ __forceinline__ CellS<LP> get(int cell, int line) const {
-    CellS<LP> X;
-    X.u = v[0][cell][line];
-    X.lap = v[1][cell][line];
-    X.F0 = v[2][cell][line];
-    X.F1 = v[3][cell][line];
-    X.D0 = v[4][cell][line];
-    X.D1 = v[5][cell][line];
-    return X;
-  }
-};
-
-// Band rows of cells [ia, ib) of one line (chunk origin c0, line length n)
-// from the cell buffer (cell i at index i - c0 + 1), written to B[f][i-c0][line]
-// with the right side r taken from R(i).
-template <class LP, int L, class RhsF>
-__device__ __forceinline__ void band_group(const CellBuf<LP, L>& cb, int line, int c0, int ia, int ib,
-                                           int n, LP* B, RhsF R) {
-  CellS<LP> P = cb.get(ia - c0 + 1, line);
-  LP Lf[4] = {LP(0), LP(0), LP(0), LP(0)};
-  if (ia > 0) face_scaled(cb.get(ia - c0, line), P, ia - 1 > 0, ia + 1 < n, Lf);
-  for (int i = ia; i < ib; ++i) {
-    LP Rf[4] = {LP(0), LP(0), LP(0), LP(0)};
-    if (i + 1 < n) {
-      CellS<LP> Q = cb.get(i - c0 + 2, line);
-      face_scaled(P, Q, i > 0, i + 2 < n, Rf);
-      P = Q;
+// Band rows of the cells ia .. ib-1 (at most G) of one line, built in
+// registers straight from the staged film tile: the scaled film values of the
+// G + 2 cells ia-1 .. ia+G, the G + 1 faces between them, and each row from
+// the derivatives of its two face fluxes (a..e multiply x_{i-2}..x_{i+2}).
+// A(s, dr, dc) is the film at line cell ia + s offset by (dr, dc) in the grid.
+// EDGE: the group may reach a wall, where the outer face of an end cell
+// vanishes and faces next to a wall lose their outer stencil weight; without
+// EDGE (ia >= 2 and ia + G + 1 < n) every face is interior.  OUT(s, a, b, c,
+// d, e) receives the row of cell ia + s.
+template <class LP, int G, bool EDGE, class Acc, class Out>
+__device__ __forceinline__ void band_rows(const LineK<LP>& L, Acc A, int ia, int ib, int n, Out out) {
+  CellS<LP> C[G + 2];
+#pragma unroll
+  for (int s = -1; s <= G; ++s)
+    C[s + 1] = cell_scaled<LP>(L.ml, L.inv_ds2, L.k3, L.k1, [&](int dr, int dc) { return A(s, dr, dc); });
+  LP F[G + 1][4];
+#pragma unroll
+  for (int f = 0; f <= G; ++f) {  // face between cells ia + f - 1 and ia + f
+    if (EDGE) {
+      const int q = ia + f - 1;
+      face_scaled(C[f], C[f + 1], q > 0, q + 2 < n, F[f]);
+      if (!(q >= 0 && q + 1 < n))
+        for (int k = 0; k < 4; ++k) F[f][k] = LP(0);
+    } else {
+      face_scaled(C[f], C[f + 1], true, true, F[f]);
     }
-    const int k = (i - c0) * 32 + line;
-    B[0 * L * 32 + k] = -Lf[0];
-    B[1 * L * 32 + k] = Rf[0] - Lf[1];
-    B[2 * L * 32 + k] = LP(1) + (Rf[1] - Lf[2]);
-    B[3 * L * 32 + k] = Rf[2] - Lf[3];
-    B[4 * L * 32 + k] = Rf[3];
-    B[5 * L * 32 + k] = R(i);
-    for (int q = 0; q < 4; ++q) Lf[q] = Rf[q];
+  }
+#pragma unroll
+  for (int s = 0; s < G; ++s)
+    if (ia + s < ib)
+      out(s, -F[s][0], F[s + 1][0] - F[s][1], LP(1) + (F[s + 1][1] - F[s][2]), F[s + 1][2] - F[s][3],
+          F[s + 1][3]);
+}
+
+// Forward elimination over the n cells of one chunk in the band buffer B
+// ([a..e, r][cell][line]).  REV runs the reversed band from the last cell to
+// the first (the second half of a twisted line).  SPILL(c, g, d, z) stores
+// the factors of chunk cell c.  Full chunks run unrolled so that the band
+// loads of later cells are issued ahead of the recurrence.
+template <class LP, int L, bool REV, class Spill>
+__device__ __forceinline__ void lu_chunk(LUState<LP>& lu, const LP* B, int lane, int n, Spill spill,
+                                         int& bad) {
+  auto one = [&](int c) {
+    const int k = c * 32 + lane;
+    LP g, dl, z;
+    const bool ok =
+        REV ? lu.step(B[4 * L * 32 + k], B[3 * L * 32 + k], B[2 * L * 32 + k], B[L * 32 + k], B[k],
+                      B[5 * L * 32 + k], g, dl, z)
+            : lu.step(B[k], B[L * 32 + k], B[2 * L * 32 + k], B[3 * L * 32 + k], B[4 * L * 32 + k],
+                      B[5 * L * 32 + k], g, dl, z);
+    if (!ok) bad = 1;
+    spill(c, g, dl, z);
+  };
+  if (n == L) {
+#pragma unroll
+    for (int s = 0; s < L; ++s) one(REV ? L - 1 - s : s);
+  } else {
+    for (int s = 0; s < n; ++s) one(REV ? n - 1 - s : s);
+  }
+}
+
+// Back substitution x_c = z_c - g_c x' - d_c x'' over the n cells of one
+// chunk, outward from the seam: c = n-1..0 for the first half, c = 0..n-1
+// (REV) for the second.  F(f, c) reads factor f (g, d, z) of cell c; cells
+// with IS_SEAM(c) take the seam solution XS(c); PUT(c, x) stores x.  Full
+// chunks without seam cells run unrolled.
+template <class LP, int L, bool REV, class Fac, class SeamF, class XsF, class Put>
+__device__ __forceinline__ void bs_chunk(LP& x1, LP& x2, int n, bool any_seam, Fac F, SeamF is_seam,
+                                         XsF xs, Put put) {
+  auto one = [&](int c, bool chk) {
+    const LP x = (chk && is_seam(c)) ? xs(c) : F(2, c) - F(0, c) * x1 - F(1, c) * x2;
+    x2 = x1;
+    x1 = x;
+    put(c, x);
+  };
+  if (n == L && !any_seam) {
+#pragma unroll
+    for (int s = 0; s < L; ++s) one(REV ? s : L - 1 - s, false);
+  } else {
+    for (int s = 0; s < n; ++s) one(REV ? s : n - 1 - s, true);
   }
 }
 
 // ---------------------------------------------------------------------------
 // y sweep.  Block: 32 columns i0..i0+31.  Warp 0 / 1 solve the top / bottom
-// halves; warps 2..5 produce.  Producer thread p: half = p >> 6,
-// col = p & 31, row group = (p >> 5) & 1 (8 rows of a 16-row chunk).
+// halves; warps 2..9 produce.  Producer thread p builds the band rows of
+// half p >> 7, column p & 31 and the row group (p >> 5) & 3 (kG rows of a
+// kRY-row chunk).  Film tiles are staged from the LP film: the FP32 copy that
+// k_rhs wrote in FP32-bulk, u_k itself in FP64.
 
 template <class LP> struct YFwd {
-  double ut[2][2][kRY + 4][34];  // raw film tiles (rows r0-2.., cols i0-1..)
+  LP ut[2][2][kRY + 4][40];      // LP film tiles (rows r0-2.., cols i0-4..i0+35)
   LP wt[2][2][kRY][32];          // right sides w
-  LP lt[2][kRY + 4][35];         // film tile in LP (current producer chunk)
   LP band[2][2][6][kRY][32];     // [stage][half][a..e, r][row][col]
-  CellBuf<LP, kRY> cb[2];        // film values of the chunk's cells
 };
 template <class LP> struct YBwd {
   LP ft[3][2][3][kRY][32];       // factor tiles
@@ -180,10 +256,11 @@ template <class LP> struct YSmem {
 };
 
 template <class Mode>
-__global__ void __launch_bounds__(kSweepThreads)
-    k_ysweep(ModelK M, StepK K, const double* __restrict__ u, const typename Mode::LP* __restrict__ w,
-              typename Mode::LP* __restrict__ fac, double* __restrict__ unew,
-              double* __restrict__ vout, PartY* __restrict__ part) {
+__global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
+    k_ysweep(ModelK M, LineK<typename Mode::LP> L, const double* __restrict__ u,
+             const typename Mode::LP* __restrict__ ul, const typename Mode::LP* __restrict__ w,
+             typename Mode::LP* __restrict__ fac, double* __restrict__ unew, double* __restrict__ vout,
+             PartY* __restrict__ part) {
   typedef typename Mode::LP LP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   YSmem<LP>& S = *reinterpret_cast<YSmem<LP>*>(smem_raw);
@@ -193,16 +270,12 @@ __global__ void __launch_bounds__(kSweepThreads)
   const int nx = M.nx, ny = M.ny;
   const size_t N = (size_t)nx * ny;
   const int i0 = blockIdx.x * 32;
-  const int m = split_point(ny);
+  const int m = split_point<kRY>(ny);
   const bool twisted = m < ny;
   const int nchh[2] = {(m + kRY - 1) / kRY, twisted ? (ny - m + kRY - 1) / kRY : 0};
   const int nch = max(nchh[0], nchh[1]);
   auto r0_of = [&](int h, int q) { return h == 0 ? q * kRY : max(m, ny - (q + 1) * kRY); };
   auto r1_of = [&](int h, int q) { return h == 0 ? min(m, (q + 1) * kRY) : ny - q * kRY; };
-  const MobC<LP> ml = mob_consts<LP>(M);
-  const LP inv_ds2 = (LP)M.inv_ds2;
-  const LP k3 = (LP)(0.5 * K.theta_dt * M.inv_ds3 * M.inv_ds);
-  const LP k1 = (LP)(0.5 * K.theta_dt * M.inv_ds2);
   LP* fg = fac;
   LP* fd = fac + N;
   LP* fz = fac + 2 * N;
@@ -215,11 +288,8 @@ __global__ void __launch_bounds__(kSweepThreads)
     for (int h = 0; h < 2; ++h) {
       if (q >= nchh[h]) continue;
       const int r0 = r0_of(h, q), r1 = r1_of(h, q);
-      copy_tile_f64<kRY + 4, 34, 34>(&S.s.f.ut[slot][h][0][0], u, r0 - 2, i0 - 1, ny, nx, p);
-      for (int k = p; k < kRY * 32; k += kNP) {
-        int r = k >> 5, c = k & 31;
-        if (r0 + r < r1 && i0 + c < nx) cpT(&S.s.f.wt[slot][h][r][c], w + (size_t)(r0 + r) * nx + i0 + c);
-      }
+      copy_tile<LP, kRY + 4, 40, 40>(&S.s.f.ut[slot][h][0][0], ul, r0 - 2, i0 - 4, ny, nx, p);
+      copy_rows<LP, kRY, 32, 32>(&S.s.f.wt[slot][h][0][0], w, r0, i0, r1 - r0, nx, p);
     }
     __pipeline_commit();
   };
@@ -237,37 +307,30 @@ __global__ void __launch_bounds__(kSweepThreads)
         pbar();
         if (t + 1 < nch) issue_fwd(t + 1);  // slot (t+1)&1 was consumed last tick
         const int slot = t & 1;
-        for (int h = 0; h < 2; ++h) {
-          if (t >= nchh[h]) continue;
-          for (int k = p; k < (kRY + 4) * 34; k += kNP) {
-            int r = k / 34, c = k - r * 34;
-            S.s.f.lt[h][r][c] = tile_lp<LP>(S.s.f.ut[slot][h][r][c]);
-          }
-        }
-        pbar();
-        // phase A: film values of rows r0-1..r1 of each half's 32 columns
-        for (int h = 0; h < 2; ++h) {
-          if (t >= nchh[h]) continue;
-          const int r0 = r0_of(h, t), r1 = r1_of(h, t);
-          for (int k = p; k < (kRY + 2) * 32; k += kNP) {
-            const int cr = k >> 5, c = k & 31;  // cell row index: global row r0 - 1 + cr
-            if (r0 - 1 + cr > r1 || i0 + c >= nx) continue;
-            const int rr = cr + 1, cc = c + 1;  // tile position of the cell
-            S.s.f.cb[h].put(cr, c, cell_scaled<LP>(ml, inv_ds2, k3, k1, [&](int dr, int dc) {
-                              return S.s.f.lt[h][rr + dr][cc + dc];
-                            }));
-          }
-        }
-        pbar();
-        // phase B: band rows; thread p covers (half, column, 3 rows)
+        // band rows: thread p builds rows ja..jb-1 of column c of half h
         {
           const int h = p >> 7, g = (p >> 5) & 3, c = p & 31;
           if (t < nchh[h] && i0 + c < nx) {
             const int r0 = r0_of(h, t), r1 = r1_of(h, t);
-            const int ja = r0 + 3 * g, jb = min(r1, ja + 3);
-            if (ja < jb)
-              band_group<LP, kRY>(S.s.f.cb[h], c, r0, ja, jb, ny, &S.s.f.band[t & 1][h][0][0][0],
-                                  [&](int j) { return S.s.f.wt[slot][h][j - r0][c]; });
+            const int ja = r0 + kG * g, jb = min(r1, ja + kG);
+            if (ja < jb) {
+              LP* B = &S.s.f.band[t & 1][h][0][0][0];
+              const LP* T = &S.s.f.ut[slot][h][ja - r0 + 2][c + 4];  // cell ja in the tile
+              auto A = [&](int s, int dr, int dc) { return T[(s + dr) * 40 + dc]; };
+              auto out = [&](int s, LP a, LP b, LP cc, LP d, LP e) {
+                const int k = (ja - r0 + s) * 32 + c;
+                B[0 * kRY * 32 + k] = a;
+                B[1 * kRY * 32 + k] = b;
+                B[2 * kRY * 32 + k] = cc;
+                B[3 * kRY * 32 + k] = d;
+                B[4 * kRY * 32 + k] = e;
+                B[5 * kRY * 32 + k] = S.s.f.wt[slot][h][ja - r0 + s][c];
+              };
+              if (ja >= 2 && ja + kG + 1 < ny)
+                band_rows<LP, kG, false>(L, A, ja, jb, ny, out);
+              else
+                band_rows<LP, kG, true>(L, A, ja, jb, ny, out);
+            }
           }
         }
       }
@@ -277,31 +340,16 @@ __global__ void __launch_bounds__(kSweepThreads)
         const int r0 = r0_of(h, q), r1 = r1_of(h, q);
         const LP* B = &S.s.f.band[q & 1][h][0][0][0];
         const int col = i0 + lane;
-        if (h == 0) {
-          for (int j = r0; j < r1; ++j) {
-            const int k = (j - r0) * 32 + lane;
-            LP g, dl, z;
-            if (!lu.step(B[k], B[kRY * 32 + k], B[2 * kRY * 32 + k], B[3 * kRY * 32 + k],
-                         B[4 * kRY * 32 + k], B[5 * kRY * 32 + k], g, dl, z))
-              pivot_bad = 1;
-            const size_t idx = (size_t)j * nx + col;
-            fg[idx] = g;
-            fd[idx] = dl;
-            fz[idx] = z;
-          }
-        } else {
-          for (int j = r1 - 1; j >= r0; --j) {
-            const int k = (j - r0) * 32 + lane;
-            LP g, dl, z;
-            if (!lu.step(B[4 * kRY * 32 + k], B[3 * kRY * 32 + k], B[2 * kRY * 32 + k],
-                         B[kRY * 32 + k], B[k], B[5 * kRY * 32 + k], g, dl, z))
-              pivot_bad = 1;
-            const size_t idx = (size_t)j * nx + col;
-            fg[idx] = g;
-            fd[idx] = dl;
-            fz[idx] = z;
-          }
-        }
+        auto spill = [&](int c, LP g, LP dl, LP z) {
+          const size_t idx = (size_t)(r0 + c) * nx + col;
+          fg[idx] = g;
+          fd[idx] = dl;
+          fz[idx] = z;
+        };
+        if (h == 0)
+          lu_chunk<LP, kRY, false>(lu, B, lane, r1 - r0, spill, pivot_bad);
+        else
+          lu_chunk<LP, kRY, true>(lu, B, lane, r1 - r0, spill, pivot_bad);
       }
     }
     __syncthreads();
@@ -325,11 +373,8 @@ __global__ void __launch_bounds__(kSweepThreads)
       const int q = nchh[h] - 1 - bq;
       if (q < 0) continue;
       const int r0 = r0_of(h, q), r1 = r1_of(h, q);
-      for (int k = p; k < 3 * kRY * 32; k += kNP) {
-        int f = k / (kRY * 32), rem = k - f * kRY * 32, r = rem >> 5, c = rem & 31;
-        if (r0 + r < r1 && i0 + c < nx)
-          cpT(&S.s.b.ft[slot][h][f][r][c], fac + (size_t)f * N + (size_t)(r0 + r) * nx + i0 + c);
-      }
+      for (int f = 0; f < 3; ++f)
+        copy_rows<LP, kRY, 32, 32>(&S.s.b.ft[slot][h][f][0][0], fac + (size_t)f * N, r0, i0, r1 - r0, nx, p);
     }
   };
   auto issue_bwd_u = [&](int bq) {  // u_k tiles of backward chunk bq
@@ -338,11 +383,7 @@ __global__ void __launch_bounds__(kSweepThreads)
       const int q = nchh[h] - 1 - bq;
       if (q < 0) continue;
       const int r0 = r0_of(h, q), r1 = r1_of(h, q);
-      for (int k = p; k < kRY * 32; k += kNP) {
-        int r = k >> 5, c = k & 31;
-        if (r0 + r < r1 && i0 + c < nx)
-          cp8(&S.s.b.ukt[slot][h][r][c], u + (size_t)(r0 + r) * nx + i0 + c);
-      }
+      copy_rows<double, kRY, 32, 32>(&S.s.b.ukt[slot][h][0][0], u, r0, i0, r1 - r0, nx, p);
     }
   };
   LP x1 = LP(0), x2 = LP(0);
@@ -379,28 +420,15 @@ __global__ void __launch_bounds__(kSweepThreads)
           const int r0 = r0_of(h, q), r1 = r1_of(h, q);
           const int slot = t % 3;
           LP* X = &S.s.b.xb[t & 1][h][0][0];
-          if (h == 0) {
-            for (int j = r1 - 1; j >= r0; --j) {
-              const int k = j - r0;
-              LP x = (twisted && j >= m - 2)
-                         ? S.xs[lane][j - (m - 2)]
-                         : S.s.b.ft[slot][h][2][k][lane] - S.s.b.ft[slot][h][0][k][lane] * x1 -
-                               S.s.b.ft[slot][h][1][k][lane] * x2;
-              x2 = x1;
-              x1 = x;
-              X[k * 32 + lane] = x;
-            }
-          } else {
-            for (int j = r0; j < r1; ++j) {
-              const int k = j - r0;
-              LP x = (j <= m + 1) ? S.xs[lane][j - (m - 2)]
-                                  : S.s.b.ft[slot][h][2][k][lane] - S.s.b.ft[slot][h][0][k][lane] * x1 -
-                                        S.s.b.ft[slot][h][1][k][lane] * x2;
-              x2 = x1;
-              x1 = x;
-              X[k * 32 + lane] = x;
-            }
-          }
+          auto F = [&](int f, int c) { return S.s.b.ft[slot][h][f][c][lane]; };
+          auto xs = [&](int c) { return S.xs[lane][r0 + c - (m - 2)]; };
+          auto put = [&](int c, LP x) { X[c * 32 + lane] = x; };
+          if (h == 0)
+            bs_chunk<LP, kRY, false>(x1, x2, r1 - r0, twisted && r1 > m - 2, F,
+                                     [&](int c) { return twisted && r0 + c >= m - 2; }, xs, put);
+          else
+            bs_chunk<LP, kRY, true>(x1, x2, r1 - r0, r0 <= m + 1, F,
+                                    [&](int c) { return r0 + c <= m + 1; }, xs, put);
         }
       }
     } else {
@@ -412,8 +440,11 @@ __global__ void __launch_bounds__(kSweepThreads)
           if (q < 0) continue;
           const int r0 = r0_of(h, q), r1 = r1_of(h, q);
           const LP* X = &S.s.b.xb[bq & 1][h][0][0];
-          for (int k = p; k < kRY * 32; k += kNP) {
-            int r = k >> 5, c = k & 31;
+#pragma unroll
+          for (int e = 0; e < (kRY * 32 + kNP - 1) / kNP; ++e) {
+            const int k = p + e * kNP;
+            if (k >= kRY * 32) continue;
+            const int r = k >> 5, c = k & 31;
             const int j = r0 + r, col = i0 + c;
             if (j >= r1 || col >= nx) continue;
             const LP x = X[k];
@@ -473,16 +504,15 @@ __global__ void __launch_bounds__(kSweepThreads)
 
 // ---------------------------------------------------------------------------
 // x sweep.  Block: 32 rows j0..j0+31.  Warp 0 / 1 solve the left / right
-// halves of the rows (lane = row); warps 2..5 produce.  Producer thread p:
-// half = p >> 6, row = p & 31, column group = (p >> 5) & 1 (8 columns of a
-// 16-column chunk).  Factor scratch per block: fac[((blk*3 + f)*nx + col)*32 + row].
+// halves of the rows (lane = row); warps 2..9 produce.  Producer thread p
+// builds the band rows of half p >> 7, row p & 31 and the column group
+// (p >> 5) & 3 (kG columns of a kCX-column chunk).  Factor scratch per block:
+// fac[((blk*3 + f)*nx + col)*32 + row].
 
 template <class LP> struct XFwd {
-  double ut[2][2][34][kCX + 4];  // raw film tiles (rows j0-1.., cols c0-2..)
+  LP ut[2][2][34][kCX + 5];      // LP film tiles (rows j0-1.., cols c0-2..c0+kCX+1)
   LP rt[2][2][32][kCX + 1];      // right sides
-  LP lt[2][34][kCX + 5];         // film tile in LP
   LP band[2][2][6][kCX][32];     // [stage][half][a..e, r][col][row]
-  CellBuf<LP, kCX> cb[2];        // film values of the chunk's cells
 };
 template <class LP> struct XBwd {
   LP ft[3][2][3][kCX][32];       // factor tiles [f][col][row]
@@ -499,9 +529,10 @@ template <class LP> struct XSmem {
 };
 
 template <class Mode>
-__global__ void __launch_bounds__(kSweepThreads)
-    k_xsweep(ModelK M, StepK K, const double* __restrict__ u, typename Mode::LP* __restrict__ rw,
-              typename Mode::LP* __restrict__ fac, PartX* __restrict__ part) {
+__global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
+    k_xsweep(ModelK M, LineK<typename Mode::LP> L, const typename Mode::LP* __restrict__ ul,
+             typename Mode::LP* __restrict__ rw, typename Mode::LP* __restrict__ fac,
+             PartX* __restrict__ part) {
   typedef typename Mode::LP LP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   XSmem<LP>& S = *reinterpret_cast<XSmem<LP>*>(smem_raw);
@@ -510,16 +541,12 @@ __global__ void __launch_bounds__(kSweepThreads)
   const int p = threadIdx.x - 64;
   const int nx = M.nx, ny = M.ny;
   const int j0 = blockIdx.x * 32;
-  const int m = split_point(nx);
+  const int m = split_point<kCX>(nx);
   const bool twisted = m < nx;
   const int nchh[2] = {(m + kCX - 1) / kCX, twisted ? (nx - m + kCX - 1) / kCX : 0};
   const int nch = max(nchh[0], nchh[1]);
   auto c0_of = [&](int h, int q) { return h == 0 ? q * kCX : max(m, nx - (q + 1) * kCX); };
   auto c1_of = [&](int h, int q) { return h == 0 ? min(m, (q + 1) * kCX) : nx - q * kCX; };
-  const MobC<LP> ml = mob_consts<LP>(M);
-  const LP inv_ds2 = (LP)M.inv_ds2;
-  const LP k3 = (LP)(0.5 * K.theta_dt * M.inv_ds3 * M.inv_ds);
-  const LP k1 = (LP)(0.5 * K.theta_dt * M.inv_ds2);
   LP* facb = fac + (size_t)blockIdx.x * 3 * nx * 32;
   int pivot_bad = 0;
 
@@ -528,7 +555,7 @@ __global__ void __launch_bounds__(kSweepThreads)
     for (int h = 0; h < 2; ++h) {
       if (q >= nchh[h]) continue;
       const int c0 = c0_of(h, q), c1 = c1_of(h, q);
-      copy_tile_f64<34, kCX + 4, kCX + 4>(&S.s.f.ut[slot][h][0][0], u, j0 - 1, c0 - 2, ny, nx, p);
+      copy_tile<LP, 34, kCX + 4, kCX + 5>(&S.s.f.ut[slot][h][0][0], ul, j0 - 1, c0 - 2, ny, nx, p);
       for (int k = p; k < 32 * kCX; k += kNP) {
         int r = k / kCX, c = k - r * kCX;
         if (j0 + r < ny && c0 + c < c1) cpT(&S.s.f.rt[slot][h][r][c], rw + (size_t)(j0 + r) * nx + c0 + c);
@@ -548,37 +575,30 @@ __global__ void __launch_bounds__(kSweepThreads)
         pbar();
         if (t + 1 < nch) issue_fwd(t + 1);  // slot (t+1)&1 was consumed last tick
         const int slot = t & 1;
-        for (int h = 0; h < 2; ++h) {
-          if (t >= nchh[h]) continue;
-          for (int k = p; k < 34 * (kCX + 4); k += kNP) {
-            int r = k / (kCX + 4), c = k - r * (kCX + 4);
-            S.s.f.lt[h][r][c] = tile_lp<LP>(S.s.f.ut[slot][h][r][c]);
-          }
-        }
-        pbar();
-        // phase A: film values of cols c0-1..c1 of each half's 32 rows
-        for (int h = 0; h < 2; ++h) {
-          if (t >= nchh[h]) continue;
-          const int c0 = c0_of(h, t), c1 = c1_of(h, t);
-          for (int k = p; k < (kCX + 2) * 32; k += kNP) {
-            const int ci = k >> 5, r = k & 31;  // cell col index: global col c0 - 1 + ci
-            if (c0 - 1 + ci > c1 || j0 + r >= ny) continue;
-            const int rr = r + 1, cc = ci + 1;
-            S.s.f.cb[h].put(ci, r, cell_scaled<LP>(ml, inv_ds2, k3, k1, [&](int dr, int dc) {
-                              return S.s.f.lt[h][rr + dr][cc + dc];
-                            }));
-          }
-        }
-        pbar();
-        // phase B: band rows; thread p covers (half, row, 3 columns)
+        // band rows: thread p builds rows ia..ib-1 of row r of half h
         {
           const int h = p >> 7, g = (p >> 5) & 3, r = p & 31;
           if (t < nchh[h] && j0 + r < ny) {
             const int c0 = c0_of(h, t), c1 = c1_of(h, t);
-            const int ia = c0 + 3 * g, ib = min(c1, ia + 3);
-            if (ia < ib)
-              band_group<LP, kCX>(S.s.f.cb[h], r, c0, ia, ib, nx, &S.s.f.band[t & 1][h][0][0][0],
-                                  [&](int i) { return S.s.f.rt[slot][h][r][i - c0]; });
+            const int ia = c0 + kG * g, ib = min(c1, ia + kG);
+            if (ia < ib) {
+              LP* B = &S.s.f.band[t & 1][h][0][0][0];
+              const LP* T = &S.s.f.ut[slot][h][r + 1][ia - c0 + 2];  // cell ia in the tile
+              auto A = [&](int s, int dr, int dc) { return T[dr * (kCX + 5) + s + dc]; };
+              auto out = [&](int s, LP a, LP b, LP c, LP d, LP e) {
+                const int k = (ia - c0 + s) * 32 + r;
+                B[0 * kCX * 32 + k] = a;
+                B[1 * kCX * 32 + k] = b;
+                B[2 * kCX * 32 + k] = c;
+                B[3 * kCX * 32 + k] = d;
+                B[4 * kCX * 32 + k] = e;
+                B[5 * kCX * 32 + k] = S.s.f.rt[slot][h][r][ia - c0 + s];
+              };
+              if (ia >= 2 && ia + kG + 1 < nx)
+                band_rows<LP, kG, false>(L, A, ia, ib, nx, out);
+              else
+                band_rows<LP, kG, true>(L, A, ia, ib, nx, out);
+            }
           }
         }
       }
@@ -590,29 +610,16 @@ __global__ void __launch_bounds__(kSweepThreads)
         LP* fg = facb;
         LP* fd = facb + (size_t)nx * 32;
         LP* fz = facb + (size_t)2 * nx * 32;
-        if (h == 0) {
-          for (int i = c0; i < c1; ++i) {
-            const int k = (i - c0) * 32 + lane;
-            LP g, dl, z;
-            if (!lu.step(B[k], B[kCX * 32 + k], B[2 * kCX * 32 + k], B[3 * kCX * 32 + k],
-                         B[4 * kCX * 32 + k], B[5 * kCX * 32 + k], g, dl, z))
-              pivot_bad = 1;
-            fg[(size_t)i * 32 + lane] = g;
-            fd[(size_t)i * 32 + lane] = dl;
-            fz[(size_t)i * 32 + lane] = z;
-          }
-        } else {
-          for (int i = c1 - 1; i >= c0; --i) {
-            const int k = (i - c0) * 32 + lane;
-            LP g, dl, z;
-            if (!lu.step(B[4 * kCX * 32 + k], B[3 * kCX * 32 + k], B[2 * kCX * 32 + k],
-                         B[kCX * 32 + k], B[k], B[5 * kCX * 32 + k], g, dl, z))
-              pivot_bad = 1;
-            fg[(size_t)i * 32 + lane] = g;
-            fd[(size_t)i * 32 + lane] = dl;
-            fz[(size_t)i * 32 + lane] = z;
-          }
-        }
+        auto spill = [&](int c, LP g, LP dl, LP z) {
+          const size_t o = (size_t)(c0 + c) * 32 + lane;
+          fg[o] = g;
+          fd[o] = dl;
+          fz[o] = z;
+        };
+        if (h == 0)
+          lu_chunk<LP, kCX, false>(lu, B, lane, c1 - c0, spill, pivot_bad);
+        else
+          lu_chunk<LP, kCX, true>(lu, B, lane, c1 - c0, spill, pivot_bad);
       }
     }
     __syncthreads();
@@ -632,11 +639,8 @@ __global__ void __launch_bounds__(kSweepThreads)
       const int q = nchh[h] - 1 - bq;
       if (q < 0) continue;
       const int c0 = c0_of(h, q), c1 = c1_of(h, q);
-      for (int f = 0; f < 3; ++f) {
-        const LP* src = facb + ((size_t)f * nx + c0) * 32;
-        for (int k = p; k < (c1 - c0) * 32; k += kNP)
-          cpT(&S.s.b.ft[slot][h][f][k >> 5][k & 31], src + k);
-      }
+      for (int f = 0; f < 3; ++f)
+        copy_span<LP>(&S.s.b.ft[slot][h][f][0][0], facb + ((size_t)f * nx + c0) * 32, (c1 - c0) * 32, p);
     }
     __pipeline_commit();
   };
@@ -664,28 +668,15 @@ __global__ void __launch_bounds__(kSweepThreads)
         if (q >= 0 && j0 + lane < ny) {
           const int c0 = c0_of(h, q), c1 = c1_of(h, q);
           const int slot = t % 3;
-          if (h == 0) {
-            for (int i = c1 - 1; i >= c0; --i) {
-              const int k = i - c0;
-              LP x = (twisted && i >= m - 2)
-                         ? S.xs[lane][i - (m - 2)]
-                         : S.s.b.ft[slot][h][2][k][lane] - S.s.b.ft[slot][h][0][k][lane] * x1 -
-                               S.s.b.ft[slot][h][1][k][lane] * x2;
-              x2 = x1;
-              x1 = x;
-              S.s.b.xb[t & 1][h][k][lane] = x;
-            }
-          } else {
-            for (int i = c0; i < c1; ++i) {
-              const int k = i - c0;
-              LP x = (i <= m + 1) ? S.xs[lane][i - (m - 2)]
-                                  : S.s.b.ft[slot][h][2][k][lane] - S.s.b.ft[slot][h][0][k][lane] * x1 -
-                                        S.s.b.ft[slot][h][1][k][lane] * x2;
-              x2 = x1;
-              x1 = x;
-              S.s.b.xb[t & 1][h][k][lane] = x;
-            }
-          }
+          auto F = [&](int f, int c) { return S.s.b.ft[slot][h][f][c][lane]; };
+          auto xs = [&](int c) { return S.xs[lane][c0 + c - (m - 2)]; };
+          auto put = [&](int c, LP x) { S.s.b.xb[t & 1][h][c][lane] = x; };
+          if (h == 0)
+            bs_chunk<LP, kCX, false>(x1, x2, c1 - c0, twisted && c1 > m - 2, F,
+                                     [&](int c) { return twisted && c0 + c >= m - 2; }, xs, put);
+          else
+            bs_chunk<LP, kCX, true>(x1, x2, c1 - c0, c0 <= m + 1, F,
+                                    [&](int c) { return c0 + c <= m + 1; }, xs, put);
         }
       }
     } else {

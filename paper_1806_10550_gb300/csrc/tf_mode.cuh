@@ -50,18 +50,27 @@ template <class Mode> struct Launch {
   }
   static cudaError_t rhs_c(tf_ctx& c, const double* u_k, double dt) {
     dim3 grid(c.grid_rx, c.grid_ry);
-    k_rhs<Mode><<<grid, 256, smem_rhs, c.stream>>>(c.mk, step(c, dt), u_k, (const HP*)c.bn, (LP*)c.w,
-                                                   c.px);
+    k_rhs<Mode><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k,
+                                                   (const HP*)c.bn, (LP*)c.w,
+                                                   (LP*)c.ulp, c.px);
     return cudaGetLastError();
   }
+  // film the sweeps stage: u_k itself in FP64, its FP32 copy (written by
+  // k_rhs of the same iteration) in FP32-bulk
+  static const LP* film_lp(const tf_ctx& c, const double* u_k) {
+    return sizeof(LP) == sizeof(double) ? (const LP*)u_k : (const LP*)c.ulp;
+  }
   static cudaError_t xsweep_c(tf_ctx& c, double dt, const double* u_k) {
-    k_xsweep<Mode><<<c.grid_x, kSweepThreads, smem_x, c.stream>>>(c.mk, step(c, dt), u_k, (LP*)c.w,
+    k_xsweep<Mode><<<c.grid_x, kSweepThreads, smem_x, c.stream>>>(c.mk, line_consts<LP>(c.mk, step(c, dt)),
+                                                       film_lp(c, u_k), (LP*)c.w,
                                                        (LP*)c.fac_x, c.px + c.grid_rx * c.grid_ry);
     return cudaGetLastError();
   }
   static cudaError_t ysweep_c(tf_ctx& c, const double* u_k, double dt, double* u_next,
                               double* v_out) {
-    k_ysweep<Mode><<<c.grid_y, kSweepThreads, smem_y, c.stream>>>(c.mk, step(c, dt), u_k, (const LP*)c.w,
+    k_ysweep<Mode><<<c.grid_y, kSweepThreads, smem_y, c.stream>>>(c.mk, line_consts<LP>(c.mk, step(c, dt)),
+                                                       u_k, film_lp(c, u_k),
+                                                       (const LP*)c.w,
                                                        (LP*)c.fac_y, u_next, v_out, c.py);
     return cudaGetLastError();
   }

@@ -1,7 +1,8 @@
 // tf_sweeps.cuh -- residual kernel and the line machinery shared by the
 // sweeps of one Newton--ADI iteration (eqs. JacobianSystem1-3):
 //
-//   k_rhs     2-D tiles: r = -G(u_k) in HP, stored in LP (the x right side)
+//   k_rhs     2-D tiles: r = -G(u_k) in HP, stored in LP (the x right side);
+//             in FP32-bulk also the FP32 film copy that the sweeps stage
 //   (the x and y sweeps that solve the lines are in tf_line_sweeps.cuh)
 //
 // Each line is solved exactly by a twisted ("meet in the middle") LU
@@ -25,8 +26,6 @@
 #include "tf_kernels.cuh"
 
 namespace tf {
-
-constexpr int kChunk = 32;  // cells per staged chunk along a line
 
 // ---------------------------------------------------------------------------
 // residual -> right side of the x solve
@@ -56,8 +55,10 @@ template <class HP, int T> struct RhsSmem {
 
 template <class Mode>
 __global__ void __launch_bounds__(256)
-    k_rhs(ModelK M, StepK K, const double* __restrict__ u, const typename Mode::HP* __restrict__ bn,
-          typename Mode::LP* __restrict__ rhs, PartX* __restrict__ part) {
+    k_rhs(ModelK M, RhsK<typename Mode::HP> RK, const double* __restrict__ u,
+          const typename Mode::HP* __restrict__ bn,
+          typename Mode::LP* __restrict__ rhs, typename Mode::LP* __restrict__ ul,
+          PartX* __restrict__ part) {
   typedef typename Mode::HP HP;
   typedef typename Mode::LP LP;
   constexpr int T = 32, NT = 256;
@@ -65,15 +66,15 @@ __global__ void __launch_bounds__(256)
   RhsSmem<HP, T>& S = *reinterpret_cast<RhsSmem<HP, T>*>(smem_raw);
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * T, j0 = blockIdx.y * T;
-  const MobC<HP> mc = mob_consts<HP>(M);
-  const HP inv_ds2 = from_f64<HP>(M.inv_ds2);
+  const MobC<HP>& mc = RK.mc;
+  const HP inv_ds2 = RK.inv_ds2;
   for (int k = tid; k < (T + 4) * (T + 4); k += NT) {
     int r = k / (T + 4), c = k - r * (T + 4);
     int gj = reflect_index(j0 - 2 + r, M.ny), gi = reflect_index(x0 - 2 + c, M.nx);
     S.u[r][c] = film_hp<HP>(__ldg(u + (size_t)gj * M.nx + gi));
   }
   __syncthreads();
-  const HP four = from_f64<HP>(4.0);
+  const HP four = RK.four;
   for (int k = tid; k < (T + 2) * (T + 2); k += NT) {
     int r = k / (T + 2), c = k - r * (T + 2);
     HP uc = S.u[r + 1][c + 1];
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(256)
     S.fy[r][c] = F;
   }
   __syncthreads();
-  const HP gscale = from_f64<HP>(0.5 * M.inv_ds2 * K.theta_dt);
+  const HP gscale = RK.gscale;
   LP g = LP(0);  // max |G| in LP: a norm for reporting, not a decision
   for (int k = tid; k < T * T; k += NT) {
     int r = k / T, c = k - r * T;
@@ -123,6 +124,9 @@ __global__ void __launch_bounds__(256)
       HP Gv = hp_norm(hp_add(hp_sub(S.u[r + 2][c + 2], bn[idx]), hp_mul(gscale, dp)));
       LP gl = to_lp<LP, HP>(Gv);
       rhs[idx] = -gl;
+      // FP32 film for the sweeps: the leading float of the double-float
+      // height (the truncated height the FP32 Jacobian is built from)
+      if constexpr (sizeof(LP) == 4) ul[idx] = S.u[r + 2][c + 2].hi;
       LP ag = fabs(gl);
       if (!(ag <= g)) g = ag;
     }
@@ -197,11 +201,12 @@ __device__ __forceinline__ bool seam(const LUState<LP>& S, const LUState<LP>& R,
   return solve4(A, b, x);
 }
 
-// Where each line splits: the first half covers cells [0, m); twisting
-// needs m >= 2 and n - m >= 2.
-__host__ __device__ __forceinline__ int split_point(int n) {
-  int nch = (n + kChunk - 1) / kChunk;
-  int m = ((nch + 1) / 2) * kChunk;
+// Where each line splits: the first half covers cells [0, m) with m a
+// multiple of the chunk length C near n/2; twisting needs m >= 2 and
+// n - m >= 2.
+template <int C> __host__ __device__ __forceinline__ int split_point(int n) {
+  const int nch = (n + C - 1) / C;
+  const int m = ((nch + 1) / 2) * C;
   if (m >= n - 1 || m < 2) return n;  // no second half
   return m;
 }

@@ -76,7 +76,7 @@ def test_residual_parity(torch, mode, nx, ny):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("nx,ny", [(1, 40), (40, 1), (3, 2), (37, 53), (64, 64), (130, 97)])
+@pytest.mark.parametrize("nx,ny", [(1, 40), (40, 1), (3, 2), (37, 53), (64, 64), (130, 97), (203, 151)])
 def test_one_iteration_parity(torch, mode, nx, ny):
     ds, dt = 1.9, 20.0
     om, p = models(nx, ny, ds, mode)
