@@ -126,6 +126,7 @@ template <class T> struct MobC {
   T dA1, dB1;  // (m-2) A1 and (n-2) B1
   int model, n, m;
   bool unitC;  // C == 1
+  bool pl32;   // power law with (n, m) = (3, 2)
 };
 template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
   MobC<T> c;
@@ -142,6 +143,7 @@ template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
   c.n = M.n;
   c.m = M.m;
   c.unitC = M.C == 1.0;
+  c.pl32 = M.model == 0 && M.n == 3 && M.m == 2;
   return c;
 }
 
@@ -152,13 +154,23 @@ template <class T> struct LineK {
   MobC<T> ml;
   T inv_ds2;  // 1/ds^2
   T k3, k1;   // theta dt/(2 ds^4) and theta dt/(2 ds^2): the band's face scales
+  // folded factors of the (n, m) = (3, 2) power law (ml.pl32):
+  // F0 = k3 C h^3, F1 = k1 A1 - k1 B1 / h, D0 = (k1 / ds^2) 3 C h^2 (the
+  // Laplacian left unscaled), D1 = k1 B1 / h^2
+  T pF0, pF1a, pF1b, pD0, pD1;
 };
 template <class T> inline LineK<T> line_consts(const ModelK& M, const StepK& K) {
   LineK<T> L;
   L.ml = mob_consts<T>(M);
   L.inv_ds2 = (T)M.inv_ds2;
-  L.k3 = (T)(0.5 * K.theta_dt * M.inv_ds3 * M.inv_ds);
-  L.k1 = (T)(0.5 * K.theta_dt * M.inv_ds2);
+  const double k3 = 0.5 * K.theta_dt * M.inv_ds3 * M.inv_ds, k1 = 0.5 * K.theta_dt * M.inv_ds2;
+  L.k3 = (T)k3;
+  L.k1 = (T)k1;
+  L.pF0 = (T)(k3 * M.C);
+  L.pF1a = (T)(k1 * M.A1);
+  L.pF1b = (T)(k1 * M.B1);
+  L.pD0 = (T)(k1 * M.inv_ds2 * 3.0 * M.C);
+  L.pD1 = (T)(k1 * M.B1);
   return L;
 }
 template <class T> struct RhsK {
@@ -175,39 +187,65 @@ template <class T> inline RhsK<T> rhs_consts(const ModelK& M, const StepK& K) {
   return R;
 }
 
+template <class T> struct MobPair {
+  T a, b;
+};
+
 // f0 = C h^3 and f1 = h^3 Pi'(h) = A1 h^(2-m) - B1 h^(2-n)
-// (Sec. Thin Film Models, eq. GeneralDisPreForm).
+// (Sec. Thin Film Models, eq. GeneralDisPreForm); the linear model has
+// constant f0 = c0, f1 = c1.  General exponents and the linear model are
+// evaluated out of line, so that kernels inline only the (n, m) = (3, 2)
+// power law.
 template <class T>
-TF_HD void mobility(const MobC<T>& c, const T& h, const T& s, T& f0, T& f1) {
+__host__ __device__ __noinline__ MobPair<T> mobility_general(const MobC<T> c, const T h, const T s) {
+  MobPair<T> r;
   if (c.model == 1) {
-    f0 = c.c0;
-    f1 = c.c1;
-    return;
+    r.a = c.c0;
+    r.b = c.c1;
+    return r;
   }
-  f0 = c.unitC ? (h * h) * h : c.C * (h * h) * h;
-  if (c.n == 3 && c.m == 2) {  // f1 = A1 - B1 / h
-    f1 = c.A1 - c.B1 * s;
-    return;
-  }
+  r.a = c.unitC ? (h * h) * h : c.C * (h * h) * h;
   T a = c.m == 2 ? c.A1 : c.A1 * hpow_neg(h, s, c.m - 2);
   T b = c.n == 2 ? c.B1 : c.B1 * hpow_neg(h, s, c.n - 2);
-  f1 = a - b;
+  r.b = a - b;
+  return r;
 }
 // f0' = 3 C h^2, f1' = -(m-2) A1 h^(1-m) + (n-2) B1 h^(1-n).
 template <class T>
-TF_HD void mobility_d(const MobC<T>& c, const T& h, const T& s, T& d0, T& d1) {
+__host__ __device__ __noinline__ MobPair<T> mobility_d_general(const MobC<T> c, const T h, const T s) {
+  MobPair<T> r;
   if (c.model == 1) {
-    d0 = zero<T>();
-    d1 = zero<T>();
+    r.a = zero<T>();
+    r.b = zero<T>();
+    return r;
+  }
+  r.a = c.three * c.C * (h * h);
+  T b = c.dB1 * hpow_neg(h, s, c.n - 1);
+  r.b = c.m == 2 ? b : b - c.dA1 * hpow_neg(h, s, c.m - 1);
+  return r;
+}
+
+template <class T>
+TF_HD void mobility(const MobC<T>& c, const T& h, const T& s, T& f0, T& f1) {
+  if (c.pl32) {  // f1 = A1 - B1 / h
+    f0 = c.unitC ? (h * h) * h : c.C * (h * h) * h;
+    f1 = c.A1 - c.B1 * s;
     return;
   }
-  d0 = c.three * c.C * (h * h);
-  if (c.n == 3 && c.m == 2) {  // f1' = B1 / h^2
+  const MobPair<T> r = mobility_general(c, h, s);
+  f0 = r.a;
+  f1 = r.b;
+}
+template <class T>
+TF_HD void mobility_d(const MobC<T>& c, const T& h, const T& s, T& d0, T& d1) {
+  if (c.pl32) {  // f1' = B1 / h^2
+    d0 = c.three * c.C * (h * h);
     d1 = c.dB1 * (s * s);
     return;
   }
-  T b = c.dB1 * hpow_neg(h, s, c.n - 1);
-  d1 = c.m == 2 ? b : b - c.dA1 * hpow_neg(h, s, c.m - 1);
+  const MobPair<T> r = mobility_d_general(c, h, s);
+  d0 = r.a;
+  d1 = r.b;
 }
 
 TF_HD int reflect_index(int i, int n) {

@@ -33,7 +33,7 @@ static_assert(2 * 4 * 32 == kNP && 4 * kG == kRY && 4 * kG == kCX,
 // (row0, col0) into shared memory (row pitch DP elements), reflecting indices
 // at the walls.  Interior tiles whose rows are 16-byte aligned move in
 // 16-byte cp.async vectors; other tiles element by element.  Executed by the
-// producer threads.
+// producer threads; copy loops stay rolled to keep the kernels' code small.
 template <class T, int R, int C, int DP>
 __device__ __forceinline__ void copy_tile(T* dst, const T* __restrict__ src, int row0, int col0, int ny,
                                           int nx, int p) {
@@ -43,16 +43,13 @@ __device__ __forceinline__ void copy_tile(T* dst, const T* __restrict__ src, int
   if (inner && (C % V) == 0 && (DP % V) == 0 && (nx % V) == 0 &&
       (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
     constexpr int CV = C / V;
+#pragma unroll 1
     for (int k = p; k < R * CV; k += kNP) {
       const int r = k / CV, c = (k - r * CV) * V;
       __pipeline_memcpy_async(dst + r * DP + c, base + (size_t)r * nx + c, 16);
     }
-  } else if (inner) {
-    for (int k = p; k < R * C; k += kNP) {
-      const int r = k / C, c = k - r * C;
-      cpT(dst + r * DP + c, base + (size_t)r * nx + c);
-    }
   } else {
+#pragma unroll 1
     for (int k = p; k < R * C; k += kNP) {
       const int r = k / C, c = k - r * C;
       const int gj = reflect_index(row0 + r, ny), gi = reflect_index(col0 + c, nx);
@@ -73,11 +70,13 @@ __device__ __forceinline__ void copy_rows(T* dst, const T* __restrict__ src, int
   if ((C % V) == 0 && (DP % V) == 0 && col0 + C <= nx && (nx % V) == 0 &&
       (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
     constexpr int CV = C / V;
+#pragma unroll 1
     for (int k = p; k < nr * CV; k += kNP) {
       const int r = k / CV, c = (k - r * CV) * V;
       __pipeline_memcpy_async(dst + r * DP + c, base + (size_t)r * nx + c, 16);
     }
   } else {
+#pragma unroll 1
     for (int k = p; k < nr * C; k += kNP) {
       const int r = k / C, c = k - r * C;
       if (col0 + c < nx) cpT(dst + r * DP + c, base + (size_t)r * nx + c);
@@ -91,8 +90,10 @@ template <class T>
 __device__ __forceinline__ void copy_span(T* dst, const T* __restrict__ src, int n, int p) {
   constexpr int V = 16 / sizeof(T);
   if ((n % V) == 0 && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+#pragma unroll 1
     for (int k = p; k < n / V; k += kNP) __pipeline_memcpy_async(dst + k * V, src + k * V, 16);
   } else {
+#pragma unroll 1
     for (int k = p; k < n; k += kNP) cpT(dst + k, src + k);
   }
 }
@@ -125,6 +126,23 @@ __device__ __forceinline__ CellS<LP> cell_scaled(const MobC<LP>& ml, LP inv_ds2,
   return X;
 }
 
+// The same values for the (n, m) = (3, 2) power law with the constant
+// factors folded on the host (LineK): the Laplacian is left unscaled and
+// 1/ds^2 moves into D0, so faces see the same products.
+template <class LP, class Acc>
+__device__ __forceinline__ CellS<LP> cell_pl32(const LineK<LP>& L, Acc U) {
+  CellS<LP> X;
+  const LP uc = U(0, 0);
+  X.u = uc;
+  X.lap = ((U(0, 1) - uc) + (U(0, -1) - uc)) + ((U(1, 0) - uc) + (U(-1, 0) - uc));
+  const LP s = rcp(uc), h2 = uc * uc;
+  X.F0 = L.pF0 * (h2 * uc);
+  X.F1 = L.pF1a - L.pF1b * s;
+  X.D0 = L.pD0 * h2;
+  X.D1 = L.pD1 * (s * s);
+  return X;
+}
+
 template <class LP>
 __device__ __forceinline__ void face_scaled(const CellS<LP>& P, const CellS<LP>& Q, bool pl, bool qr,
                                             LP dF[4]) {
@@ -152,14 +170,20 @@ __device__ __forceinline__ void face_scaled(const CellS<LP>& P, const CellS<LP>&
 // A(s, dr, dc) is the film at line cell ia + s offset by (dr, dc) in the grid.
 // EDGE: the group may reach a wall, where the outer face of an end cell
 // vanishes and faces next to a wall lose their outer stencil weight; without
-// EDGE (ia >= 2 and ia + G + 1 < n) every face is interior.  OUT(s, a, b, c,
-// d, e) receives the row of cell ia + s.
-template <class LP, int G, bool EDGE, class Acc, class Out>
+// EDGE (ia >= 2 and ia + G + 1 < n) every face is interior.  PL32 selects
+// the folded (n, m) = (3, 2) power law.  OUT(s, a, b, c, d, e) receives the
+// row of cell ia + s.
+template <class LP, int G, bool EDGE, bool PL32, class Acc, class Out>
 __device__ __forceinline__ void band_rows(const LineK<LP>& L, Acc A, int ia, int ib, int n, Out out) {
   CellS<LP> C[G + 2];
 #pragma unroll
-  for (int s = -1; s <= G; ++s)
-    C[s + 1] = cell_scaled<LP>(L.ml, L.inv_ds2, L.k3, L.k1, [&](int dr, int dc) { return A(s, dr, dc); });
+  for (int s = -1; s <= G; ++s) {
+    auto U = [&](int dr, int dc) { return A(s, dr, dc); };
+    if constexpr (PL32)
+      C[s + 1] = cell_pl32<LP>(L, U);
+    else
+      C[s + 1] = cell_scaled<LP>(L.ml, L.inv_ds2, L.k3, L.k1, U);
+  }
   LP F[G + 1][4];
 #pragma unroll
   for (int f = 0; f <= G; ++f) {  // face between cells ia + f - 1 and ia + f
@@ -180,51 +204,43 @@ __device__ __forceinline__ void band_rows(const LineK<LP>& L, Acc A, int ia, int
 }
 
 // Forward elimination over the n cells of one chunk in the band buffer B
-// ([a..e, r][cell][line]).  REV runs the reversed band from the last cell to
-// the first (the second half of a twisted line).  SPILL(c, g, d, z) stores
-// the factors of chunk cell c.  Full chunks run unrolled so that the band
-// loads of later cells are issued ahead of the recurrence.
-template <class LP, int L, bool REV, class Spill>
+// ([a..e, r][cell][line]), cell 0 first.  The producers store both halves of
+// a twisted line in this processing order -- the second half with its band
+// reversed (e..a) and its cells from the far end -- so one code path serves
+// both solver warps.  SPILL(s, g, d, z) stores the factors of processed cell
+// s.  The loop is unrolled so that band loads run ahead of the recurrence.
+template <class LP, int L, class Spill>
 __device__ __forceinline__ void lu_chunk(LUState<LP>& lu, const LP* B, int lane, int n, Spill spill,
                                          int& bad) {
-  auto one = [&](int c) {
-    const int k = c * 32 + lane;
+#pragma unroll 8
+  for (int s = 0; s < n; ++s) {
+    const int k = s * 32 + lane;
     LP g, dl, z;
-    const bool ok =
-        REV ? lu.step(B[4 * L * 32 + k], B[3 * L * 32 + k], B[2 * L * 32 + k], B[L * 32 + k], B[k],
-                      B[5 * L * 32 + k], g, dl, z)
-            : lu.step(B[k], B[L * 32 + k], B[2 * L * 32 + k], B[3 * L * 32 + k], B[4 * L * 32 + k],
-                      B[5 * L * 32 + k], g, dl, z);
-    if (!ok) bad = 1;
-    spill(c, g, dl, z);
-  };
-  if (n == L) {
-#pragma unroll
-    for (int s = 0; s < L; ++s) one(REV ? L - 1 - s : s);
-  } else {
-    for (int s = 0; s < n; ++s) one(REV ? n - 1 - s : s);
+    if (!lu.step(B[k], B[L * 32 + k], B[2 * L * 32 + k], B[3 * L * 32 + k], B[4 * L * 32 + k],
+                 B[5 * L * 32 + k], g, dl, z))
+      bad = 1;
+    spill(s, g, dl, z);
   }
 }
 
-// Back substitution x_c = z_c - g_c x' - d_c x'' over the n cells of one
-// chunk, outward from the seam: c = n-1..0 for the first half, c = 0..n-1
-// (REV) for the second.  F(f, c) reads factor f (g, d, z) of cell c; cells
-// with IS_SEAM(c) take the seam solution XS(c); PUT(c, x) stores x.  Full
-// chunks without seam cells run unrolled.
-template <class LP, int L, bool REV, class Fac, class SeamF, class XsF, class Put>
+// Back substitution x = z - g x' - d x'' over the n cells of one chunk in
+// processing order s = 0..n-1 (outward from the seam).  F(f, s) reads factor
+// f (g, d, z) of cell s; cells with IS_SEAM(s) take the seam solution XS(s);
+// PUT(s, x) stores x.  Chunks without seam cells run unrolled.
+template <class LP, class Fac, class SeamF, class XsF, class Put>
 __device__ __forceinline__ void bs_chunk(LP& x1, LP& x2, int n, bool any_seam, Fac F, SeamF is_seam,
                                          XsF xs, Put put) {
-  auto one = [&](int c, bool chk) {
-    const LP x = (chk && is_seam(c)) ? xs(c) : F(2, c) - F(0, c) * x1 - F(1, c) * x2;
+  auto one = [&](int s, bool chk) {
+    const LP x = (chk && is_seam(s)) ? xs(s) : F(2, s) - F(0, s) * x1 - F(1, s) * x2;
     x2 = x1;
     x1 = x;
-    put(c, x);
+    put(s, x);
   };
-  if (n == L && !any_seam) {
-#pragma unroll
-    for (int s = 0; s < L; ++s) one(REV ? s : L - 1 - s, false);
+  if (!any_seam) {
+#pragma unroll 8
+    for (int s = 0; s < n; ++s) one(s, false);
   } else {
-    for (int s = 0; s < n; ++s) one(REV ? s : n - 1 - s, true);
+    for (int s = 0; s < n; ++s) one(s, true);
   }
 }
 
@@ -272,8 +288,10 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   const int i0 = blockIdx.x * 32;
   const int m = split_point<kRY>(ny);
   const bool twisted = m < ny;
-  const int nchh[2] = {(m + kRY - 1) / kRY, twisted ? (ny - m + kRY - 1) / kRY : 0};
-  const int nch = max(nchh[0], nchh[1]);
+  // chunks per half (a runtime-indexed array would live in local memory)
+  const int nch0 = (m + kRY - 1) / kRY, nch1 = twisted ? (ny - m + kRY - 1) / kRY : 0;
+  const int nch = max(nch0, nch1);
+  auto nchh = [&](int h) { return h ? nch1 : nch0; };
   auto r0_of = [&](int h, int q) { return h == 0 ? q * kRY : max(m, ny - (q + 1) * kRY); };
   auto r1_of = [&](int h, int q) { return h == 0 ? min(m, (q + 1) * kRY) : ny - q * kRY; };
   LP* fg = fac;
@@ -285,8 +303,9 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   // issue the film and w tiles of chunk q of both halves into ring slot q & 1
   auto issue_fwd = [&](int q) {
     const int slot = q & 1;
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
-      if (q >= nchh[h]) continue;
+      if (q >= nchh(h)) continue;
       const int r0 = r0_of(h, q), r1 = r1_of(h, q);
       copy_tile<LP, kRY + 4, 40, 40>(&S.s.f.ut[slot][h][0][0], ul, r0 - 2, i0 - 4, ny, nx, p);
       copy_rows<LP, kRY, 32, 32>(&S.s.f.wt[slot][h][0][0], w, r0, i0, r1 - r0, nx, p);
@@ -310,46 +329,54 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
         // band rows: thread p builds rows ja..jb-1 of column c of half h
         {
           const int h = p >> 7, g = (p >> 5) & 3, c = p & 31;
-          if (t < nchh[h] && i0 + c < nx) {
+          if (t < nchh(h) && i0 + c < nx) {
             const int r0 = r0_of(h, t), r1 = r1_of(h, t);
             const int ja = r0 + kG * g, jb = min(r1, ja + kG);
             if (ja < jb) {
+              // band in the solver's processing order (see lu_chunk)
               LP* B = &S.s.f.band[t & 1][h][0][0][0];
+              LP* Ba = B + (h ? 4 : 0) * kRY * 32;
+              LP* Bb = B + (h ? 3 : 1) * kRY * 32;
+              LP* Bd = B + (h ? 1 : 3) * kRY * 32;
+              LP* Be = B + (h ? 0 : 4) * kRY * 32;
               const LP* T = &S.s.f.ut[slot][h][ja - r0 + 2][c + 4];  // cell ja in the tile
               auto A = [&](int s, int dr, int dc) { return T[(s + dr) * 40 + dc]; };
               auto out = [&](int s, LP a, LP b, LP cc, LP d, LP e) {
-                const int k = (ja - r0 + s) * 32 + c;
-                B[0 * kRY * 32 + k] = a;
-                B[1 * kRY * 32 + k] = b;
+                const int j = ja + s;
+                const int k = (h ? r1 - 1 - j : j - r0) * 32 + c;
+                Ba[k] = a;
+                Bb[k] = b;
                 B[2 * kRY * 32 + k] = cc;
-                B[3 * kRY * 32 + k] = d;
-                B[4 * kRY * 32 + k] = e;
-                B[5 * kRY * 32 + k] = S.s.f.wt[slot][h][ja - r0 + s][c];
+                Bd[k] = d;
+                Be[k] = e;
+                B[5 * kRY * 32 + k] = S.s.f.wt[slot][h][j - r0][c];
               };
-              if (ja >= 2 && ja + kG + 1 < ny)
-                band_rows<LP, kG, false>(L, A, ja, jb, ny, out);
+              const bool edge = !(ja >= 2 && ja + kG + 1 < ny);
+              if (!L.ml.pl32)  // general exponents or the linear model
+                band_rows<LP, kG, true, false>(L, A, ja, jb, ny, out);
+              else if (!edge)
+                band_rows<LP, kG, false, true>(L, A, ja, jb, ny, out);
               else
-                band_rows<LP, kG, true>(L, A, ja, jb, ny, out);
+                band_rows<LP, kG, true, true>(L, A, ja, jb, ny, out);
             }
           }
         }
       }
     } else if (t >= 1) {
       const int q = t - 1, h = warp;
-      if (q < nchh[h] && i0 + lane < nx) {
+      if (q < nchh(h) && i0 + lane < nx) {
         const int r0 = r0_of(h, q), r1 = r1_of(h, q);
         const LP* B = &S.s.f.band[q & 1][h][0][0][0];
         const int col = i0 + lane;
-        auto spill = [&](int c, LP g, LP dl, LP z) {
-          const size_t idx = (size_t)(r0 + c) * nx + col;
+        // processed cell s is row r0 + s (top half) or r1 - 1 - s (bottom)
+        const int jb = h ? r1 - 1 : r0, js = h ? -1 : 1;
+        auto spill = [&](int s, LP g, LP dl, LP z) {
+          const size_t idx = (size_t)(jb + js * s) * nx + col;
           fg[idx] = g;
           fd[idx] = dl;
           fz[idx] = z;
         };
-        if (h == 0)
-          lu_chunk<LP, kRY, false>(lu, B, lane, r1 - r0, spill, pivot_bad);
-        else
-          lu_chunk<LP, kRY, true>(lu, B, lane, r1 - r0, spill, pivot_bad);
+        lu_chunk<LP, kRY>(lu, B, lane, r1 - r0, spill, pivot_bad);
       }
     }
     __syncthreads();
@@ -366,21 +393,24 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   __syncthreads();
 
   // ---------------- backward ticks ----------------
-  // chunk order: b-th backward chunk of half h is chunk nchh[h]-1-b.
+  // chunk order: b-th backward chunk of half h is chunk nchh(h)-1-b.
   auto issue_bwd_f = [&](int bq) {  // factor tiles of backward chunk bq
     const int slot = bq % 3;
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
-      const int q = nchh[h] - 1 - bq;
+      const int q = nchh(h) - 1 - bq;
       if (q < 0) continue;
       const int r0 = r0_of(h, q), r1 = r1_of(h, q);
+#pragma unroll 1
       for (int f = 0; f < 3; ++f)
         copy_rows<LP, kRY, 32, 32>(&S.s.b.ft[slot][h][f][0][0], fac + (size_t)f * N, r0, i0, r1 - r0, nx, p);
     }
   };
   auto issue_bwd_u = [&](int bq) {  // u_k tiles of backward chunk bq
     const int slot = bq % 3;
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
-      const int q = nchh[h] - 1 - bq;
+      const int q = nchh(h) - 1 - bq;
       if (q < 0) continue;
       const int r0 = r0_of(h, q), r1 = r1_of(h, q);
       copy_rows<double, kRY, 32, 32>(&S.s.b.ukt[slot][h][0][0], u, r0, i0, r1 - r0, nx, p);
@@ -415,52 +445,50 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   for (int t = 0; t <= nch; ++t) {
     if (solver) {
       if (t < nch) {
-        const int h = warp, q = nchh[h] - 1 - t;
+        const int h = warp, q = nchh(h) - 1 - t;
         if (q >= 0 && i0 + lane < nx) {
           const int r0 = r0_of(h, q), r1 = r1_of(h, q);
           const int slot = t % 3;
           LP* X = &S.s.b.xb[t & 1][h][0][0];
-          auto F = [&](int f, int c) { return S.s.b.ft[slot][h][f][c][lane]; };
-          auto xs = [&](int c) { return S.xs[lane][r0 + c - (m - 2)]; };
-          auto put = [&](int c, LP x) { X[c * 32 + lane] = x; };
-          if (h == 0)
-            bs_chunk<LP, kRY, false>(x1, x2, r1 - r0, twisted && r1 > m - 2, F,
-                                     [&](int c) { return twisted && r0 + c >= m - 2; }, xs, put);
-          else
-            bs_chunk<LP, kRY, true>(x1, x2, r1 - r0, r0 <= m + 1, F,
-                                    [&](int c) { return r0 + c <= m + 1; }, xs, put);
+          // processed cell s is chunk row n-1-s (top half, upward) or s
+          const int n = r1 - r0, rb = h ? 0 : n - 1, rs = h ? 1 : -1;
+          auto F = [&](int f, int s) { return S.s.b.ft[slot][h][f][rb + rs * s][lane]; };
+          auto xs = [&](int s) { return S.xs[lane][r0 + rb + rs * s - (m - 2)]; };
+          auto put = [&](int s, LP x) { X[(rb + rs * s) * 32 + lane] = x; };
+          auto is_seam = [&](int s) {
+            const int j = r0 + rb + rs * s;
+            return twisted && (h ? j <= m + 1 : j >= m - 2);
+          };
+          bs_chunk<LP>(x1, x2, n, twisted && (h ? r0 <= m + 1 : r1 > m - 2), F, is_seam, xs, put);
         }
       }
     } else {
       // finish backward chunk t-1: update, store, reduce
       if (t >= 1) {
         const int bq = t - 1, slot = bq % 3;
-        for (int h = 0; h < 2; ++h) {
-          const int q = nchh[h] - 1 - bq;
+        // 2 * kRY * 32 cells of both halves over the producers, one body
+        // (unrolled twice) so that the update's code stays small
+#pragma unroll 2
+        for (int k2 = p; k2 < 2 * kRY * 32; k2 += kNP) {
+          const int h = k2 >= kRY * 32 ? 1 : 0, k = k2 - h * kRY * 32;
+          const int q = nchh(h) - 1 - bq;
           if (q < 0) continue;
-          const int r0 = r0_of(h, q), r1 = r1_of(h, q);
-          const LP* X = &S.s.b.xb[bq & 1][h][0][0];
-#pragma unroll
-          for (int e = 0; e < (kRY * 32 + kNP - 1) / kNP; ++e) {
-            const int k = p + e * kNP;
-            if (k >= kRY * 32) continue;
-            const int r = k >> 5, c = k & 31;
-            const int j = r0 + r, col = i0 + c;
-            if (j >= r1 || col >= nx) continue;
-            const LP x = X[k];
-            const double uk = S.s.b.ukt[slot][h][r][c];
-            double un;
-            if constexpr (sizeof(LP) == 8)
-              un = uk + (double)x;
-            else
-              un = f64_add_f32(uk, (float)x);
-            const size_t idx = (size_t)j * nx + col;
-            unew[idx] = un;
-            if (vout) vout[idx] = to_f64(x);
-            LP ru = rel_update(x, uk);
-            if (!(ru <= err)) err = ru;
-            if (!positive_finite_bits(un)) nonfinite = 1;
-          }
+          const int r = k >> 5, c = k & 31;
+          const int j = r0_of(h, q) + r, col = i0 + c;
+          if (j >= r1_of(h, q) || col >= nx) continue;
+          const LP x = S.s.b.xb[bq & 1][h][r][c];
+          const double uk = S.s.b.ukt[slot][h][r][c];
+          double un;
+          if constexpr (sizeof(LP) == 8)
+            un = uk + (double)x;
+          else
+            un = f64_add_f32(uk, (float)x);
+          const size_t idx = (size_t)j * nx + col;
+          unew[idx] = un;
+          if (vout) vout[idx] = to_f64(x);
+          LP ru = rel_update(x, uk);
+          if (!(ru <= err)) err = ru;
+          if (!positive_finite_bits(un)) nonfinite = 1;
         }
       }
       // prefetch: factors two chunks ahead, u_k one chunk ahead of the solvers
@@ -543,8 +571,9 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   const int j0 = blockIdx.x * 32;
   const int m = split_point<kCX>(nx);
   const bool twisted = m < nx;
-  const int nchh[2] = {(m + kCX - 1) / kCX, twisted ? (nx - m + kCX - 1) / kCX : 0};
-  const int nch = max(nchh[0], nchh[1]);
+  const int nch0 = (m + kCX - 1) / kCX, nch1 = twisted ? (nx - m + kCX - 1) / kCX : 0;
+  const int nch = max(nch0, nch1);
+  auto nchh = [&](int h) { return h ? nch1 : nch0; };
   auto c0_of = [&](int h, int q) { return h == 0 ? q * kCX : max(m, nx - (q + 1) * kCX); };
   auto c1_of = [&](int h, int q) { return h == 0 ? min(m, (q + 1) * kCX) : nx - q * kCX; };
   LP* facb = fac + (size_t)blockIdx.x * 3 * nx * 32;
@@ -552,10 +581,12 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
 
   auto issue_fwd = [&](int q) {
     const int slot = q & 1;
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
-      if (q >= nchh[h]) continue;
+      if (q >= nchh(h)) continue;
       const int c0 = c0_of(h, q), c1 = c1_of(h, q);
       copy_tile<LP, 34, kCX + 4, kCX + 5>(&S.s.f.ut[slot][h][0][0], ul, j0 - 1, c0 - 2, ny, nx, p);
+#pragma unroll 1
       for (int k = p; k < 32 * kCX; k += kNP) {
         int r = k / kCX, c = k - r * kCX;
         if (j0 + r < ny && c0 + c < c1) cpT(&S.s.f.rt[slot][h][r][c], rw + (size_t)(j0 + r) * nx + c0 + c);
@@ -578,48 +609,56 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
         // band rows: thread p builds rows ia..ib-1 of row r of half h
         {
           const int h = p >> 7, g = (p >> 5) & 3, r = p & 31;
-          if (t < nchh[h] && j0 + r < ny) {
+          if (t < nchh(h) && j0 + r < ny) {
             const int c0 = c0_of(h, t), c1 = c1_of(h, t);
             const int ia = c0 + kG * g, ib = min(c1, ia + kG);
             if (ia < ib) {
+              // band in the solver's processing order (see lu_chunk)
               LP* B = &S.s.f.band[t & 1][h][0][0][0];
+              LP* Ba = B + (h ? 4 : 0) * kCX * 32;
+              LP* Bb = B + (h ? 3 : 1) * kCX * 32;
+              LP* Bd = B + (h ? 1 : 3) * kCX * 32;
+              LP* Be = B + (h ? 0 : 4) * kCX * 32;
               const LP* T = &S.s.f.ut[slot][h][r + 1][ia - c0 + 2];  // cell ia in the tile
               auto A = [&](int s, int dr, int dc) { return T[dr * (kCX + 5) + s + dc]; };
               auto out = [&](int s, LP a, LP b, LP c, LP d, LP e) {
-                const int k = (ia - c0 + s) * 32 + r;
-                B[0 * kCX * 32 + k] = a;
-                B[1 * kCX * 32 + k] = b;
+                const int i = ia + s;
+                const int k = (h ? c1 - 1 - i : i - c0) * 32 + r;
+                Ba[k] = a;
+                Bb[k] = b;
                 B[2 * kCX * 32 + k] = c;
-                B[3 * kCX * 32 + k] = d;
-                B[4 * kCX * 32 + k] = e;
-                B[5 * kCX * 32 + k] = S.s.f.rt[slot][h][r][ia - c0 + s];
+                Bd[k] = d;
+                Be[k] = e;
+                B[5 * kCX * 32 + k] = S.s.f.rt[slot][h][r][i - c0];
               };
-              if (ia >= 2 && ia + kG + 1 < nx)
-                band_rows<LP, kG, false>(L, A, ia, ib, nx, out);
+              const bool edge = !(ia >= 2 && ia + kG + 1 < nx);
+              if (!L.ml.pl32)  // general exponents or the linear model
+                band_rows<LP, kG, true, false>(L, A, ia, ib, nx, out);
+              else if (!edge)
+                band_rows<LP, kG, false, true>(L, A, ia, ib, nx, out);
               else
-                band_rows<LP, kG, true>(L, A, ia, ib, nx, out);
+                band_rows<LP, kG, true, true>(L, A, ia, ib, nx, out);
             }
           }
         }
       }
     } else if (t >= 1) {
       const int q = t - 1, h = warp;
-      if (q < nchh[h] && j0 + lane < ny) {
+      if (q < nchh(h) && j0 + lane < ny) {
         const int c0 = c0_of(h, q), c1 = c1_of(h, q);
         const LP* B = &S.s.f.band[q & 1][h][0][0][0];
         LP* fg = facb;
         LP* fd = facb + (size_t)nx * 32;
         LP* fz = facb + (size_t)2 * nx * 32;
-        auto spill = [&](int c, LP g, LP dl, LP z) {
-          const size_t o = (size_t)(c0 + c) * 32 + lane;
+        // processed cell s is column c0 + s (left half) or c1 - 1 - s (right)
+        const int ib = h ? c1 - 1 : c0, is = h ? -1 : 1;
+        auto spill = [&](int s, LP g, LP dl, LP z) {
+          const size_t o = (size_t)(ib + is * s) * 32 + lane;
           fg[o] = g;
           fd[o] = dl;
           fz[o] = z;
         };
-        if (h == 0)
-          lu_chunk<LP, kCX, false>(lu, B, lane, c1 - c0, spill, pivot_bad);
-        else
-          lu_chunk<LP, kCX, true>(lu, B, lane, c1 - c0, spill, pivot_bad);
+        lu_chunk<LP, kCX>(lu, B, lane, c1 - c0, spill, pivot_bad);
       }
     }
     __syncthreads();
@@ -635,10 +674,12 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   __syncthreads();
   auto issue_bwd = [&](int bq) {
     const int slot = bq % 3;
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
-      const int q = nchh[h] - 1 - bq;
+      const int q = nchh(h) - 1 - bq;
       if (q < 0) continue;
       const int c0 = c0_of(h, q), c1 = c1_of(h, q);
+#pragma unroll 1
       for (int f = 0; f < 3; ++f)
         copy_span<LP>(&S.s.b.ft[slot][h][f][0][0], facb + ((size_t)f * nx + c0) * 32, (c1 - c0) * 32, p);
     }
@@ -664,28 +705,31 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   for (int t = 0; t <= nch; ++t) {
     if (solver) {
       if (t < nch) {
-        const int h = warp, q = nchh[h] - 1 - t;
+        const int h = warp, q = nchh(h) - 1 - t;
         if (q >= 0 && j0 + lane < ny) {
           const int c0 = c0_of(h, q), c1 = c1_of(h, q);
           const int slot = t % 3;
-          auto F = [&](int f, int c) { return S.s.b.ft[slot][h][f][c][lane]; };
-          auto xs = [&](int c) { return S.xs[lane][c0 + c - (m - 2)]; };
-          auto put = [&](int c, LP x) { S.s.b.xb[t & 1][h][c][lane] = x; };
-          if (h == 0)
-            bs_chunk<LP, kCX, false>(x1, x2, c1 - c0, twisted && c1 > m - 2, F,
-                                     [&](int c) { return twisted && c0 + c >= m - 2; }, xs, put);
-          else
-            bs_chunk<LP, kCX, true>(x1, x2, c1 - c0, c0 <= m + 1, F,
-                                    [&](int c) { return c0 + c <= m + 1; }, xs, put);
+          // processed cell s is chunk column n-1-s (left half, leftward) or s
+          const int n = c1 - c0, cb = h ? 0 : n - 1, cs = h ? 1 : -1;
+          auto F = [&](int f, int s) { return S.s.b.ft[slot][h][f][cb + cs * s][lane]; };
+          auto xs = [&](int s) { return S.xs[lane][c0 + cb + cs * s - (m - 2)]; };
+          auto put = [&](int s, LP x) { S.s.b.xb[t & 1][h][cb + cs * s][lane] = x; };
+          auto is_seam = [&](int s) {
+            const int i = c0 + cb + cs * s;
+            return twisted && (h ? i <= m + 1 : i >= m - 2);
+          };
+          bs_chunk<LP>(x1, x2, n, twisted && (h ? c0 <= m + 1 : c1 > m - 2), F, is_seam, xs, put);
         }
       }
     } else {
       if (t >= 1) {  // store w of backward chunk t-1, coalesced along rows
         const int bq = t - 1;
+#pragma unroll 1
         for (int h = 0; h < 2; ++h) {
-          const int q = nchh[h] - 1 - bq;
+          const int q = nchh(h) - 1 - bq;
           if (q < 0) continue;
           const int c0 = c0_of(h, q), c1 = c1_of(h, q);
+#pragma unroll 1
           for (int k = p; k < 32 * kCX; k += kNP) {
             int r = k / kCX, c = k - r * kCX;
             if (j0 + r < ny && c0 + c < c1) rw[(size_t)(j0 + r) * nx + c0 + c] = S.s.b.xb[bq & 1][h][c][r];

@@ -267,7 +267,6 @@ TF_HD double f64_add_f32(double u, float v) {
   const int shift = ev - eu + 925;  // (ev - 150) - (eu - 1075)
   if (eu == 0 || eu == 0x7ff || ev == 0xff || shift > 37) return u + f64_of_f32(v);
   int64_t mu = (int64_t)((ub & 0xfffffffffffffull) | 0x10000000000000ull);
-  if (ub >> 63) mu = -mu;
   uint64_t av = (uint64_t)((vb & 0x7fffffu) | 0x800000u);
   if (shift >= 0) {
     av <<= shift;
@@ -276,7 +275,17 @@ TF_HD double f64_add_f32(double u, float v) {
   } else {
     av = 0;
   }
-  const int64_t S = mu + ((vb >> 31) ? -(int64_t)av : (int64_t)av);
+  const int64_t sv = (vb >> 31) ? -(int64_t)av : (int64_t)av;
+  if ((ub >> 63) == 0) {
+    // u > 0 and the sum stays in u's binade (the usual Newton update): the
+    // significand sum is the result's significand, exactly
+    const int64_t S0 = mu + sv;
+    if ((S0 >> 52) == 1)
+      return double_of((ub & 0xfff0000000000000ull) | ((uint64_t)S0 & 0xfffffffffffffull));
+  } else {
+    mu = -mu;
+  }
+  const int64_t S = mu + sv;
   if (S == 0) return 0.0;
   const uint64_t sgn = S < 0 ? 0x8000000000000000ull : 0ull;
   uint64_t mag = (uint64_t)(S < 0 ? -S : S);
