@@ -479,10 +479,12 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
           const LP x = S.s.b.xb[bq & 1][h][r][c];
           const double uk = S.s.b.ukt[slot][h][r][c];
           double un;
+          // one native FP64 add per cell (correctly rounded); the exact
+          // integer widening keeps the conversion off the FP64 pipe
           if constexpr (sizeof(LP) == 8)
             un = uk + (double)x;
           else
-            un = f64_add_f32(uk, (float)x);
+            un = uk + f64_of_f32((float)x);
           const size_t idx = (size_t)j * nx + col;
           unew[idx] = un;
           if (vout) vout[idx] = to_f64(x);

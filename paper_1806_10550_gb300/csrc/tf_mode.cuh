@@ -26,20 +26,22 @@ template <class Mode> struct Launch {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     if ((e = cudaFuncSetAttribute(k_stencil<Mode, 0>, A, (int)smem_stencil))) return e;
     if ((e = cudaFuncSetAttribute(k_stencil<Mode, 1>, A, (int)smem_stencil))) return e;
-    if ((e = cudaFuncSetAttribute(k_rhs<Mode>, A, (int)smem_rhs))) return e;
+    if ((e = cudaFuncSetAttribute(k_rhs<Mode, false>, A, (int)smem_rhs))) return e;
+    if ((e = cudaFuncSetAttribute(k_rhs<Mode, true>, A, (int)smem_rhs))) return e;
     if ((e = cudaFuncSetAttribute(k_xsweep<Mode>, A, (int)smem_x))) return e;
     if ((e = cudaFuncSetAttribute(k_ysweep<Mode>, A, (int)smem_y))) return e;
     // the sweeps run two blocks per SM only with the largest shared carveout
     const cudaFuncAttribute C = cudaFuncAttributePreferredSharedMemoryCarveout;
     if ((e = cudaFuncSetAttribute(k_xsweep<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if ((e = cudaFuncSetAttribute(k_ysweep<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
-    return cudaFuncSetAttribute(k_rhs<Mode>, C, (int)cudaSharedmemCarveoutMaxShared);
+    if ((e = cudaFuncSetAttribute(k_rhs<Mode, true>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+    return cudaFuncSetAttribute(k_rhs<Mode, false>, C, (int)cudaSharedmemCarveoutMaxShared);
   }
 
   static cudaError_t explicit_part_c(tf_ctx& c, const double* u_old, double dt) {
-    dim3 grid(c.grid_st_x, c.grid_st_y), block(16, 16);
-    k_stencil<Mode, 0><<<grid, block, smem_stencil, c.stream>>>(c.mk, step(c, dt), u_old, (HP*)c.bn,
-                                                                nullptr, nullptr);
+    dim3 grid(c.grid_rx, c.grid_ry);
+    k_rhs<Mode, true><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old,
+                                                         (HP*)c.bn, nullptr, nullptr, nullptr);
     return cudaGetLastError();
   }
   static cudaError_t residual_c(tf_ctx& c, const double* u_k, double dt, double* G) {
@@ -50,8 +52,8 @@ template <class Mode> struct Launch {
   }
   static cudaError_t rhs_c(tf_ctx& c, const double* u_k, double dt) {
     dim3 grid(c.grid_rx, c.grid_ry);
-    k_rhs<Mode><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k,
-                                                   (const HP*)c.bn, (LP*)c.w,
+    k_rhs<Mode, false><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k,
+                                                   (HP*)c.bn, (LP*)c.w,
                                                    (LP*)c.ulp, c.px);
     return cudaGetLastError();
   }

@@ -53,10 +53,13 @@ template <class HP, int T> struct RhsSmem {
   HP fx[T][T + 1], fy[T + 1][T];
 };
 
-template <class Mode>
-__global__ void __launch_bounds__(256)
+// EXPL = false: the residual pass of one Newton iteration.  EXPL = true: the
+// explicit part b^n = u^n - (1 - theta) dt D(u^n) of a step (eq.
+// CrankNicolson), written to bn in HP; rhs, ul and part are unused.
+template <class Mode, bool EXPL>
+__global__ void __launch_bounds__(256, 4)  // shared memory allows 4 blocks per SM: up to 64 registers
     k_rhs(ModelK M, RhsK<typename Mode::HP> RK, const double* __restrict__ u,
-          const typename Mode::HP* __restrict__ bn,
+          typename Mode::HP* __restrict__ bn,
           typename Mode::LP* __restrict__ rhs, typename Mode::LP* __restrict__ ul,
           PartX* __restrict__ part) {
   typedef typename Mode::HP HP;
@@ -121,6 +124,10 @@ __global__ void __launch_bounds__(256)
     if (gj < M.ny && gi < M.nx) {
       const size_t idx = (size_t)gj * M.nx + gi;
       HP dp = hp_add(hp_sub(S.fx[r][c + 1], S.fx[r][c]), hp_sub(S.fy[r + 1][c], S.fy[r][c]));
+      if constexpr (EXPL) {  // gscale holds (1 - theta) dt / (2 ds^2)
+        bn[idx] = hp_norm(hp_sub(S.u[r + 2][c + 2], hp_mul(gscale, dp)));
+        continue;
+      }
       HP Gv = hp_norm(hp_add(hp_sub(S.u[r + 2][c + 2], bn[idx]), hp_mul(gscale, dp)));
       LP gl = to_lp<LP, HP>(Gv);
       rhs[idx] = -gl;
@@ -131,6 +138,7 @@ __global__ void __launch_bounds__(256)
       if (!(ag <= g)) g = ag;
     }
   }
+  if constexpr (EXPL) return;
   for (int o = 16; o > 0; o >>= 1) {
     LP g2 = __shfl_xor_sync(0xffffffffu, g, o);
     if (!(g2 <= g)) g = g2;
