@@ -54,7 +54,7 @@ int iterate(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_o
   if (tm) TF_CK(cudaEventRecord(c.ev[3], c.stream));
   TF_CK(c.ops->ysweep(c, u_k, dt, u_next, v_out));
   if (tm) TF_CK(cudaEventRecord(c.ev[4], c.stream));
-  int r = finalize(c, c.grid_rx * c.grid_ry + c.grid_x, c.grid_y);
+  int r = finalize(c, c.n_rhs_parts + c.grid_x, c.grid_y);
   if (r) return r;
   if (tm) {
     c.timing.rhs_ms += elapsed(c.ev[0], c.ev[1]);
@@ -262,6 +262,10 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   c->grid_y = (p->nx + 31) / 32;
   c->grid_rx = (p->nx + 31) / 32;
   c->grid_ry = (p->ny + 31) / 32;
+  c->grid_pkx = (p->nx + 63) / 64;
+  c->grid_pky = (p->ny + 31) / 32;
+  c->packed_rhs = p->precision != TF_FP64 && p->model == TF_MODEL_POWERLAW && p->n == 3 && p->m == 2;
+  c->n_rhs_parts = c->packed_rhs ? c->grid_pkx * c->grid_pky : c->grid_rx * c->grid_ry;
   c->grid_st_x = (p->nx + 15) / 16;
   c->grid_st_y = (p->ny + 15) / 16;
   c->grid_stats = 304;

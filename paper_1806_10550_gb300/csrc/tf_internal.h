@@ -43,6 +43,9 @@ struct tf_ctx {
   int grid_x;      // blocks of the x sweep (32 rows each)
   int grid_y;      // blocks of the y sweep (32 columns each)
   int grid_rx, grid_ry;      // 2-D residual grid (32 x 32 tiles)
+  int grid_pkx, grid_pky;    // packed FP32-bulk residual grid (64 x 32 tiles)
+  bool packed_rhs;           // FP32-bulk with the (3, 2) power law: packed residual kernel
+  int n_rhs_parts;           // partial results written by the residual kernel in use
   int grid_st_x, grid_st_y;  // 2-D stencil grid (16 x 16 tiles)
   int grid_stats;  // blocks of k_grid_stats
   void* bn;        // explicit part b^n, HP storage

@@ -2,7 +2,10 @@
 // tf_mode_fp64.cu and once by tf_mode_f32b.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "tf_internal.h"
+#include "tf_rhs_packed.cuh"
 
 namespace tf {
 
@@ -11,6 +14,7 @@ template <class Mode> struct Launch {
   typedef typename Mode::LP LP;
   static constexpr size_t smem_stencil = sizeof(StencilSmem<HP, 16, 16>);
   static constexpr size_t smem_rhs = sizeof(RhsSmem<HP, 32>);
+  static constexpr bool kF32B = std::is_same<Mode, ModeF32B>::value;
   static constexpr size_t smem_x = sizeof(XSmem<LP>);
   static constexpr size_t smem_y = sizeof(YSmem<LP>);
 
@@ -35,10 +39,24 @@ template <class Mode> struct Launch {
     if ((e = cudaFuncSetAttribute(k_xsweep<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if ((e = cudaFuncSetAttribute(k_ysweep<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if ((e = cudaFuncSetAttribute(k_rhs<Mode, true>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+    if constexpr (kF32B) {
+      const int sp = (int)sizeof(RhsPackedSmem);
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<false>, A, sp))) return e;
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<true>, A, sp))) return e;
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<false>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<true>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+    }
     return cudaFuncSetAttribute(k_rhs<Mode, false>, C, (int)cudaSharedmemCarveoutMaxShared);
   }
 
   static cudaError_t explicit_part_c(tf_ctx& c, const double* u_old, double dt) {
+    if constexpr (kF32B) {
+      if (c.packed_rhs) {
+        k_rhs_packed<true><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
+            c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, nullptr, nullptr, nullptr);
+        return cudaGetLastError();
+      }
+    }
     dim3 grid(c.grid_rx, c.grid_ry);
     k_rhs<Mode, true><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old,
                                                          (HP*)c.bn, nullptr, nullptr, nullptr);
@@ -51,6 +69,13 @@ template <class Mode> struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t rhs_c(tf_ctx& c, const double* u_k, double dt) {
+    if constexpr (kF32B) {
+      if (c.packed_rhs) {
+        k_rhs_packed<false><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
+            c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px);
+        return cudaGetLastError();
+      }
+    }
     dim3 grid(c.grid_rx, c.grid_ry);
     k_rhs<Mode, false><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k,
                                                    (HP*)c.bn, (LP*)c.w,
@@ -65,7 +90,7 @@ template <class Mode> struct Launch {
   static cudaError_t xsweep_c(tf_ctx& c, double dt, const double* u_k) {
     k_xsweep<Mode><<<c.grid_x, kSweepThreads, smem_x, c.stream>>>(c.mk, line_consts<LP>(c.mk, step(c, dt)),
                                                        film_lp(c, u_k), (LP*)c.w,
-                                                       (LP*)c.fac_x, c.px + c.grid_rx * c.grid_ry);
+                                                       (LP*)c.fac_x, c.px + c.n_rhs_parts);
     return cudaGetLastError();
   }
   static cudaError_t ysweep_c(tf_ctx& c, const double* u_k, double dt, double* u_next,

@@ -1,0 +1,298 @@
+// tf_rhs_packed.cuh -- the FP32-bulk residual kernel on packed FP32x2 pipes.
+//
+// Same computation as k_rhs<ModeF32B> (tf_sweeps.cuh): the residual
+// G = u_k + theta dt D(u_k) - b^n of eq. CrankNicolson in double-float,
+// with D the flux-form operator of Sec. Flux Discretization, or the explicit
+// part b^n = u^n - (1 - theta) dt D(u^n).  Each thread carries two
+// horizontally adjacent cells through every double-float operation, one
+// lane each of the sm_100+ paired FP32 instructions (add/mul/fma on float2),
+// in the same per-lane operation order as the scalar double-float code, so
+// the results are the scalar kernel's bit for bit.  Shared memory holds the
+// high and low parts in separate planes, so a pair of cells is one 8-byte
+// load.  Used for the (n, m) = (3, 2) power law; other models take the scalar
+// kernel.
+#pragma once
+
+#include "tf_sweeps.cuh"
+
+namespace tf {
+
+// ---------------------------------------------------------------------------
+// packed double-float: lane-wise the operations of tf_numeric.cuh
+
+struct df2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, p_neg(b)); }
+__device__ __forceinline__ float2 p_splat(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ void p_two_sum(float2 a, float2 b, float2& s, float2& e) {
+  s = p_add(a, b);
+  const float2 bb = p_sub(s, a);
+  e = p_add(p_sub(a, p_sub(s, bb)), p_sub(b, bb));
+}
+__device__ __forceinline__ void p_fast_two_sum(float2 a, float2 b, float2& s, float2& e) {
+  s = p_add(a, b);
+  e = p_sub(b, p_sub(s, a));
+}
+__device__ __forceinline__ df2 d2(float2 hi, float2 lo) {
+  df2 r;
+  r.hi = hi;
+  r.lo = lo;
+  return r;
+}
+__device__ __forceinline__ df2 d2_splat(df64 a) { return d2(p_splat(a.hi), p_splat(a.lo)); }
+__device__ __forceinline__ df2 d2_neg(df2 a) { return d2(p_neg(a.hi), p_neg(a.lo)); }
+// lazy (unnormalised) add / multiply and the fold: df_add_u, df_mul_u, df_norm
+__device__ __forceinline__ df2 d2_add_u(df2 a, df2 b) {
+  float2 s, e;
+  p_two_sum(a.hi, b.hi, s, e);
+  return d2(s, p_add(e, p_add(a.lo, b.lo)));
+}
+__device__ __forceinline__ df2 d2_sub_u(df2 a, df2 b) { return d2_add_u(a, d2_neg(b)); }
+__device__ __forceinline__ df2 d2_mul_u(df2 a, df2 b) {
+  const float2 p = p_mul(a.hi, b.hi);
+  float2 e = p_fma(a.hi, b.hi, p_neg(p));
+  e = p_fma(a.hi, b.lo, e);
+  e = p_fma(a.lo, b.hi, e);
+  return d2(p, e);
+}
+__device__ __forceinline__ df2 d2_norm(df2 a) {
+  float2 s, e;
+  p_fast_two_sum(a.hi, a.lo, s, e);
+  return d2(s, e);
+}
+// normalised add / multiply: operator+ and operator* of df64
+__device__ __forceinline__ df2 d2_add(df2 a, df2 b) {
+  float2 s, e;
+  p_two_sum(a.hi, b.hi, s, e);
+  e = p_add(e, p_add(a.lo, b.lo));
+  p_fast_two_sum(s, e, s, e);
+  return d2(s, e);
+}
+__device__ __forceinline__ df2 d2_sub(df2 a, df2 b) { return d2_add(a, d2_neg(b)); }
+__device__ __forceinline__ df2 d2_mul(df2 a, df2 b) {
+  float2 p = p_mul(a.hi, b.hi);
+  float2 e = p_fma(a.hi, b.hi, p_neg(p));
+  e = p_fma(a.hi, b.lo, e);
+  e = p_fma(a.lo, b.hi, e);
+  p_fast_two_sum(p, e, p, e);
+  return d2(p, e);
+}
+// 1/a as df_rcp: the correctly rounded float reciprocal (what 1.0f / x
+// gives), refined by one double-float Newton step
+__device__ __forceinline__ df2 d2_rcp(df2 a) {
+  const df2 Y = d2(make_float2(__frcp_rn(a.hi.x), __frcp_rn(a.hi.y)), p_splat(0.0f));
+  const df2 r = d2_sub(d2(p_splat(1.0f), p_splat(0.0f)), d2_mul(a, Y));
+  return d2_add(Y, d2_mul(Y, r));
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+
+constexpr int kPR = 32;   // tile rows
+constexpr int kPC = 64;   // tile columns
+constexpr int kPT = 512;  // threads
+
+struct RhsPackedSmem {
+  float uh[kPR + 4][kPC + 8], ul[kPR + 4][kPC + 8];  // film, cols x0-4 ..
+  float laph[kPR + 2][kPC + 4], lapl[kPR + 2][kPC + 4];  // cell values, cols x0-2 ..
+  float f0h[kPR + 2][kPC + 4], f0l[kPR + 2][kPC + 4];
+  float f1h[kPR + 2][kPC + 4], f1l[kPR + 2][kPC + 4];
+  float fxh[kPR][kPC + 2], fxl[kPR][kPC + 2];  // face kf: cells x0-2+kf | x0-1+kf
+  float fyh[kPR + 1][kPC], fyl[kPR + 1][kPC];  // face k: rows j0-1+k | j0+k
+};
+
+// load the pair of plane entries at (row, even col)
+template <int W>
+__device__ __forceinline__ df2 ld2(const float (&h)[W], const float (&l)[W], int c) {
+  return d2(*reinterpret_cast<const float2*>(&h[c]), *reinterpret_cast<const float2*>(&l[c]));
+}
+template <int W>
+__device__ __forceinline__ void st2(float (&h)[W], float (&l)[W], int c, df2 v) {
+  *reinterpret_cast<float2*>(&h[c]) = v.hi;
+  *reinterpret_cast<float2*>(&l[c]) = v.lo;
+}
+// the odd-offset pair (A.y, B.x) of two consecutive aligned pairs
+__device__ __forceinline__ df2 mid2(df2 A, df2 B) {
+  return d2(make_float2(A.hi.y, B.hi.x), make_float2(A.lo.y, B.lo.x));
+}
+
+template <bool EXPL>
+__global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per SM: up to 64 registers
+    k_rhs_packed(ModelK M, RhsK<df64> RK, const double* __restrict__ u, df64* __restrict__ bn,
+                 float* __restrict__ rhs, float* __restrict__ ulp, PartX* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RhsPackedSmem& S = *reinterpret_cast<RhsPackedSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kPC, j0 = blockIdx.y * kPR;
+  const int nx = M.nx, ny = M.ny;
+  // b^n of this thread's stage-4 cells, loaded first so that its latency
+  // overlaps the stencil stages
+  constexpr int W4 = kPC / 2, N4 = kPR * W4 / kPT;
+  static_assert(kPR * W4 == N4 * kPT, "stage 4 gives every thread the same number of pairs");
+  df64 bnr[N4][2];
+  if constexpr (!EXPL) {
+#pragma unroll
+    for (int e = 0; e < N4; ++e) {
+      const int k = tid + e * kPT, r = k / W4, c = 2 * (k - r * W4);
+      const int gj = j0 + r, gi = x0 + c;
+      bnr[e][0] = bnr[e][1] = df_make(1.0f, 0.0f);
+      if (gj < ny && gi < nx) {
+        const size_t idx = (size_t)gj * nx + gi;
+        bnr[e][0] = bn[idx];
+        if (gi + 1 < nx) bnr[e][1] = bn[idx + 1];
+      }
+    }
+  }
+  // ---- stage 1: film tile (two-cell halo, wall-reflected) as double-float planes
+  {
+    constexpr int W2 = (kPC + 8) / 2;
+    const bool inner_x = x0 - 4 >= 0 && x0 + kPC + 4 <= nx && (nx & 1) == 0 &&
+                         (reinterpret_cast<uintptr_t>(u) & 15) == 0;
+    for (int k = tid; k < (kPR + 4) * W2; k += kPT) {
+      const int r = k / W2, c = 2 * (k - r * W2);
+      const int gj = reflect_index(j0 - 2 + r, ny);
+      double a, b;
+      if (inner_x) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(u + (size_t)gj * nx + (x0 - 4 + c)));
+        a = v.x;
+        b = v.y;
+      } else {
+        a = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 4 + c, nx));
+        b = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 3 + c, nx));
+      }
+      const df64 da = df_of_pos_f64_fast(a), db = df_of_pos_f64_fast(b);
+      *reinterpret_cast<float2*>(&S.uh[r][c]) = make_float2(da.hi, db.hi);
+      *reinterpret_cast<float2*>(&S.ul[r][c]) = make_float2(da.lo, db.lo);
+    }
+  }
+  __syncthreads();
+  // ---- stage 2: lap, f0, f1 of cells (rs, cs): global (j0-1+rs, x0-2+cs)
+  {
+    const df2 four = d2_splat(RK.four), inv_ds2 = d2_splat(RK.inv_ds2);
+    const df2 A1 = d2_splat(RK.mc.A1), B1 = d2_splat(RK.mc.B1), C = d2_splat(RK.mc.C);
+    const bool unitC = RK.mc.unitC;
+    constexpr int W2 = (kPC + 4) / 2;
+    for (int k = tid; k < (kPR + 2) * W2; k += kPT) {
+      const int rs = k / W2, cs = 2 * (k - rs * W2);
+      const int tr = rs + 1, tc = cs + 2;  // the pair's position in the film tile
+      const df2 uc = ld2(S.uh[tr], S.ul[tr], tc);
+      const df2 Wp = ld2(S.uh[tr], S.ul[tr], tc - 2), Ep = ld2(S.uh[tr], S.ul[tr], tc + 2);
+      const df2 E = mid2(uc, Ep), Wn = mid2(Wp, uc);
+      const df2 Sn = ld2(S.uh[tr + 1], S.ul[tr + 1], tc), Nn = ld2(S.uh[tr - 1], S.ul[tr - 1], tc);
+      const df2 nb = d2_add_u(d2_add_u(E, Wn), d2_add_u(Sn, Nn));
+      st2(S.laph[rs], S.lapl[rs], cs, d2_norm(d2_mul_u(d2_sub_u(nb, d2_mul_u(four, uc)), inv_ds2)));
+      // f0 = C h^3, f1 = A1 - B1 / h (the (3, 2) power law)
+      const df2 s = d2_rcp(uc);
+      const df2 h2 = d2_mul(uc, uc);
+      const df2 f0 = unitC ? d2_mul(h2, uc) : d2_mul(d2_mul(C, h2), uc);
+      const df2 f1 = d2_sub(A1, d2_mul(B1, s));
+      st2(S.f0h[rs], S.f0l[rs], cs, d2_norm(f0));
+      st2(S.f1h[rs], S.f1l[rs], cs, d2_norm(f1));
+    }
+  }
+  __syncthreads();
+  // ---- stage 3: face fluxes f0bar dLap + f1bar du (zero on the walls)
+  {
+    constexpr int WX = (kPC + 2) / 2, WY = kPC / 2, NXF = kPR * WX;
+    // x- and y-face pairs in one loop, so that the threads share the work evenly
+    for (int k2 = tid; k2 < NXF + (kPR + 1) * WY; k2 += kPT) {
+      if (k2 >= NXF) {
+        const int k = k2 - NXF;
+        const int q = k / WY, c = 2 * (k - q * WY);  // face between rows j0-1+q and j0+q
+        const df2 f0P = ld2(S.f0h[q], S.f0l[q], c + 2), f0Q = ld2(S.f0h[q + 1], S.f0l[q + 1], c + 2);
+        const df2 f1P = ld2(S.f1h[q], S.f1l[q], c + 2), f1Q = ld2(S.f1h[q + 1], S.f1l[q + 1], c + 2);
+        const df2 lP = ld2(S.laph[q], S.lapl[q], c + 2), lQ = ld2(S.laph[q + 1], S.lapl[q + 1], c + 2);
+        const df2 uP = ld2(S.uh[q + 1], S.ul[q + 1], c + 4), uQ = ld2(S.uh[q + 2], S.ul[q + 2], c + 4);
+        df2 F = d2_norm(d2_add_u(d2_mul_u(d2_add_u(f0P, f0Q), d2_sub_u(lQ, lP)),
+                                 d2_mul_u(d2_add_u(f1P, f1Q), d2_sub_u(uQ, uP))));
+        const int gp = j0 - 1 + q;
+        if (!(gp >= 0 && gp + 1 < ny)) F = d2(p_splat(0.0f), p_splat(0.0f));
+        st2(S.fyh[q], S.fyl[q], c, F);
+        continue;
+      }
+      const int k = k2;
+      const int r = k / WX, kf = 2 * (k - r * WX);  // faces kf, kf + 1 of row j0 + r
+      const int rs = r + 1, tr = r + 2;
+      const df2 f0P = ld2(S.f0h[rs], S.f0l[rs], kf), f0R = ld2(S.f0h[rs], S.f0l[rs], kf + 2);
+      const df2 f1P = ld2(S.f1h[rs], S.f1l[rs], kf), f1R = ld2(S.f1h[rs], S.f1l[rs], kf + 2);
+      const df2 lP = ld2(S.laph[rs], S.lapl[rs], kf), lR = ld2(S.laph[rs], S.lapl[rs], kf + 2);
+      const df2 uP = ld2(S.uh[tr], S.ul[tr], kf + 2), uR = ld2(S.uh[tr], S.ul[tr], kf + 4);
+      const df2 f0Q = mid2(f0P, f0R), f1Q = mid2(f1P, f1R), lQ = mid2(lP, lR), uQ = mid2(uP, uR);
+      df2 F = d2_norm(d2_add_u(d2_mul_u(d2_add_u(f0P, f0Q), d2_sub_u(lQ, lP)),
+                               d2_mul_u(d2_add_u(f1P, f1Q), d2_sub_u(uQ, uP))));
+      const int gp = x0 - 2 + kf;  // left cell of face kf
+      if (!(gp >= 0 && gp + 1 < nx)) F.hi.x = F.lo.x = 0.0f;
+      if (!(gp + 1 >= 0 && gp + 2 < nx)) F.hi.y = F.lo.y = 0.0f;
+      st2(S.fxh[r], S.fxl[r], kf, F);
+    }
+  }
+  __syncthreads();
+  // ---- stage 4: G (or b^n) of the tile's cells, two per thread
+  const df2 gscale = d2_splat(RK.gscale);
+  float g = 0.0f;  // max |G| in FP32: a norm for reporting, not a decision
+#pragma unroll
+  for (int e = 0; e < N4; ++e) {
+    const int k = tid + e * kPT, r = k / W4, c = 2 * (k - r * W4);
+    const int gj = j0 + r, gi = x0 + c;
+    if (gj >= ny || gi >= nx) continue;
+    const bool two = gi + 1 < nx;
+    const df2 A = ld2(S.fxh[r], S.fxl[r], c), B = ld2(S.fxh[r], S.fxl[r], c + 2);
+    const df2 dp = d2_add_u(d2_sub_u(B, mid2(A, B)),
+                            d2_sub_u(ld2(S.fyh[r + 1], S.fyl[r + 1], c), ld2(S.fyh[r], S.fyl[r], c)));
+    const df2 uc = ld2(S.uh[r + 2], S.ul[r + 2], c + 4);
+    const size_t idx = (size_t)gj * nx + gi;
+    if constexpr (EXPL) {
+      const df2 b = d2_norm(d2_sub_u(uc, d2_mul_u(gscale, dp)));
+      bn[idx] = df_make(b.hi.x, b.lo.x);
+      if (two) bn[idx + 1] = df_make(b.hi.y, b.lo.y);
+    } else {
+      const df64 b0 = bnr[e][0], b1 = bnr[e][1];
+      const df2 Gv = d2_norm(d2_add_u(d2_sub_u(uc, d2(make_float2(b0.hi, b1.hi), make_float2(b0.lo, b1.lo))),
+                                      d2_mul_u(gscale, dp)));
+      const float2 gl = p_add(Gv.hi, Gv.lo);
+      // FP32 film for the sweeps: the leading float of the double-float height
+      if (two && ((nx | gi) & 1) == 0) {
+        *reinterpret_cast<float2*>(rhs + idx) = make_float2(-gl.x, -gl.y);
+        *reinterpret_cast<float2*>(ulp + idx) = uc.hi;
+      } else {
+        rhs[idx] = -gl.x;
+        ulp[idx] = uc.hi.x;
+        if (two) {
+          rhs[idx + 1] = -gl.y;
+          ulp[idx + 1] = uc.hi.y;
+        }
+      }
+      float ag = fabsf(gl.x);
+      if (!(ag <= g)) g = ag;
+      ag = two ? fabsf(gl.y) : 0.0f;
+      if (!(ag <= g)) g = ag;
+    }
+  }
+  if constexpr (EXPL) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float g2 = __shfl_xor_sync(0xffffffffu, g, o);
+    if (!(g2 <= g)) g = g2;
+  }
+  __shared__ float red[kPT / 32];
+  if ((tid & 31) == 0) red[tid >> 5] = g;
+  __syncthreads();
+  if (tid == 0) {
+    float mx = red[0];
+    for (int k = 1; k < kPT / 32; ++k)
+      if (!(red[k] <= mx)) mx = red[k];
+    PartX p;
+    p.gnorm = (double)mx;
+    p.pivot = 0;
+    p.pad = 0;
+    part[blockIdx.y * gridDim.x + blockIdx.x] = p;
+  }
+}
+
+}  // namespace tf
