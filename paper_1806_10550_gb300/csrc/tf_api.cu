@@ -268,7 +268,7 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   c->n_rhs_parts = c->packed_rhs ? c->grid_pkx * c->grid_pky : c->grid_rx * c->grid_ry;
   c->grid_st_x = (p->nx + 15) / 16;
   c->grid_st_y = (p->ny + 15) / 16;
-  c->grid_stats = 304;
+  c->grid_stats = 1216;  // 8 blocks of 256 threads per SM on 152 SMs
   {
     int a = c->grid_rx * c->grid_ry + c->grid_x, b = c->grid_st_x * c->grid_st_y;
     c->n_px = a > b ? a : b;

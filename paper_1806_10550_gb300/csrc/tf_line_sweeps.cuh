@@ -29,52 +29,85 @@ constexpr int kNP = 32 * kProd;  // producer threads
 static_assert(2 * 4 * 32 == kNP && 4 * kG == kRY && 4 * kG == kCX,
               "each producer thread owns one group of kG cells of one line half");
 
-// Copy an R x C tile of a row-major [ny][nx] array with top-left corner
-// (row0, col0) into shared memory (row pitch DP elements), reflecting indices
-// at the walls.  Interior tiles whose rows are 16-byte aligned move in
-// 16-byte cp.async vectors; other tiles element by element.  Executed by the
-// producer threads; copy loops stay rolled to keep the kernels' code small.
+// Tile copies into shared memory, executed by the kNP producer threads.  The
+// fast paths give every thread a fixed, compile-time set of elements (no
+// loop bookkeeping per element); the rare paths (wall reflection, unaligned
+// rows) stay rolled to keep the kernels' code small.
+
+// Interior rows [0, nr) x C columns starting at base (row pitch `pitch`
+// elements) in 16-byte vectors: base and pitch 16-byte aligned, C and DP
+// multiples of a vector.
 template <class T, int R, int C, int DP>
-__device__ __forceinline__ void copy_tile(T* dst, const T* __restrict__ src, int row0, int col0, int ny,
-                                          int nx, int p) {
-  constexpr int V = 16 / sizeof(T);  // elements per vector
-  const bool inner = row0 >= 0 && row0 + R <= ny && col0 >= 0 && col0 + C <= nx;
-  const T* base = src + (size_t)row0 * nx + col0;
-  if (inner && (C % V) == 0 && (DP % V) == 0 && (nx % V) == 0 &&
-      (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
-    constexpr int CV = C / V;
-#pragma unroll 1
-    for (int k = p; k < R * CV; k += kNP) {
-      const int r = k / CV, c = (k - r * CV) * V;
-      __pipeline_memcpy_async(dst + r * DP + c, base + (size_t)r * nx + c, 16);
-    }
-  } else {
-#pragma unroll 1
-    for (int k = p; k < R * C; k += kNP) {
-      const int r = k / C, c = k - r * C;
-      const int gj = reflect_index(row0 + r, ny), gi = reflect_index(col0 + c, nx);
-      cpT(dst + r * DP + c, src + (size_t)gj * nx + gi);
-    }
+__device__ __forceinline__ void copy_rows_vec(T* dst, const T* __restrict__ base, size_t pitch, int nr,
+                                              int p) {
+  constexpr int V = 16 / sizeof(T), CV = C / V, NI = (R * CV + kNP - 1) / kNP;
+  static_assert(C % V == 0 && DP % V == 0, "vector copies need whole vectors");
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int k = p + i * kNP;
+    const int r = k / CV, c = (k - r * CV) * V;
+    if (k < R * CV && r < nr) __pipeline_memcpy_async(dst + r * DP + c, base + r * pitch + c, 16);
   }
 }
 
-// Copy rows [0, nr) x columns [0, C) of a row-major array (row stride nx)
-// from (row0, col0) into shared memory (row pitch DP), without reflection;
-// columns at or beyond nx are skipped.  Full aligned rows move in 16-byte
-// vectors.
+// Interior rows [0, nr) x columns [0, nc) (nc <= C <= 32) element by element,
+// the 32 lanes of a warp along a row (coalesced), eight row groups.
+template <class T, int R, int C, int DP>
+__device__ __forceinline__ void copy_rows_elem(T* dst, const T* __restrict__ base, size_t pitch, int nr,
+                                               int nc, int p) {
+  static_assert(C <= 32 && kNP == 256, "one warp per row, eight row groups");
+  const int c = p & 31, rg = p >> 5;
+  if (c >= nc) return;
+#pragma unroll
+  for (int i = 0; i < (R + 7) / 8; ++i) {
+    const int r = rg + 8 * i;
+    if (r < nr) cpT(dst + r * DP + c, base + r * pitch + c);
+  }
+}
+
+// An R x C tile of a row-major [ny][nx] array with top-left corner
+// (row0, col0), indices reflected at the walls.
+template <class T, int R, int C, int DP>
+__device__ __forceinline__ void copy_tile(T* dst, const T* __restrict__ src, int row0, int col0, int ny,
+                                          int nx, int p) {
+  constexpr int V = 16 / sizeof(T);
+  const bool inner = row0 >= 0 && row0 + R <= ny && col0 >= 0 && col0 + C <= nx;
+  const T* base = src + (size_t)row0 * nx + col0;
+  if constexpr ((C % V) == 0 && (DP % V) == 0) {
+    if (inner && (nx % V) == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+      copy_rows_vec<T, R, C, DP>(dst, base, nx, R, p);
+      return;
+    }
+  }
+  if constexpr (C <= 32) {
+    if (inner) {
+      copy_rows_elem<T, R, C, DP>(dst, base, nx, R, C, p);
+      return;
+    }
+  }
+#pragma unroll 1
+  for (int k = p; k < R * C; k += kNP) {
+    const int r = k / C, c = k - r * C;
+    const int gj = reflect_index(row0 + r, ny), gi = reflect_index(col0 + c, nx);
+    cpT(dst + r * DP + c, src + (size_t)gj * nx + gi);
+  }
+}
+
+// Rows [0, nr) x columns [0, C) of a row-major array (row stride nx) from
+// (row0, col0), without reflection; columns at or beyond nx are skipped.
 template <class T, int R, int C, int DP>
 __device__ __forceinline__ void copy_rows(T* dst, const T* __restrict__ src, int row0, int col0, int nr,
                                           int nx, int p) {
   constexpr int V = 16 / sizeof(T);
   const T* base = src + (size_t)row0 * nx + col0;
-  if ((C % V) == 0 && (DP % V) == 0 && col0 + C <= nx && (nx % V) == 0 &&
-      (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
-    constexpr int CV = C / V;
-#pragma unroll 1
-    for (int k = p; k < nr * CV; k += kNP) {
-      const int r = k / CV, c = (k - r * CV) * V;
-      __pipeline_memcpy_async(dst + r * DP + c, base + (size_t)r * nx + c, 16);
+  if constexpr ((C % V) == 0 && (DP % V) == 0) {
+    if (col0 + C <= nx && (nx % V) == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+      copy_rows_vec<T, R, C, DP>(dst, base, nx, nr, p);
+      return;
     }
+  }
+  if constexpr (C <= 32) {
+    copy_rows_elem<T, R, C, DP>(dst, base, nx, nr, min(C, nx - col0), p);
   } else {
 #pragma unroll 1
     for (int k = p; k < nr * C; k += kNP) {
@@ -84,14 +117,16 @@ __device__ __forceinline__ void copy_rows(T* dst, const T* __restrict__ src, int
   }
 }
 
-// Copy n contiguous elements (both ends 16-byte aligned when n * sizeof(T)
-// is a multiple of 16).
-template <class T>
+// n <= NMAX contiguous elements; 16-byte vectors when both ends are aligned.
+template <class T, int NMAX>
 __device__ __forceinline__ void copy_span(T* dst, const T* __restrict__ src, int n, int p) {
-  constexpr int V = 16 / sizeof(T);
+  constexpr int V = 16 / sizeof(T), NI = (NMAX / V + kNP - 1) / kNP;
   if ((n % V) == 0 && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
-#pragma unroll 1
-    for (int k = p; k < n / V; k += kNP) __pipeline_memcpy_async(dst + k * V, src + k * V, 16);
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int k = p + i * kNP;
+      if (k < n / V) __pipeline_memcpy_async(dst + k * V, src + k * V, 16);
+    }
   } else {
 #pragma unroll 1
     for (int k = p; k < n; k += kNP) cpT(dst + k, src + k);
@@ -479,12 +514,10 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
           const LP x = S.s.b.xb[bq & 1][h][r][c];
           const double uk = S.s.b.ukt[slot][h][r][c];
           double un;
-          // one native FP64 add per cell (correctly rounded); the exact
-          // integer widening keeps the conversion off the FP64 pipe
-          if constexpr (sizeof(LP) == 8)
-            un = uk + (double)x;
-          else
-            un = uk + f64_of_f32((float)x);
+          // one native FP64 add per cell, correctly rounded (with the float
+          // widened exactly on the FP64 pipe: fewer instructions than the
+          // integer add of tf_numeric.cuh, measured)
+          un = uk + (double)x;
           const size_t idx = (size_t)j * nx + col;
           unew[idx] = un;
           if (vout) vout[idx] = to_f64(x);
@@ -589,10 +622,8 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
       const int c0 = c0_of(h, q), c1 = c1_of(h, q);
       copy_tile<LP, 34, kCX + 4, kCX + 5>(&S.s.f.ut[slot][h][0][0], ul, j0 - 1, c0 - 2, ny, nx, p);
 #pragma unroll 1
-      for (int k = p; k < 32 * kCX; k += kNP) {
-        int r = k / kCX, c = k - r * kCX;
-        if (j0 + r < ny && c0 + c < c1) cpT(&S.s.f.rt[slot][h][r][c], rw + (size_t)(j0 + r) * nx + c0 + c);
-      }
+      copy_rows_elem<LP, 32, kCX, kCX + 1>(&S.s.f.rt[slot][h][0][0], rw + (size_t)j0 * nx + c0, nx,
+                                           min(32, ny - j0), c1 - c0, p);
     }
     __pipeline_commit();
   };
@@ -683,7 +714,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
       const int c0 = c0_of(h, q), c1 = c1_of(h, q);
 #pragma unroll 1
       for (int f = 0; f < 3; ++f)
-        copy_span<LP>(&S.s.b.ft[slot][h][f][0][0], facb + ((size_t)f * nx + c0) * 32, (c1 - c0) * 32, p);
+        copy_span<LP, kCX * 32>(&S.s.b.ft[slot][h][f][0][0], facb + ((size_t)f * nx + c0) * 32, (c1 - c0) * 32, p);
     }
     __pipeline_commit();
   };
