@@ -275,7 +275,9 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   }
   c->n_py = c->grid_y > c->grid_stats ? c->grid_y : c->grid_stats;
   const size_t hp = c->ops->hp_bytes, lp = c->ops->lp_bytes;
-  const size_t facx = (size_t)3 * c->grid_x * 32 * (size_t)p->nx;
+  // factor scratch: one slab per block of 32 lines, line half and chunk
+  const size_t facx = tf::fac_slab<tf::kCX>(c->grid_x, 0, 0, tf::chunks_per_half<tf::kCX>(p->nx));
+  const size_t facy = tf::fac_slab<tf::kRY>(c->grid_y, 0, 0, tf::chunks_per_half<tf::kRY>(p->ny));
   int r = TF_OK;
   cudaError_t e = c->ops->prepare();
   if (e != cudaSuccess) r = cuda_fail(e);
@@ -283,7 +285,7 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   if (!r) r = dalloc(&c->w, c->N * lp);
   if (!r && lp != sizeof(double)) r = dalloc(&c->ulp, c->N * lp);
   if (!r) r = dalloc(&c->fac_x, facx * lp);
-  if (!r) r = dalloc(&c->fac_y, 3 * c->N * lp);
+  if (!r) r = dalloc(&c->fac_y, facy * lp);
   if (!r) r = dalloc(&c->ubuf, c->N * sizeof(double));
   if (!r) r = dalloc(&c->ubuf2, c->N * sizeof(double));
   if (!r) r = dalloc(&c->px, (size_t)c->n_px * sizeof(tf::PartX));

@@ -93,7 +93,9 @@ TF_HD double to_f64(float x) { return f64_of_f32(x); }
 TF_HD double rcp(double x) { return 1.0 / x; }
 TF_HD float rcp(float x) {
 #ifdef __CUDA_ARCH__
-  return __fdividef(1.0f, x);  // MUFU reciprocal, about 2 ulp: FP32 solves only
+  float r;  // the MUFU reciprocal alone, about 1 ulp: FP32 Jacobian and solves only
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 #else
   return 1.0f / x;
 #endif
@@ -414,9 +416,10 @@ __device__ __forceinline__ void face_dF(const CellLP<LP>& P, const CellLP<LP>& Q
 template <class LP> struct LUState {
   LP g1, d1, z1, g2, d2, z2;  // (gamma, delta, z) of rows i-1 and i-2
   __device__ __forceinline__ void reset() { g1 = d1 = z1 = g2 = d2 = z2 = LP(0); }
-  // Eliminate row i (a x_{i-2} + b x_{i-1} + c x_i + d x_{i+1} + e x_{i+2} = r);
-  // returns false on a zero or non-finite pivot.
-  __device__ __forceinline__ bool step(LP a, LP b, LP c, LP d, LP e, LP r, LP& g, LP& dl, LP& z) {
+  // Eliminate row i (a x_{i-2} + b x_{i-1} + c x_i + d x_{i+1} + e x_{i+2} = r).
+  // chk accumulates pivot * (1/pivot): it turns NaN, and stays NaN, once a
+  // pivot is zero or non-finite, so callers test it once per chunk.
+  __device__ __forceinline__ void step(LP a, LP b, LP c, LP d, LP e, LP r, LP& g, LP& dl, LP& z, LP& chk) {
     LP beta = b - a * g2;
     LP mu = c - a * d2 - beta * g1;
     LP inv = rcp(mu);
@@ -429,7 +432,7 @@ template <class LP> struct LUState {
     g1 = g;
     d1 = dl;
     z1 = z;
-    return (mu != LP(0)) && isfinite(mu);
+    chk = fma(mu, inv, chk);
   }
 };
 

@@ -242,20 +242,36 @@ __device__ __forceinline__ void band_rows(const LineK<LP>& L, Acc A, int ia, int
 // ([a..e, r][cell][line]), cell 0 first.  The producers store both halves of
 // a twisted line in this processing order -- the second half with its band
 // reversed (e..a) and its cells from the far end -- so one code path serves
-// both solver warps.  SPILL(s, g, d, z) stores the factors of processed cell
-// s.  The loop is unrolled so that band loads run ahead of the recurrence.
-template <class LP, int L, class Spill>
-__device__ __forceinline__ void lu_chunk(LUState<LP>& lu, const LP* B, int lane, int n, Spill spill,
-                                         int& bad) {
+// both solver warps.  The factors go to Q[f * L * 32 + s * 32] (this lane's
+// column of the chunk's factor slab).  A zero or non-finite pivot sets bad.
+// The loop is unrolled so that band loads run ahead of the recurrence.
+template <class LP, int L>
+__device__ __forceinline__ void lu_chunk(LUState<LP>& lu, const LP* B, int lane, int n, LP* Q, int& bad) {
+  LP chk = LP(0);
 #pragma unroll 8
   for (int s = 0; s < n; ++s) {
     const int k = s * 32 + lane;
     LP g, dl, z;
-    if (!lu.step(B[k], B[L * 32 + k], B[2 * L * 32 + k], B[3 * L * 32 + k], B[4 * L * 32 + k],
-                 B[5 * L * 32 + k], g, dl, z))
-      bad = 1;
-    spill(s, g, dl, z);
+    lu.step(B[k], B[L * 32 + k], B[2 * L * 32 + k], B[3 * L * 32 + k], B[4 * L * 32 + k], B[5 * L * 32 + k],
+            g, dl, z, chk);
+    Q[s * 32] = g;
+    Q[L * 32 + s * 32] = dl;
+    Q[2 * L * 32 + s * 32] = z;
   }
+  if (!(chk == chk)) bad = 1;
+}
+
+// Factor scratch of a sweep: for every block of 32 lines, line half and
+// chunk, one slab [g, d, z][cell][line] of 3 * L * 32 values, cells in the
+// solver's processing order; the backward pass stages a slab with one
+// contiguous copy.
+template <int L> __host__ __device__ inline int chunks_per_half(int n) {
+  const int m = split_point<L>(n);
+  const int a = (m + L - 1) / L, b = m < n ? (n - m + L - 1) / L : 0;
+  return a > b ? a : b;
+}
+template <int L> __host__ __device__ inline size_t fac_slab(int blk, int h, int q, int nch) {
+  return (((size_t)blk * 2 + h) * nch + q) * (size_t)(3 * L * 32);
 }
 
 // Back substitution x = z - g x' - d x'' over the n cells of one chunk in
@@ -329,9 +345,6 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   auto nchh = [&](int h) { return h ? nch1 : nch0; };
   auto r0_of = [&](int h, int q) { return h == 0 ? q * kRY : max(m, ny - (q + 1) * kRY); };
   auto r1_of = [&](int h, int q) { return h == 0 ? min(m, (q + 1) * kRY) : ny - q * kRY; };
-  LP* fg = fac;
-  LP* fd = fac + N;
-  LP* fz = fac + 2 * N;
   int pivot_bad = 0;
 
   // ---------------- producer helpers ----------------
@@ -403,15 +416,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
         const int r0 = r0_of(h, q), r1 = r1_of(h, q);
         const LP* B = &S.s.f.band[q & 1][h][0][0][0];
         const int col = i0 + lane;
-        // processed cell s is row r0 + s (top half) or r1 - 1 - s (bottom)
-        const int jb = h ? r1 - 1 : r0, js = h ? -1 : 1;
-        auto spill = [&](int s, LP g, LP dl, LP z) {
-          const size_t idx = (size_t)(jb + js * s) * nx + col;
-          fg[idx] = g;
-          fd[idx] = dl;
-          fz[idx] = z;
-        };
-        lu_chunk<LP, kRY>(lu, B, lane, r1 - r0, spill, pivot_bad);
+        lu_chunk<LP, kRY>(lu, B, lane, r1 - r0, fac + fac_slab<kRY>(blockIdx.x, h, q, nch) + lane, pivot_bad);
       }
     }
     __syncthreads();
@@ -435,10 +440,8 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
     for (int h = 0; h < 2; ++h) {
       const int q = nchh(h) - 1 - bq;
       if (q < 0) continue;
-      const int r0 = r0_of(h, q), r1 = r1_of(h, q);
-#pragma unroll 1
-      for (int f = 0; f < 3; ++f)
-        copy_rows<LP, kRY, 32, 32>(&S.s.b.ft[slot][h][f][0][0], fac + (size_t)f * N, r0, i0, r1 - r0, nx, p);
+      copy_span<LP, 3 * kRY * 32>(&S.s.b.ft[slot][h][0][0][0], fac + fac_slab<kRY>(blockIdx.x, h, q, nch),
+                                  3 * kRY * 32, p);
     }
   };
   auto issue_bwd_u = [&](int bq) {  // u_k tiles of backward chunk bq
@@ -485,9 +488,10 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
           const int r0 = r0_of(h, q), r1 = r1_of(h, q);
           const int slot = t % 3;
           LP* X = &S.s.b.xb[t & 1][h][0][0];
-          // processed cell s is chunk row n-1-s (top half, upward) or s
+          // processed cell s is chunk row n-1-s (top half, upward) or s; its
+          // factors are slab cell n-1-s (the forward pass ran the other way)
           const int n = r1 - r0, rb = h ? 0 : n - 1, rs = h ? 1 : -1;
-          auto F = [&](int f, int s) { return S.s.b.ft[slot][h][f][rb + rs * s][lane]; };
+          auto F = [&](int f, int s) { return S.s.b.ft[slot][h][f][n - 1 - s][lane]; };
           auto xs = [&](int s) { return S.xs[lane][r0 + rb + rs * s - (m - 2)]; };
           auto put = [&](int s, LP x) { X[(rb + rs * s) * 32 + lane] = x; };
           auto is_seam = [&](int s) {
@@ -569,8 +573,8 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
 // x sweep.  Block: 32 rows j0..j0+31.  Warp 0 / 1 solve the left / right
 // halves of the rows (lane = row); warps 2..9 produce.  Producer thread p
 // builds the band rows of half p >> 7, row p & 31 and the column group
-// (p >> 5) & 3 (kG columns of a kCX-column chunk).  Factor scratch per block:
-// fac[((blk*3 + f)*nx + col)*32 + row].
+// (p >> 5) & 3 (kG columns of a kCX-column chunk).  Factor scratch: one slab
+// per block, half and chunk (fac_slab).
 
 template <class LP> struct XFwd {
   LP ut[2][2][34][kCX + 5];      // LP film tiles (rows j0-1.., cols c0-2..c0+kCX+1)
@@ -611,7 +615,6 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   auto nchh = [&](int h) { return h ? nch1 : nch0; };
   auto c0_of = [&](int h, int q) { return h == 0 ? q * kCX : max(m, nx - (q + 1) * kCX); };
   auto c1_of = [&](int h, int q) { return h == 0 ? min(m, (q + 1) * kCX) : nx - q * kCX; };
-  LP* facb = fac + (size_t)blockIdx.x * 3 * nx * 32;
   int pivot_bad = 0;
 
   auto issue_fwd = [&](int q) {
@@ -680,18 +683,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
       if (q < nchh(h) && j0 + lane < ny) {
         const int c0 = c0_of(h, q), c1 = c1_of(h, q);
         const LP* B = &S.s.f.band[q & 1][h][0][0][0];
-        LP* fg = facb;
-        LP* fd = facb + (size_t)nx * 32;
-        LP* fz = facb + (size_t)2 * nx * 32;
-        // processed cell s is column c0 + s (left half) or c1 - 1 - s (right)
-        const int ib = h ? c1 - 1 : c0, is = h ? -1 : 1;
-        auto spill = [&](int s, LP g, LP dl, LP z) {
-          const size_t o = (size_t)(ib + is * s) * 32 + lane;
-          fg[o] = g;
-          fd[o] = dl;
-          fz[o] = z;
-        };
-        lu_chunk<LP, kCX>(lu, B, lane, c1 - c0, spill, pivot_bad);
+        lu_chunk<LP, kCX>(lu, B, lane, c1 - c0, fac + fac_slab<kCX>(blockIdx.x, h, q, nch) + lane, pivot_bad);
       }
     }
     __syncthreads();
@@ -711,10 +703,8 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
     for (int h = 0; h < 2; ++h) {
       const int q = nchh(h) - 1 - bq;
       if (q < 0) continue;
-      const int c0 = c0_of(h, q), c1 = c1_of(h, q);
-#pragma unroll 1
-      for (int f = 0; f < 3; ++f)
-        copy_span<LP, kCX * 32>(&S.s.b.ft[slot][h][f][0][0], facb + ((size_t)f * nx + c0) * 32, (c1 - c0) * 32, p);
+      copy_span<LP, 3 * kCX * 32>(&S.s.b.ft[slot][h][0][0][0], fac + fac_slab<kCX>(blockIdx.x, h, q, nch),
+                                  3 * kCX * 32, p);
     }
     __pipeline_commit();
   };
@@ -742,9 +732,10 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
         if (q >= 0 && j0 + lane < ny) {
           const int c0 = c0_of(h, q), c1 = c1_of(h, q);
           const int slot = t % 3;
-          // processed cell s is chunk column n-1-s (left half, leftward) or s
+          // processed cell s is chunk column n-1-s (left half, leftward) or s;
+          // its factors are slab cell n-1-s
           const int n = c1 - c0, cb = h ? 0 : n - 1, cs = h ? 1 : -1;
-          auto F = [&](int f, int s) { return S.s.b.ft[slot][h][f][cb + cs * s][lane]; };
+          auto F = [&](int f, int s) { return S.s.b.ft[slot][h][f][n - 1 - s][lane]; };
           auto xs = [&](int s) { return S.xs[lane][c0 + cb + cs * s - (m - 2)]; };
           auto put = [&](int s, LP x) { S.s.b.xb[t & 1][h][cb + cs * s][lane] = x; };
           auto is_seam = [&](int s) {
