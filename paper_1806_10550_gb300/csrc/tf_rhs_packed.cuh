@@ -155,19 +155,27 @@ __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per 
     constexpr int W2 = (kPC + 8) / 2;
     const bool inner_x = x0 - 4 >= 0 && x0 + kPC + 4 <= nx && (nx & 1) == 0 &&
                          (reinterpret_cast<uintptr_t>(u) & 15) == 0;
-    for (int k = tid; k < (kPR + 4) * W2; k += kPT) {
+    // all of a thread's loads are issued before the first conversion
+    constexpr int NP = (kPR + 4) * W2, N1 = (NP + kPT - 1) / kPT;
+    double2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const int k = min(tid + i * kPT, NP - 1);
       const int r = k / W2, c = 2 * (k - r * W2);
       const int gj = reflect_index(j0 - 2 + r, ny);
-      double a, b;
       if (inner_x) {
-        const double2 v = __ldg(reinterpret_cast<const double2*>(u + (size_t)gj * nx + (x0 - 4 + c)));
-        a = v.x;
-        b = v.y;
+        v[i] = __ldg(reinterpret_cast<const double2*>(u + (size_t)gj * nx + (x0 - 4 + c)));
       } else {
-        a = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 4 + c, nx));
-        b = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 3 + c, nx));
+        v[i].x = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 4 + c, nx));
+        v[i].y = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 3 + c, nx));
       }
-      const df64 da = df_of_pos_f64_fast(a), db = df_of_pos_f64_fast(b);
+    }
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const int k = tid + i * kPT;
+      if (k >= NP) break;
+      const int r = k / W2, c = 2 * (k - r * W2);
+      const df64 da = df_of_pos_f64_fast(v[i].x), db = df_of_pos_f64_fast(v[i].y);
       *reinterpret_cast<float2*>(&S.uh[r][c]) = make_float2(da.hi, db.hi);
       *reinterpret_cast<float2*>(&S.ul[r][c]) = make_float2(da.lo, db.lo);
     }
