@@ -56,6 +56,10 @@ extern "C" {
 /* models (Sec. Thin Film Models) */
 #define TF_MODEL_POWERLAW 0 /* f0 = C h^3, f1 = h^3 Pi'(h), power-law Pi    */
 #define TF_MODEL_LINEAR 1   /* f0 = c0, f1 = c1 (the linear test model)      */
+#define TF_MODEL_NLC 2      /* f0 = C h^3, f1 = h^3 Pi_NLC'(h): eqs. DisjPressNLC,
+                               mh_model (nematic liquid crystal film)          */
+#define TF_MODEL_POLYMER 3  /* f0 = C h^3, f1 = h^3 Pi_POL'(h): eq.
+                               DisjPressPolymer (polymer film on SiOx/Si)     */
 
 /* precision modes */
 #define TF_FP64 0      /* every operation in IEEE double                       */
@@ -86,6 +90,16 @@ typedef struct {
   int grow_after;        /* consecutive accepted steps before dt grows        */
   double rupture_h;      /* tf_advance stops when min h < rupture_h (0 = off) */
   int precision;         /* TF_FP64 or TF_FP32_BULK                            */
+  /* TF_MODEL_NLC: Pi = K[(b/h)^3 - (b/h)^2] + (N/2)(m(h)/h)^2,
+     m(h) = g(h) h^2/(h^2 + beta^2), g(h) = [1 + tanh((h - 2b)/w)]/2, with b
+     above; the paper's set (eq. NLC_paras) is C = 0.0857, K = 36, N = 1.67,
+     beta = 1, w = 0.05, b = 0.01.  All > 0.                               */
+  double nlc_K, nlc_N, nlc_beta, nlc_w;
+  /* TF_MODEL_POLYMER: Pi = -psi'(h), psi = Cp/h^8 - A_SiOx/(12 pi h^2)
+     + (A_SiOx - A_Si)/(12 pi (h + d)^2); the paper's set (eq.
+     Polymer_scales) is C = 0.00581, Cp = 1.181, A_SiOx = 41.25,
+     A_Si = -243.75, d = 191.  Cp > 0, d >= 0.                            */
+  double pol_C, pol_A_SiOx, pol_A_Si, pol_d;
 } tf_params;
 
 typedef struct tf_ctx tf_ctx;
@@ -124,7 +138,9 @@ typedef struct {
 /* Fill *p with the defaults: power-law model, C = 1, b = 0.1, n = 3, m = 2,
  * contact angle 20 degrees (kappa derived), theta = 0.5, tol 1e-10, K = 10,
  * dt_min 1e-9, dt_max 1e30, shrink 0.5, grow 1.25 after 5, no rupture stop,
- * TF_FP64.  nx, ny, ds are set to 0 and must be filled in.               */
+ * TF_FP64; the NLC and polymer parameters hold the paper's sets (C and b
+ * must still be set for those models).  nx, ny, ds are set to 0 and must
+ * be filled in.                                                          */
 void tf_params_default(tf_params* p);
 
 /* Create a context: validates *p, allocates the device workspace (about

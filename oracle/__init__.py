@@ -32,6 +32,8 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
 MODEL_POWERLAW = 0
 MODEL_LINEAR = 1
+MODEL_NLC = 2
+MODEL_POLYMER = 3
 
 
 class _Model(C.Structure):
@@ -40,6 +42,10 @@ class _Model(C.Structure):
         ("cap_C", C.c_double), ("b", C.c_double), ("kappa", C.c_double),
         ("n", C.c_int), ("m", C.c_int), ("c0", C.c_double), ("c1", C.c_double),
         ("theta", C.c_double),
+        ("nlc_K", C.c_double), ("nlc_N", C.c_double), ("nlc_beta", C.c_double),
+        ("nlc_w", C.c_double),
+        ("pol_C", C.c_double), ("pol_A1", C.c_double), ("pol_A2", C.c_double),
+        ("pol_d", C.c_double),
     ]
 
 
@@ -103,6 +109,7 @@ def lib():
         L.or_kappa_from_contact_angle.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int]
         L.or_dpi.restype = C.c_double
         L.or_dpi.argtypes = [C.POINTER(_Model), C.c_double]
+        L.or_pi.argtypes = [C.POINTER(_Model), C.c_double, dp, dp, dp]
         L.or_mobility.argtypes = [C.POINTER(_Model), C.c_double, dp, dp, dp, dp]
         L.or_lsa.argtypes = [C.POINTER(_Model), C.c_double, dp, dp]
         L.or_laplacian.argtypes = [C.POINTER(_Model), dp, dp]
@@ -149,10 +156,22 @@ class Model:
     c0: float = 1.0
     c1: float = 1.0
     theta: float = 0.5
+    # NLC model, eq. NLC_paras (K, N, beta, w; with cap_C = 0.0857, b = 0.01)
+    nlc_K: float = 36.0
+    nlc_N: float = 1.67
+    nlc_beta: float = 1.0
+    nlc_w: float = 0.05
+    # polymer model, eq. Polymer_scales (C, A_SiOx, A_Si, d; with cap_C = 0.00581)
+    pol_C: float = 1.181
+    pol_A1: float = 41.25
+    pol_A2: float = -243.75
+    pol_d: float = 191.0
 
     def c(self) -> _Model:
         return _Model(self.nx, self.ny, self.ds, self.model, self.cap_C, self.b,
-                      self.kappa, self.n, self.m, self.c0, self.c1, self.theta)
+                      self.kappa, self.n, self.m, self.c0, self.c1, self.theta,
+                      self.nlc_K, self.nlc_N, self.nlc_beta, self.nlc_w,
+                      self.pol_C, self.pol_A1, self.pol_A2, self.pol_d)
 
 
 @dataclass
@@ -187,6 +206,13 @@ def mobility(M: Model, h: float):
 
 def dpi(M: Model, h: float) -> float:
     return lib().or_dpi(C.byref(M.c()), h)
+
+
+def pi_derivs(M: Model, h: float):
+    """(Pi, Pi', Pi'') of the model's disjoining pressure at height h."""
+    p, d1, d2 = C.c_double(), C.c_double(), C.c_double()
+    lib().or_pi(C.byref(M.c()), h, C.byref(p), C.byref(d1), C.byref(d2))
+    return p.value, d1.value, d2.value
 
 
 def lsa(M: Model, h0: float):

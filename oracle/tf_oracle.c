@@ -53,10 +53,60 @@ double or_kappa_from_contact_angle(double th, double b, int n, int m) {
   return (1.0 - cos(th)) / (b * Mf);
 }
 
-/* Pi(h) = kappa[(b/h)^n - (b/h)^m]  =>  Pi'(h) = kappa[m r^m - n r^n]/h. */
-double or_dpi(const or_model* M, double h) {
+/* Disjoining pressure and its first two derivatives, Sec. Thin Film Models.
+ *
+ * Power law: Pi = kappa[r^n - r^m], r = b/h, so Pi' = kappa[m r^m - n r^n]/h
+ * and Pi'' = kappa[n(n+1) r^n - m(m+1) r^m]/h^2.
+ *
+ * NLC (eqs. DisjPressNLC, mh_model): Pi = K[r^3 - r^2] + (N/2) q^2 with
+ * q = m(h)/h = g(h) h/(h^2 + beta^2), g = [1 + tanh(s)]/2, s = (h - 2b)/w:
+ *   g' = (1 - tanh^2 s)/(2w),  g'' = -tanh(s)(1 - tanh^2 s)/w^2,
+ *   q' = g' h/D + g (beta^2 - h^2)/D^2,  D = h^2 + beta^2,
+ *   q'' = g'' h/D + 2 g' (beta^2 - h^2)/D^2 + g 2h(h^2 - 3 beta^2)/D^3,
+ *   (N/2 q^2)' = N q q',  (N/2 q^2)'' = N (q'^2 + q q'').
+ *
+ * Polymer (eq. DisjPressPolymer): Pi = -psi' with
+ * psi = Cp h^-8 - A1/(12 pi) h^-2 + (A1 - A2)/(12 pi) (h + d)^-2:
+ *   Pi   =   8 Cp h^-9  -  A1/(6 pi) h^-3 + (A1 - A2)/(6 pi) (h + d)^-3,
+ *   Pi'  = -72 Cp h^-10 +  A1/(2 pi) h^-4 - (A1 - A2)/(2 pi) (h + d)^-4,
+ *   Pi'' = 720 Cp h^-11 - 2 A1/pi   h^-5 + 2 (A1 - A2)/pi   (h + d)^-5. */
+void or_pi(const or_model* M, double h, double* pi, double* dpi, double* d2pi) {
+  if (M->model == OR_MODEL_POLYMER) {
+    const double PI = 3.14159265358979323846;
+    double A1 = M->pol_A1, A12 = M->pol_A1 - M->pol_A2, Cp = M->pol_C, e = h + M->pol_d;
+    *pi = 8.0 * Cp / ipow(h, 9) - A1 / (6.0 * PI * ipow(h, 3)) + A12 / (6.0 * PI * ipow(e, 3));
+    *dpi = -72.0 * Cp / ipow(h, 10) + A1 / (2.0 * PI * ipow(h, 4)) - A12 / (2.0 * PI * ipow(e, 4));
+    *d2pi = 720.0 * Cp / ipow(h, 11) - 2.0 * A1 / (PI * ipow(h, 5)) + 2.0 * A12 / (PI * ipow(e, 5));
+    return;
+  }
+  if (M->model == OR_MODEL_NLC) {
+    double r = M->b / h, K = M->nlc_K, N = M->nlc_N, w = M->nlc_w, be2 = M->nlc_beta * M->nlc_beta;
+    double p1 = K * (r * r * r - r * r);
+    double dp1 = K * (2.0 * r * r - 3.0 * r * r * r) / h;
+    double d2p1 = K * (12.0 * r * r * r - 6.0 * r * r) / (h * h);
+    double t = tanh((h - 2.0 * M->b) / w), sech2 = 1.0 - t * t;
+    double g = 0.5 * (1.0 + t), dg = sech2 / (2.0 * w), d2g = -t * sech2 / (w * w);
+    double D = h * h + be2;
+    double q = g * h / D;
+    double dq = dg * h / D + g * (be2 - h * h) / (D * D);
+    double d2q = d2g * h / D + 2.0 * dg * (be2 - h * h) / (D * D) + g * 2.0 * h * (h * h - 3.0 * be2) / (D * D * D);
+    *pi = p1 + 0.5 * N * q * q;
+    *dpi = dp1 + N * q * dq;
+    *d2pi = d2p1 + N * (dq * dq + q * d2q);
+    return;
+  }
   double r = M->b / h;
-  return M->kappa * ((double)M->m * ipow(r, M->m) - (double)M->n * ipow(r, M->n)) / h;
+  double rn = ipow(r, M->n), rm = ipow(r, M->m);
+  double n = (double)M->n, m = (double)M->m;
+  *pi = M->kappa * (rn - rm);
+  *dpi = M->kappa * (m * rm - n * rn) / h;
+  *d2pi = M->kappa * (n * (n + 1.0) * rn - m * (m + 1.0) * rm) / (h * h);
+}
+
+double or_dpi(const or_model* M, double h) {
+  double p, d1, d2;
+  or_pi(M, h, &p, &d1, &d2);
+  return d1;
 }
 
 /* Sec. Thin Film Models, eq. GeneralDisPreForm: f0 = C h^3, f1 = h^3 Pi'(h).
@@ -70,11 +120,8 @@ void or_mobility(const or_model* M, double h, double* f0, double* f1,
     *df1 = 0.0;
     return;
   }
-  double r = M->b / h;
-  double rn = ipow(r, M->n), rm = ipow(r, M->m);
-  double n = (double)M->n, m = (double)M->m;
-  double dpi = M->kappa * (m * rm - n * rn) / h;
-  double d2pi = M->kappa * (n * (n + 1.0) * rn - m * (m + 1.0) * rm) / (h * h);
+  double pi, dpi, d2pi;
+  or_pi(M, h, &pi, &dpi, &d2pi);
   *f0 = M->cap_C * h * h * h;
   *df0 = 3.0 * M->cap_C * h * h;
   *f1 = h * h * h * dpi;

@@ -8,7 +8,8 @@
  * What it computes (Lam, Cummings & Kondic, "Computing dynamics of thin films
  * via large scale GPU-based simulations"):
  *   u_t + div[ f0(u) grad lap u + f1(u) grad u ] = 0       (eq. GoverningEquation)
- *   f0 = C h^3, f1 = h^3 Pi'(h), Pi = kappa[(b/h)^n - (b/h)^m] (eq. GeneralDisPreForm)
+ *   f0 = C h^3, f1 = h^3 Pi'(h), Pi = kappa[(b/h)^n - (b/h)^m] (eq. GeneralDisPreForm),
+ *   or Pi = Pi_NLC (eqs. DisjPressNLC, mh_model) or Pi_POL (eq. DisjPressPolymer),
  * discretised by cell-centred finite volumes (Sec. Conservation Law,
  * Sec. Flux Discretization), Crank--Nicolson / theta in time (eq. TrapRule),
  * solved by the pseudo-Newton ADI iteration (eqs. JacobianSystem1-3) with the
@@ -25,7 +26,7 @@
 extern "C" {
 #endif
 
-enum { OR_MODEL_POWERLAW = 0, OR_MODEL_LINEAR = 1 };
+enum { OR_MODEL_POWERLAW = 0, OR_MODEL_LINEAR = 1, OR_MODEL_NLC = 2, OR_MODEL_POLYMER = 3 };
 
 typedef struct {
   int nx, ny;          /* cells in x and y                                  */
@@ -36,6 +37,14 @@ typedef struct {
   int n, m;            /* exponents, n > m >= 1                             */
   double c0, c1;       /* linear model: f0 = c0, f1 = c1                    */
   double theta;        /* time weighting; 0.5 = Crank--Nicolson             */
+  /* NLC model (eqs. DisjPressNLC, mh_model): Pi = K[(b/h)^3 - (b/h)^2]
+     + (N/2)(m(h)/h)^2, m(h) = g(h) h^2/(h^2 + beta^2),
+     g(h) = [1 + tanh((h - 2b)/w)]/2                                       */
+  double nlc_K, nlc_N, nlc_beta, nlc_w;
+  /* polymer model (eq. DisjPressPolymer): Pi = -psi'(h),
+     psi = Cp/h^8 - A1/(12 pi h^2) + (A1 - A2)/(12 pi (h + d)^2),
+     A1 = A_SiOx, A2 = A_Si                                                 */
+  double pol_C, pol_A1, pol_A2, pol_d;
 } or_model;
 
 typedef struct {
@@ -67,7 +76,10 @@ typedef struct {
  * M = (n - m) / ((m - 1)(n - 1)).                                          */
 double or_kappa_from_contact_angle(double theta_c, double b, int n, int m);
 
-/* Pi'(h) for the power law. */
+/* Pi(h), Pi'(h) and Pi''(h) of the model (power law, NLC or polymer). */
+void or_pi(const or_model* M, double h, double* pi, double* dpi, double* d2pi);
+
+/* Pi'(h). */
 double or_dpi(const or_model* M, double h);
 
 /* Mobilities f0, f1 and their derivatives at one height.                   */

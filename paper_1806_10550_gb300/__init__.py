@@ -32,6 +32,8 @@ TF_ADV_DT_MIN = 2
 TF_ADV_RUPTURE = 3
 TF_MODEL_POWERLAW = 0
 TF_MODEL_LINEAR = 1
+TF_MODEL_NLC = 2
+TF_MODEL_POLYMER = 3
 TF_FP64 = 0
 TF_FP32_BULK = 1
 
@@ -46,6 +48,10 @@ class TfParams(C.Structure):
         ("dt_min", C.c_double), ("dt_max", C.c_double), ("dt_shrink", C.c_double),
         ("dt_grow", C.c_double), ("grow_after", C.c_int), ("rupture_h", C.c_double),
         ("precision", C.c_int),
+        ("nlc_K", C.c_double), ("nlc_N", C.c_double), ("nlc_beta", C.c_double),
+        ("nlc_w", C.c_double),
+        ("pol_C", C.c_double), ("pol_A_SiOx", C.c_double), ("pol_A_Si", C.c_double),
+        ("pol_d", C.c_double),
     ]
 
 

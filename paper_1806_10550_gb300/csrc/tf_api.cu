@@ -179,6 +179,14 @@ void tf_params_default(tf_params* p) {
   p->grow_after = 5;
   p->rupture_h = 0.0;
   p->precision = TF_FP64;
+  p->nlc_K = 36.0;
+  p->nlc_N = 1.67;
+  p->nlc_beta = 1.0;
+  p->nlc_w = 0.05;
+  p->pol_C = 1.181;
+  p->pol_A_SiOx = 41.25;
+  p->pol_A_Si = -243.75;
+  p->pol_d = 191.0;
 }
 
 const char* tf_strerror(int code) {
@@ -221,7 +229,13 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   if (p->nx < 1 || p->ny < 1 || !(p->ds > 0.0) || !isfinite(p->ds)) return TF_ERR_ARG;
   if ((double)p->nx * (double)p->ny >= 2147483647.0) return TF_ERR_ARG;
   if (p->nx > 65536 || p->ny > 65536) return TF_ERR_ARG;
-  if (p->model != TF_MODEL_POWERLAW && p->model != TF_MODEL_LINEAR) return TF_ERR_ARG;
+  if (p->model < TF_MODEL_POWERLAW || p->model > TF_MODEL_POLYMER) return TF_ERR_ARG;
+  if (p->model == TF_MODEL_NLC &&
+      !(p->cap_C > 0.0 && p->b > 0.0 && p->nlc_K > 0.0 && p->nlc_N > 0.0 && p->nlc_beta > 0.0 && p->nlc_w > 0.0))
+    return TF_ERR_ARG;
+  if (p->model == TF_MODEL_POLYMER && !(p->cap_C > 0.0 && p->pol_C > 0.0 && p->pol_d >= 0.0 &&
+                                        isfinite(p->pol_A_SiOx) && isfinite(p->pol_A_Si)))
+    return TF_ERR_ARG;
   if (!(p->theta >= 0.0 && p->theta <= 1.0)) return TF_ERR_ARG;
   if (p->newton_max_iter < 1 || p->newton_fixed_iter < 0) return TF_ERR_ARG;
   if (!(p->dt_shrink > 0.0 && p->dt_shrink < 1.0) || !(p->dt_grow >= 1.0) || p->grow_after < 1)
@@ -258,6 +272,15 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   mk.B1 = kappa * (double)p->n * pow(p->b, p->n);
   mk.c0 = p->c0;
   mk.c1 = p->c1;
+  mk.nlc_K = p->nlc_K;
+  mk.nlc_N = p->nlc_N;
+  mk.nlc_beta = p->nlc_beta;
+  mk.nlc_w = p->nlc_w;
+  mk.b = p->b;
+  mk.pol_C = p->pol_C;
+  mk.pol_A1 = p->pol_A_SiOx;
+  mk.pol_A2 = p->pol_A_Si;
+  mk.pol_d = p->pol_d;
   c->grid_x = (p->ny + 31) / 32;
   c->grid_y = (p->nx + 31) / 32;
   c->grid_rx = (p->nx + 31) / 32;

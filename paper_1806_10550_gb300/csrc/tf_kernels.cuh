@@ -34,12 +34,15 @@ namespace tf {
 
 struct ModelK {
   int nx, ny;
-  int model;  // 0 power law, 1 linear
+  int model;  // 0 power law, 1 linear, 2 NLC, 3 polymer
   int n, m;
   double inv_ds, inv_ds2, inv_ds3;
   double C;       // f0 = C h^3
   double A1, B1;  // f1 = A1 s^(m-2) - B1 s^(n-2), s = 1/h
   double c0, c1;  // linear model
+  double b;       // precursor scale of the NLC Pi
+  double nlc_K, nlc_N, nlc_beta, nlc_w;
+  double pol_C, pol_A1, pol_A2, pol_d;  // A1 = A_SiOx, A2 = A_Si
 };
 
 struct StepK {
@@ -129,6 +132,8 @@ template <class T> struct MobC {
   int model, n, m;
   bool unitC;  // C == 1
   bool pl32;   // power law with (n, m) = (3, 2)
+  // NLC and polymer parameters (evaluated out of line, see pi_model)
+  double Cd, b, K, N, beta2, w, pC, pA1, pA12, pd;
 };
 template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
   MobC<T> c;
@@ -146,6 +151,16 @@ template <class T> TF_HD MobC<T> mob_consts(const ModelK& M) {
   c.m = M.m;
   c.unitC = M.C == 1.0;
   c.pl32 = M.model == 0 && M.n == 3 && M.m == 2;
+  c.Cd = M.C;
+  c.b = M.b;
+  c.K = M.nlc_K;
+  c.N = M.nlc_N;
+  c.beta2 = M.nlc_beta * M.nlc_beta;
+  c.w = M.nlc_w;
+  c.pC = M.pol_C;
+  c.pA1 = M.pol_A1;
+  c.pA12 = M.pol_A1 - M.pol_A2;
+  c.pd = M.pol_d;
   return c;
 }
 
@@ -195,6 +210,56 @@ template <class T> struct MobPair {
   T a, b;
 };
 
+// Pi', Pi'' of the NLC and polymer models (Sec. Thin Film Models), in R =
+// float (the FP32 Jacobian) or double (everything FP64-class):
+//   NLC (eqs. DisjPressNLC, mh_model): Pi = K[r^3 - r^2] + (N/2) q^2, r = b/h,
+//     q = m(h)/h = g h/D, D = h^2 + beta^2, g = [1 + tanh((h - 2b)/w)]/2;
+//     Pi' = K(2r^2 - 3r^3)/h + N q q',  Pi'' = K(12r^3 - 6r^2)/h^2 + N(q'^2 + q q''),
+//     q' = g' h/D + g(beta^2 - h^2)/D^2,
+//     q'' = g'' h/D + 2g'(beta^2 - h^2)/D^2 + 2g h(h^2 - 3beta^2)/D^3,
+//     g' = (1 - t^2)/(2w), g'' = -t(1 - t^2)/w^2, t = tanh((h - 2b)/w).
+//   Polymer (eq. DisjPressPolymer), Pi = -psi':
+//     Pi' = -72 Cp/h^10 + A1/(2 pi h^4) - (A1 - A2)/(2 pi (h + d)^4),
+//     Pi'' = 720 Cp/h^11 - 2A1/(pi h^5) + 2(A1 - A2)/(pi (h + d)^5).
+__host__ __device__ inline float r_tanh(float x) { return tanhf(x); }
+__host__ __device__ inline double r_tanh(double x) { return tanh(x); }
+template <class R, class T>
+__host__ __device__ inline void pi_model(const MobC<T>& c, R h, R& d1, R& d2) {
+  if (c.model == 3) {
+    const R pi = R(3.14159265358979323846);
+    const R Cp = R(c.pC), A1 = R(c.pA1), A12 = R(c.pA12), e = h + R(c.pd);
+    const R h2 = h * h, h4 = h2 * h2, h5 = h4 * h, h10 = h5 * h5, e2 = e * e, e4 = e2 * e2;
+    d1 = R(-72) * Cp / h10 + A1 / (R(2) * pi * h4) - A12 / (R(2) * pi * e4);
+    d2 = R(720) * Cp / (h10 * h) - R(2) * A1 / (pi * h5) + R(2) * A12 / (pi * e4 * e);
+    return;
+  }
+  const R b = R(c.b), K = R(c.K), N = R(c.N), be2 = R(c.beta2), w = R(c.w);
+  const R r = b / h, r2 = r * r, r3 = r2 * r;
+  const R t = r_tanh((h - R(2) * b) / w), sech2 = R(1) - t * t;
+  const R g = R(0.5) * (R(1) + t), dg = sech2 / (R(2) * w), d2g = -t * sech2 / (w * w);
+  const R D = h * h + be2, bmh = be2 - h * h;
+  const R q = g * h / D;
+  const R dq = dg * h / D + g * bmh / (D * D);
+  const R d2q = d2g * h / D + R(2) * dg * bmh / (D * D) + g * R(2) * h * (h * h - R(3) * be2) / (D * D * D);
+  d1 = K * (R(2) * r2 - R(3) * r3) / h + N * q * dq;
+  d2 = K * (R(12) * r3 - R(6) * r2) / (h * h) + N * (dq * dq + q * d2q);
+}
+// Height and values between T and the arithmetic R of pi_model: float stays
+// float; double and double-float evaluate in double.
+template <class T> struct PiArith {
+  typedef double R;
+};
+template <> struct PiArith<float> {
+  typedef float R;
+};
+__host__ __device__ inline double to_r(double x) { return x; }
+__host__ __device__ inline float to_r(float x) { return x; }
+__host__ __device__ inline double to_r(df64 x) { return f64_of_df(x); }
+template <class T> __host__ __device__ inline T from_r(typename PiArith<T>::R x);
+template <> __host__ __device__ inline double from_r<double>(double x) { return x; }
+template <> __host__ __device__ inline float from_r<float>(float x) { return x; }
+template <> __host__ __device__ inline df64 from_r<df64>(double x) { return df_of_f64(x); }
+
 // f0 = C h^3 and f1 = h^3 Pi'(h) = A1 h^(2-m) - B1 h^(2-n)
 // (Sec. Thin Film Models, eq. GeneralDisPreForm); the linear model has
 // constant f0 = c0, f1 = c1.  General exponents and the linear model are
@@ -206,6 +271,15 @@ __host__ __device__ __noinline__ MobPair<T> mobility_general(const MobC<T> c, co
   if (c.model == 1) {
     r.a = c.c0;
     r.b = c.c1;
+    return r;
+  }
+  if (c.model >= 2) {  // NLC, polymer: f0 = C h^3, f1 = h^3 Pi'
+    typedef typename PiArith<T>::R R;
+    const R hr = to_r(h), h3 = hr * hr * hr;
+    R d1, d2;
+    pi_model<R>(c, hr, d1, d2);
+    r.a = from_r<T>(R(c.Cd) * h3);
+    r.b = from_r<T>(h3 * d1);
     return r;
   }
   r.a = c.unitC ? (h * h) * h : c.C * (h * h) * h;
@@ -221,6 +295,15 @@ __host__ __device__ __noinline__ MobPair<T> mobility_d_general(const MobC<T> c, 
   if (c.model == 1) {
     r.a = zero<T>();
     r.b = zero<T>();
+    return r;
+  }
+  if (c.model >= 2) {  // f0' = 3 C h^2, f1' = 3 h^2 Pi' + h^3 Pi''
+    typedef typename PiArith<T>::R R;
+    const R hr = to_r(h), h2 = hr * hr;
+    R d1, d2;
+    pi_model<R>(c, hr, d1, d2);
+    r.a = from_r<T>(R(3) * R(c.Cd) * h2);
+    r.b = from_r<T>(R(3) * h2 * d1 + h2 * hr * d2);
     return r;
   }
   r.a = c.three * c.C * (h * h);

@@ -44,6 +44,7 @@ int main(void) {
          sizeof(tf_norms));
   O(tf_params, ds); O(tf_params, kappa); O(tf_params, theta); O(tf_params, newton_fixed_iter);
   O(tf_params, grow_after); O(tf_params, rupture_h); O(tf_params, precision);
+  O(tf_params, nlc_K); O(tf_params, nlc_w); O(tf_params, pol_C); O(tf_params, pol_d);
   O(tf_step_record, accepted); O(tf_step_record, hmin); O(tf_advance_info, dt);
   return 0;
 }
