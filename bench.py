@@ -272,13 +272,22 @@ def roofline_hbm(res, N, lp_bytes, pk, traffic_per_cell=None):
                                achieved=round(it_ach, 1), frac=round(it_ach / pk["hbm_gbs"], 4)))
 
 
+MODEL_NAMES = {0: "power-law", 1: "linear", 2: "NLC", 3: "polymer"}
+
+
+def oracle_model(O, w, n):
+    """The oracle's model of a workload on an n x n grid (the workload's
+    spacing); the NLC and polymer parameters are the paper's sets."""
+    return O.Model(nx=n, ny=n, ds=w["ds"], model=w.get("model", 0), kappa=w["kappa"], b=w["b"],
+                   n=w["n"], m=w["m"], cap_C=w["cap_C"], theta=w["theta"])
+
+
 def cpu_baseline_sample(w, h0):
     """FP64 oracle on the host cores: the first time step of the workload."""
     import oracle as O
     O.build()
     N = w["N"]
-    M = O.Model(nx=N, ny=N, ds=w["ds"], kappa=w["kappa"], b=w["b"], n=w["n"], m=w["m"],
-                cap_C=w["cap_C"], theta=w["theta"])
+    M = oracle_model(O, w, N)
     ctl = O.Control(tol=w["tol"], max_iter=w["max_iter"])
     t = time.perf_counter()
     _, info = O.step(M, ctl, h0, w["dt0"])
@@ -298,8 +307,7 @@ def reference_arm(args, w):
     from paper_1806_10550_gb300 import synthetic as S
     O.build()
     n = 512
-    M = O.Model(nx=n, ny=n, ds=w["ds"], kappa=w["kappa"], b=w["b"], n=w["n"], m=w["m"],
-                cap_C=w["cap_C"], theta=w["theta"])
+    M = oracle_model(O, w, n)
     ctl = O.Control(tol=w["tol"], max_iter=w["max_iter"], dt_min=w["dt_min"],
                     dt_max=w["dt_max"], dt_shrink=w["dt_shrink"], dt_grow=w["dt_grow"],
                     grow_after=w["grow_after"])
@@ -379,7 +387,8 @@ def main():
         scaling="weak", vs_baseline=None,
         dtype=("f32 solves + f32x2 double-float residual, f64 state" if head == "f32b" else "f64"),
         data="synthetic",
-        config=dict(workload=f"{N}x{N} spinodal film, 64 lambda_m square, seed {w['seed']}",
+        config=dict(workload=(f"{N}x{N} spinodal film, {MODEL_NAMES[w.get('model', 0)]} model, "
+                              f"{w['P']} lambda_m square, seed {w['seed']}"),
                     mode=("FP32-bulk" if head == "f32b" else "FP64"),
                     dt_sequence=("replayed from the FP64 run" if head == "f32b" and "fp64" in res
                                  else "adaptive"),

@@ -272,7 +272,8 @@ def params_for_workload(w: dict, precision: int = TF_FP64, **overrides) -> TfPar
         newton_tol=float(w["tol"]), newton_max_iter=int(w["max_iter"]),
         dt_min=float(w["dt_min"]), dt_max=float(w["dt_max"]), dt_shrink=float(w["dt_shrink"]),
         dt_grow=float(w["dt_grow"]), grow_after=int(w["grow_after"]),
-        rupture_h=float(w["rupture_h"]), precision=precision)
+        rupture_h=float(w["rupture_h"]), model=int(w.get("model", TF_MODEL_POWERLAW)),
+        precision=precision)
     for k, v in overrides.items():
         setattr(p, k, v)
     return p

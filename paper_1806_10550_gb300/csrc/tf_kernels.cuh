@@ -225,24 +225,26 @@ __host__ __device__ inline float r_tanh(float x) { return tanhf(x); }
 __host__ __device__ inline double r_tanh(double x) { return tanh(x); }
 template <class R, class T>
 __host__ __device__ inline void pi_model(const MobC<T>& c, R h, R& d1, R& d2) {
+  const R ih = R(1) / h;
   if (c.model == 3) {
     const R pi = R(3.14159265358979323846);
-    const R Cp = R(c.pC), A1 = R(c.pA1), A12 = R(c.pA12), e = h + R(c.pd);
-    const R h2 = h * h, h4 = h2 * h2, h5 = h4 * h, h10 = h5 * h5, e2 = e * e, e4 = e2 * e2;
-    d1 = R(-72) * Cp / h10 + A1 / (R(2) * pi * h4) - A12 / (R(2) * pi * e4);
-    d2 = R(720) * Cp / (h10 * h) - R(2) * A1 / (pi * h5) + R(2) * A12 / (pi * e4 * e);
+    const R Cp = R(c.pC), A1 = R(c.pA1), A12 = R(c.pA12), ie = R(1) / (h + R(c.pd));
+    const R i2 = ih * ih, i4 = i2 * i2, i5 = i4 * ih, i10 = i5 * i5, e2 = ie * ie, e4 = e2 * e2;
+    const R k = R(1) / (R(2) * pi);
+    d1 = R(-72) * Cp * i10 + k * (A1 * i4 - A12 * e4);
+    d2 = R(720) * Cp * i10 * ih - R(4) * k * (A1 * i5 - A12 * e4 * ie);
     return;
   }
-  const R b = R(c.b), K = R(c.K), N = R(c.N), be2 = R(c.beta2), w = R(c.w);
-  const R r = b / h, r2 = r * r, r3 = r2 * r;
-  const R t = r_tanh((h - R(2) * b) / w), sech2 = R(1) - t * t;
-  const R g = R(0.5) * (R(1) + t), dg = sech2 / (R(2) * w), d2g = -t * sech2 / (w * w);
-  const R D = h * h + be2, bmh = be2 - h * h;
-  const R q = g * h / D;
-  const R dq = dg * h / D + g * bmh / (D * D);
-  const R d2q = d2g * h / D + R(2) * dg * bmh / (D * D) + g * R(2) * h * (h * h - R(3) * be2) / (D * D * D);
-  d1 = K * (R(2) * r2 - R(3) * r3) / h + N * q * dq;
-  d2 = K * (R(12) * r3 - R(6) * r2) / (h * h) + N * (dq * dq + q * d2q);
+  const R b = R(c.b), K = R(c.K), N = R(c.N), be2 = R(c.beta2), iw = R(1) / R(c.w);
+  const R r = b * ih, r2 = r * r, r3 = r2 * r;
+  const R t = r_tanh((h - R(2) * b) * iw), sech2 = R(1) - t * t;
+  const R g = R(0.5) * (R(1) + t), dg = R(0.5) * sech2 * iw, d2g = -t * sech2 * iw * iw;
+  const R iD = R(1) / (h * h + be2), bmh = be2 - h * h;
+  const R q = g * h * iD;
+  const R dq = (dg * h + g * bmh * iD) * iD;
+  const R d2q = (d2g * h + (R(2) * dg * bmh + g * R(2) * h * (h * h - R(3) * be2) * iD) * iD) * iD;
+  d1 = K * (R(2) * r2 - R(3) * r3) * ih + N * q * dq;
+  d2 = K * (R(12) * r3 - R(6) * r2) * ih * ih + N * (dq * dq + q * d2q);
 }
 // Height and values between T and the arithmetic R of pi_model: float stays
 // float; double and double-float evaluate in double.
@@ -312,6 +314,24 @@ __host__ __device__ __noinline__ MobPair<T> mobility_d_general(const MobC<T> c, 
   return r;
 }
 
+// f0, f1, f0', f1' of the NLC and polymer models in one out-of-line call.
+template <class T> struct MobQuad {
+  T f0, f1, d0, d1;
+};
+template <class T>
+__host__ __device__ __noinline__ MobQuad<T> mobility_model_all(const MobC<T> c, const T h) {
+  typedef typename PiArith<T>::R R;
+  const R hr = to_r(h), h2 = hr * hr, h3 = h2 * hr;
+  R d1, d2;
+  pi_model<R>(c, hr, d1, d2);
+  MobQuad<T> q;
+  q.f0 = from_r<T>(R(c.Cd) * h3);
+  q.f1 = from_r<T>(h3 * d1);
+  q.d0 = from_r<T>(R(3) * R(c.Cd) * h2);
+  q.d1 = from_r<T>(R(3) * h2 * d1 + h3 * d2);
+  return q;
+}
+
 template <class T>
 TF_HD void mobility(const MobC<T>& c, const T& h, const T& s, T& f0, T& f1) {
   if (c.pl32) {  // f1 = A1 - B1 / h
@@ -323,6 +343,22 @@ TF_HD void mobility(const MobC<T>& c, const T& h, const T& s, T& f0, T& f1) {
   f0 = r.a;
   f1 = r.b;
 }
+// f0, f1 and their derivatives together (one evaluation of Pi for the NLC
+// and polymer models).
+template <class T>
+TF_HD void mobility_all(const MobC<T>& c, const T& h, const T& s, T& f0, T& f1, T& d0, T& d1) {
+  if (c.model >= 2) {
+    const MobQuad<T> q = mobility_model_all(c, h);
+    f0 = q.f0;
+    f1 = q.f1;
+    d0 = q.d0;
+    d1 = q.d1;
+    return;
+  }
+  mobility(c, h, s, f0, f1);
+  mobility_d(c, h, s, d0, d1);
+}
+
 template <class T>
 TF_HD void mobility_d(const MobC<T>& c, const T& h, const T& s, T& d0, T& d1) {
   if (c.pl32) {  // f1' = B1 / h^2

@@ -152,8 +152,7 @@ __device__ __forceinline__ CellS<LP> cell_scaled(const MobC<LP>& ml, LP inv_ds2,
   X.lap = (((U(0, 1) - uc) + (U(0, -1) - uc)) + ((U(1, 0) - uc) + (U(-1, 0) - uc))) * inv_ds2;
   const LP s = rcp(uc);
   LP f0, f1, d0, d1;
-  mobility(ml, uc, s, f0, f1);
-  mobility_d(ml, uc, s, d0, d1);
+  mobility_all(ml, uc, s, f0, f1, d0, d1);
   X.F0 = k3 * f0;
   X.F1 = k1 * f1;
   X.D0 = k1 * d0;

@@ -229,8 +229,7 @@ __device__ __forceinline__ CellLP<LP> cell_values(const MobC<LP>& ml, LP inv_ds2
   X.u = uc;
   X.lap = (((U(0, 1) - uc) + (U(0, -1) - uc)) + ((U(1, 0) - uc) + (U(-1, 0) - uc))) * inv_ds2;
   LP s = rcp(uc);
-  mobility(ml, uc, s, X.f0, X.f1);
-  mobility_d(ml, uc, s, X.d0, X.d1);
+  mobility_all(ml, uc, s, X.f0, X.f1, X.d0, X.d1);
   return X;
 }
 

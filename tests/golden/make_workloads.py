@@ -16,6 +16,12 @@ theta_c = 20 deg, M = 1/2, C = 1, h0 = 1):
   adjoint1k 1024^2 on 16 lambda_m
 Step control: dt_max = 0.01/sigma_max, dt_min = 1e-9, shrink 1/2, grow 5/4
 after 5 accepted steps, K = 10 Newton iterations, tol 1e-10.
+
+Model variants (Sec. Thin Film Models), the scale8k geometry in units of each
+model's own lambda_m and sigma_max, the flat heights of Sec. Validation:
+  nlc8k     NLC (eq. NLC_paras: C = 0.0857, b = 0.01), h0 = 0.5
+  pol8k     polymer (eq. Polymer_scales: C = 0.00581), h0 = 3.9
+with dt0 * sigma_max and dt_max * sigma_max equal to scale8k's.
 """
 import json
 import math
@@ -32,7 +38,7 @@ def main():
     M = O.Model(nx=1, ny=1, ds=1.0, kappa=kappa, b=b, n=n, m=m)
     qm, sm = O.lsa(M, 1.0)
     lam = 2.0 * math.pi / qm
-    common = dict(b=b, n=n, m=m, theta_c=th, kappa=kappa, cap_C=1.0, h0=1.0,
+    common = dict(model=0, b=b, n=n, m=m, theta_c=th, kappa=kappa, cap_C=1.0, h0=1.0,
                   theta=0.5, lambda_m=lam, sigma_max=sm, tol=1e-10, max_iter=10,
                   dt_min=1e-9, dt_max=0.01 / sm, dt_shrink=0.5, dt_grow=1.25,
                   grow_after=5, rupture_h=2.0 * b)
@@ -49,6 +55,14 @@ def main():
     }
     for w in W.values():
         w["ds"] = w["P"] * lam / w["N"]
+    # model variants: NLC (model 2) and polymer (model 3)
+    for name, model, C, bb, h0 in (("nlc8k", 2, 0.0857, 0.01, 0.5), ("pol8k", 3, 0.00581, 0.1, 3.9)):
+        Mv = O.Model(nx=1, ny=1, ds=1.0, model=model, cap_C=C, b=bb)
+        qv, sv = O.lsa(Mv, h0)
+        lv = 2.0 * math.pi / qv
+        W[name] = dict(common, model=model, cap_C=C, b=bb, h0=h0, lambda_m=lv, sigma_max=sv,
+                       N=8192, P=64, eps=0.01, seed=1239, dt0=1e-3 * sm / sv, T=1e30,
+                       dt_max=0.01 / sv, steps=40, ds=64 * lv / 8192, rupture_h=0.0)
     out = os.path.join(os.path.dirname(__file__), "workloads.json")
     with open(out, "w") as f:
         json.dump(W, f, indent=1, sort_keys=True)
