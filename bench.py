@@ -332,6 +332,106 @@ def reference_arm(args, w):
     print(json.dumps(line))
 
 
+def ensemble_params(tf, w, f, mode):
+    """tf_params of one film of the ensemble workload."""
+    import math
+    return tf.tf_params_default(
+        nx=f["N"], ny=f["N"], ds=f["ds"], b=w["b"], n=w["n"], m=w["m"], kappa=f["kappa"],
+        contact_angle=math.radians(f["theta_c_deg"]), theta=w["theta"], newton_tol=w["tol"],
+        newton_max_iter=w["max_iter"], dt_min=w["dt_min"], dt_max=f["dt_max"],
+        dt_shrink=w["dt_shrink"], dt_grow=w["dt_grow"], grow_after=w["grow_after"], precision=mode)
+
+
+def run_ensemble(args, w):
+    """Many independent films of uneven sizes advanced together on one GPU
+    (tf_ensemble_advance), against the same films advanced one after another
+    (tf_advance).  Films are sharded across ranks (weak scaling)."""
+    import torch
+    import paper_1806_10550_gb300 as tf
+    from paper_1806_10550_gb300 import synthetic as S
+    rank, world, local, dist = dist_setup()
+    tf.library(build_if_missing=True)
+    mode = tf.TF_FP32_BULK
+    films = w["films"][rank::world]
+    A = args.steps if args.steps != 200 else w["attempts"]
+    ctxs, init, grids = [], [], []
+    for f in films:
+        ctxs.append(tf.Context(ensemble_params(tf, w, f, mode), stream=torch.cuda.Stream()))
+        init.append(torch.from_numpy(S.spinodal_film(f["N"], f["N"], w["h0"], w["eps"], f["seed"])).cuda())
+        grids.append(torch.empty_like(init[-1]))
+    dt0 = [f["dt0"] for f in films]
+
+    def reset():
+        for g, h in zip(grids, init):
+            g.copy_(h)
+        torch.cuda.synchronize()
+
+    # warm-up: W attempts per film
+    reset()
+    tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, dt0, args.warmup)
+    for c in ctxs:
+        tf.tf_timing_enable(c, True)
+    reset()
+    barrier(dist)
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with clocks:
+        e0.record()
+        infos = tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, dt0, A)
+        e1.record()
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = e0.elapsed_time(e1)
+    launches = sum(tf.tf_timing_get(c)["launches"] for c in ctxs)
+    cells = sum(f["N"] ** 2 * i["accepted"] for f, i in zip(films, infos))
+    iters = sum(i["newton_iterations"] for i in infos)
+    value = job_rate(dist, cells, ms)
+    # the same films, one after another
+    reset()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    seq = [tf.tf_advance(c, g, 0.0, 1e30, d, A, records=False)[0] for c, g, d in zip(ctxs, grids, dt0)]
+    e3.record()
+    torch.cuda.synchronize()
+    ms_seq = e2.elapsed_time(e3)
+    assert [i["accepted"] for i in seq] == [i["accepted"] for i in infos]
+    cs = clocks.summary()
+    sizes = sorted({f["N"] for f in w["films"]})
+    line = dict(
+        metric="film cell-updates/s over a 256-film ensemble",
+        value=value, unit="cell-updates/s", n_gpus=world, steps=A, warmup=args.warmup,
+        ms_per_step=ms / max(1, A), higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32 solves + f32x2 double-float residual, f64 state", data="synthetic",
+        config=dict(workload=(f"{len(w['films'])} spinodal films, N in {sizes}, contact angle "
+                              f"10-40 deg, each on {w['P']} of its lambda_m, {A} attempts each"),
+                    mode="FP32-bulk", global_batch=len(w["films"]),
+                    l2="working set larger than L2 (5 GB of films and workspace)",
+                    parallelism=f"films sharded over {world} rank(s)"),
+        accepted_steps=sum(i["accepted"] for i in infos), newton_iterations=iters,
+        sequential_value=job_rate(dist, cells, ms_seq), speedup_vs_sequential=ms_seq / ms,
+        gpu_launches=launches,
+        clocks=dict(sm_mhz=cs["sm_mhz"], sm_max_mhz=cs["sm_max_mhz"], reasons=cs["reasons"]),
+    )
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        f = next(x for x in w["films"] if x["N"] == 256)
+        M = O.Model(nx=256, ny=256, ds=f["ds"], kappa=f["kappa"], b=w["b"], n=w["n"], m=w["m"])
+        ctl = O.Control(tol=w["tol"], max_iter=w["max_iter"], dt_max=f["dt_max"])
+        h = S.spinodal_film(256, 256, w["h0"], w["eps"], f["seed"])
+        t = time.perf_counter()
+        r = O.advance(M, ctl, h, 0.0, 1e30, f["dt0"], 10)
+        el = time.perf_counter() - t
+        acc = sum(x["accepted"] for x in r.records)
+        line["cpu_baseline"] = dict(value=256 * 256 * acc / el, unit="cell-updates/s",
+                                    cores=O.num_threads(), kind="oracle",
+                                    sample=f"10 attempts of one 256^2 film of the ensemble, {el:.1f} s")
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,6 +445,9 @@ def main():
     ap.add_argument("--modes", default="fp64,f32b")
     args = ap.parse_args()
     w = load_workload(args.workload)
+    if args.workload == "ensemble" and args.impl == "ours":
+        run_ensemble(args, w)
+        return
     if args.impl == "reference":
         reference_arm(args, w)
         return

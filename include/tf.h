@@ -201,6 +201,24 @@ int tf_advance(tf_ctx* ctx, double* h, double t0, double t_end, double dt0,
                int max_attempts, const double* dt_replay, const int* iter_replay,
                tf_step_record* records, tf_advance_info* info);
 
+/* Advance n independent films together.  Film i is advanced exactly as
+ * tf_advance(ctx[i], h[i], t0[i], t_end[i], dt0[i], max_attempts[i], NULL,
+ * NULL, NULL, &info[i]) would advance it -- the same kernels in the same
+ * order, the same decisions, bit-identical grids -- but one host thread
+ * keeps the work of all films queued on their contexts' streams at once,
+ * so that the kernels of small films run side by side on the GPU (the
+ * many-film statistics runs of Sec. Results; no counterpart in the paper's
+ * implementation).  Give each context its own stream: contexts that share a
+ * stream are correct but serialised.  ctx: n distinct contexts; h: n device
+ * grids, each of its context's shape (advanced in place); t0, t_end, dt0,
+ * max_attempts: n host values each; info: n host records, required.
+ * Returns TF_OK, or a negative error at the first failing call (work of
+ * other films may then still be queued: synchronise or destroy the
+ * contexts).                                                             */
+int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const double* t0,
+                        const double* t_end, const double* dt0, const int* max_attempts,
+                        tf_advance_info* info);
+
 /* Kernel timing of a context, for measurement.  While enabled, the library
  * records CUDA events on its stream around every kernel it launches and
  * accumulates their durations per kernel kind; the sums are taken at the

@@ -8,7 +8,7 @@ CPU fallback: without the built library or a CUDA device every call raises.
 
 Functions carry the names of the C ABI: ``tf_params_default``, ``tf_init``,
 ``tf_destroy``, ``tf_residual``, ``tf_newton_iteration``,
-``tf_newton_adi_step``, ``tf_advance``, ``tf_strerror``.
+``tf_newton_adi_step``, ``tf_advance``, ``tf_ensemble_advance``, ``tf_strerror``.
 """
 from __future__ import annotations
 
@@ -110,10 +110,13 @@ def library(build_if_missing: bool = True):
     L.tf_newton_adi_step.argtypes = [vp, vp, vp, dp, C.POINTER(TfStepInfo)]
     L.tf_advance.argtypes = [vp, vp, dp, dp, dp, C.c_int, vp, vp, C.POINTER(TfStepRecord),
                              C.POINTER(TfAdvanceInfo)]
+    L.tf_ensemble_advance.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(dp),
+                                      C.POINTER(dp), C.POINTER(dp), C.POINTER(C.c_int),
+                                      C.POINTER(TfAdvanceInfo)]
     L.tf_timing_enable.argtypes = [vp, C.c_int]
     L.tf_timing_get.argtypes = [vp, C.POINTER(TfTiming)]
     for f in ("tf_init", "tf_residual", "tf_newton_iteration", "tf_newton_adi_step", "tf_advance",
-              "tf_timing_enable", "tf_timing_get"):
+              "tf_ensemble_advance", "tf_timing_enable", "tf_timing_get"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -251,6 +254,32 @@ def tf_advance(ctx: Context, h, t0: float, t_end: float, dt0: float, max_attempt
                             status=r.status, err=r.err, gnorm=r.gnorm, mass=r.mass, hmin=r.hmin))
     return dict(status=info.status, attempts=info.attempts, accepted=info.accepted,
                 newton_iterations=info.newton_iterations, t=info.t, dt=info.dt), out
+
+
+def tf_ensemble_advance(ctxs, hs, t0, t_end, dt0, max_attempts):
+    """Advance independent films together (``tf_advance`` on each, their
+    work interleaved on the contexts' streams).  ``ctxs``: contexts, one per
+    film, each best on its own stream; ``hs``: their grids (advanced in
+    place); ``t0``, ``t_end``, ``dt0``, ``max_attempts``: one value or one per
+    film.  Returns one info dict per film."""
+    n = len(ctxs)
+    if len(hs) != n:
+        raise ValueError("one grid per context")
+
+    def arr(v, ctype):
+        vals = list(v) if hasattr(v, "__len__") else [v] * n
+        if len(vals) != n:
+            raise ValueError("one value per film")
+        return (ctype * max(1, n))(*vals)
+
+    ctx_a = (C.c_void_p * max(1, n))(*[c.handle.value for c in ctxs])
+    h_a = (C.c_void_p * max(1, n))(*[c.ptr(h, "h").value for c, h in zip(ctxs, hs)])
+    infos = (TfAdvanceInfo * max(1, n))()
+    _check(library().tf_ensemble_advance(n, ctx_a, h_a, arr(t0, C.c_double), arr(t_end, C.c_double),
+                                         arr(dt0, C.c_double), arr(max_attempts, C.c_int), infos),
+           "tf_ensemble_advance")
+    return [dict(status=i.status, attempts=i.attempts, accepted=i.accepted,
+                 newton_iterations=i.newton_iterations, t=i.t, dt=i.dt) for i in infos[:n]]
 
 
 def tf_timing_enable(ctx: Context, on: bool = True):

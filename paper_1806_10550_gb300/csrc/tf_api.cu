@@ -10,6 +10,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <thread>
+#include <vector>
+
 #include "tf_internal.h"
 
 using tf::Scalars;
@@ -26,11 +29,17 @@ int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? TF_ERR_NO
 
 double mass_of(double fixed) { return fixed * 0x1p-36; }
 
-// Reduce the partials of the last passes into c.hsc (blocking).
-int finalize(tf_ctx& c, int n_px, int n_py) {
+// Reduce the partials of the last passes into the pinned c.hsc: the launch
+// and the copy are queued on the context's stream; finalize() also waits.
+int finalize_async(tf_ctx& c, int n_px, int n_py) {
   tf::k_finalize<<<1, 256, 0, c.stream>>>(c.px, n_px, c.py, n_py, c.dsc);
   TF_CK(cudaGetLastError());
   TF_CK(cudaMemcpyAsync(c.hsc, c.dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
+  return TF_OK;
+}
+int finalize(tf_ctx& c, int n_px, int n_py) {
+  int r = finalize_async(c, n_px, n_py);
+  if (r) return r;
   TF_CK(cudaStreamSynchronize(c.stream));
   return TF_OK;
 }
@@ -41,9 +50,10 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 }
 
 // One pseudo-Newton ADI iteration from u_k (b^n already formed):
-// residual -> x sweep -> y sweep -> reductions.
-int iterate(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_out, double* v_out,
-            Scalars* s) {
+// residual -> x sweep -> y sweep -> reductions, queued on the context's
+// stream; iterate_collect() reads the result once the stream has reached it.
+int iterate_launch(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_out,
+                   double* v_out) {
   const bool tm = c.timing.enabled;
   if (tm) TF_CK(cudaEventRecord(c.ev[0], c.stream));
   TF_CK(c.ops->rhs(c, u_k, dt));
@@ -54,9 +64,10 @@ int iterate(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_o
   if (tm) TF_CK(cudaEventRecord(c.ev[3], c.stream));
   TF_CK(c.ops->ysweep(c, u_k, dt, u_next, v_out));
   if (tm) TF_CK(cudaEventRecord(c.ev[4], c.stream));
-  int r = finalize(c, c.n_rhs_parts + c.grid_x, c.grid_y);
-  if (r) return r;
-  if (tm) {
+  return finalize_async(c, c.n_rhs_parts + c.grid_x, c.grid_y);
+}
+void iterate_collect(tf_ctx& c, bool w_out, Scalars* s) {
+  if (c.timing.enabled) {
     c.timing.rhs_ms += elapsed(c.ev[0], c.ev[1]);
     c.timing.x_ms += elapsed(c.ev[1], c.ev[2]);
     c.timing.y_ms += elapsed(c.ev[3], c.ev[4]);
@@ -66,34 +77,49 @@ int iterate(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_o
     c.timing.launches += 4 + (w_out && c.ops->lp_bytes != sizeof(double) ? 1 : 0);
   }
   *s = *c.hsc;
+}
+int iterate(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_out, double* v_out,
+            Scalars* s) {
+  int r = iterate_launch(c, u_k, dt, u_next, w_out, v_out);
+  if (r) return r;
+  TF_CK(cudaStreamSynchronize(c.stream));
+  iterate_collect(c, w_out != nullptr, s);
   return TF_OK;
 }
 
-int explicit_timed(tf_ctx& c, const double* h_old, double dt) {
+// The explicit part of a step; with timing on, its events (5, 6) are read
+// by explicit_collect() once the stream has passed them.
+int explicit_launch(tf_ctx& c, const double* h_old, double dt) {
   const bool tm = c.timing.enabled;
-  if (tm) TF_CK(cudaEventRecord(c.ev[0], c.stream));
+  if (tm) TF_CK(cudaEventRecord(c.ev[5], c.stream));
   TF_CK(c.ops->explicit_part(c, h_old, dt));
-  if (tm) {
-    TF_CK(cudaEventRecord(c.ev[1], c.stream));
-    TF_CK(cudaEventSynchronize(c.ev[1]));
-    c.timing.explicit_ms += elapsed(c.ev[0], c.ev[1]);
-    c.timing.explicit_launches++;
-    c.timing.launches++;
-  }
+  if (tm) TF_CK(cudaEventRecord(c.ev[6], c.stream));
   return TF_OK;
 }
+void explicit_collect(tf_ctx& c) {
+  if (!c.timing.enabled) return;
+  c.timing.explicit_ms += elapsed(c.ev[5], c.ev[6]);
+  c.timing.explicit_launches++;
+  c.timing.launches++;
+}
 
-// Mass and min h of a film (once per step), into s->mass and s->hmin.
-int film_stats(tf_ctx& c, const double* h, Scalars* s) {
+// Mass and min h of a film (once per step), into s->mass and s->hmin:
+// stats_launch queues the reduction, stats_collect reads it.
+int stats_launch(tf_ctx& c, const double* h) {
   tf::k_grid_stats<<<c.grid_stats, 256, 0, c.stream>>>(h, c.N, c.py);
   TF_CK(cudaGetLastError());
   if (c.timing.enabled) c.timing.launches += 2;
-  tf::k_finalize<<<1, 256, 0, c.stream>>>(c.px, 0, c.py, c.grid_stats, c.dsc);
-  TF_CK(cudaGetLastError());
-  TF_CK(cudaMemcpyAsync(c.hsc, c.dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
-  TF_CK(cudaStreamSynchronize(c.stream));
+  return finalize_async(c, 0, c.grid_stats);
+}
+void stats_collect(tf_ctx& c, Scalars* s) {
   s->mass = c.hsc->mass;
   s->hmin = c.hsc->hmin;
+}
+int film_stats(tf_ctx& c, const double* h, Scalars* s) {
+  int r = stats_launch(c, h);
+  if (r) return r;
+  TF_CK(cudaStreamSynchronize(c.stream));
+  stats_collect(c, s);
   return TF_OK;
 }
 
@@ -119,7 +145,7 @@ void fill_info(tf_step_info* info, int status, int it, const Scalars& s) {
 // A time step with an explicit fixed-iteration override (0 = none).
 // The iterate ping-pongs between h_new and c.ubuf; the result is in h_new.
 int step(tf_ctx& c, const double* h_old, double* h_new, double dt, int fixed_iter, tf_step_info* info) {
-  int re = explicit_timed(c, h_old, dt);
+  int re = explicit_launch(c, h_old, dt);
   if (re) return re;
   const int kmax = fixed_iter > 0 ? fixed_iter : c.p.newton_max_iter;
   const double* uk = h_old;
@@ -131,6 +157,7 @@ int step(tf_ctx& c, const double* h_old, double* h_new, double dt, int fixed_ite
     double* un = bufs[k & 1];
     int r = iterate(c, uk, dt, un, nullptr, nullptr, &s);
     if (r) return r;
+    if (k == 0) explicit_collect(c);
     it = k + 1;
     uk = un;
     status = classify(c, s, it, fixed_iter);
@@ -142,6 +169,134 @@ int step(tf_ctx& c, const double* h_old, double* h_new, double dt, int fixed_ite
   if (rs) return rs;
   fill_info(info, status, it, s);
   return status;
+}
+
+// ---------------------------------------------------------------------------
+// Ensembles of independent films (the many-film statistics runs of Sec.
+// Results).  Each film runs the state machine of tf_advance -- the same
+// kernels, in the same order, with the same decisions and results -- but
+// every wait on the GPU becomes a resumable state, so one host thread keeps
+// the work of many films queued on their own streams at once: small films
+// leave most SMs idle, and their kernels then run side by side.
+
+struct FilmRun {
+  tf_ctx* c;
+  double* h;
+  double t, t_end, dt;
+  int max_att;
+  tf_advance_info* info;
+  double *cur, *nxt;
+  int streak, a, status;
+  bool done;
+  // the attempt in flight
+  double step_dt;
+  int last, fixed, kmax, k, it, sstatus, phase;  // phase 1: iterating, 2: film statistics
+  const double* uk;
+  double* bufs[2];
+  Scalars s;
+};
+
+int film_finish(FilmRun& F) {
+  if (F.status == TF_ADV_MAX_ATTEMPTS && F.t >= F.t_end) F.status = TF_ADV_DONE;
+  if (F.cur != F.h)
+    TF_CK(cudaMemcpyAsync(F.h, F.cur, F.c->N * sizeof(double), cudaMemcpyDeviceToDevice, F.c->stream));
+  F.info->status = F.status;
+  F.info->attempts = F.a;
+  F.info->t = F.t;
+  F.info->dt = F.dt;
+  F.done = true;
+  return TF_OK;
+}
+
+// Queue the explicit part and the first iteration of the next attempt (or
+// finish the film).
+int film_start_attempt(FilmRun& F) {
+  tf_ctx& c = *F.c;
+  if (F.a >= F.max_att) return film_finish(F);
+  if (F.t >= F.t_end) {
+    F.status = TF_ADV_DONE;
+    return film_finish(F);
+  }
+  F.fixed = c.p.newton_fixed_iter;
+  F.last = 0;
+  if (F.t_end - F.t <= F.dt) {
+    F.step_dt = F.t_end - F.t;
+    F.last = 1;
+  } else {
+    F.step_dt = F.dt;
+  }
+  int r = explicit_launch(c, F.cur, F.step_dt);
+  if (r) return r;
+  F.kmax = F.fixed > 0 ? F.fixed : c.p.newton_max_iter;
+  F.k = 0;
+  F.uk = F.cur;
+  F.bufs[0] = F.nxt;
+  F.bufs[1] = c.ubuf;
+  memset(&F.s, 0, sizeof(F.s));
+  F.sstatus = TF_STEP_NOT_CONVERGED;
+  F.it = 0;
+  r = iterate_launch(c, F.uk, F.step_dt, F.bufs[0], nullptr, nullptr);
+  if (r) return r;
+  TF_CK(cudaEventRecord(c.ev[7], c.stream));
+  F.phase = 1;
+  return TF_OK;
+}
+
+// An iteration has landed: classify it as step() does, then queue the next
+// iteration or the film statistics of the step's result.
+int film_on_iteration(FilmRun& F) {
+  tf_ctx& c = *F.c;
+  iterate_collect(c, false, &F.s);
+  if (F.k == 0) explicit_collect(c);
+  F.it = F.k + 1;
+  F.uk = F.bufs[F.k & 1];
+  F.sstatus = classify(c, F.s, F.it, F.fixed);
+  ++F.k;
+  if (F.sstatus == TF_STEP_NOT_CONVERGED && F.k < F.kmax) {
+    int r = iterate_launch(c, F.uk, F.step_dt, F.bufs[F.k & 1], nullptr, nullptr);
+    if (r) return r;
+  } else {
+    if (F.uk != F.nxt)
+      TF_CK(cudaMemcpyAsync(F.nxt, F.uk, c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    int r = stats_launch(c, F.nxt);
+    if (r) return r;
+    F.phase = 2;
+  }
+  TF_CK(cudaEventRecord(c.ev[7], c.stream));
+  return TF_OK;
+}
+
+// The step's film statistics have landed: the controller of tf_advance.
+int film_on_stats(FilmRun& F) {
+  tf_ctx& c = *F.c;
+  const tf_params& P = c.p;
+  stats_collect(c, &F.s);
+  const int s = F.sstatus;
+  ++F.a;
+  F.info->newton_iterations += F.it;
+  if (s == TF_STEP_CONVERGED) {
+    double* tmp = F.cur;
+    F.cur = F.nxt;
+    F.nxt = tmp;
+    F.t = F.last ? F.t_end : F.t + F.step_dt;
+    F.info->accepted++;
+    if (++F.streak >= P.grow_after) {
+      F.dt = fmin(F.dt * P.dt_grow, P.dt_max);
+      F.streak = 0;
+    }
+    if (P.rupture_h > 0.0 && F.s.hmin < P.rupture_h) {
+      F.status = TF_ADV_RUPTURE;
+      return film_finish(F);
+    }
+  } else {
+    F.streak = 0;
+    F.dt = F.step_dt * P.dt_shrink;
+    if (F.dt < P.dt_min) {
+      F.status = TF_ADV_DT_MIN;
+      return film_finish(F);
+    }
+  }
+  return film_start_attempt(F);
 }
 
 template <class T> int dalloc(T** p, size_t bytes) {
@@ -215,7 +370,7 @@ void tf_destroy(tf_ctx* c) {
   cudaFree(c->py);
   cudaFree(c->dsc);
   if (c->hsc) cudaFreeHost(c->hsc);
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 8; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   free(c);
 }
@@ -318,8 +473,8 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
     e = cudaMallocHost((void**)&c->hsc, sizeof(Scalars));
     if (e != cudaSuccess) r = cuda_fail(e);
   }
-  for (int k = 0; k < 5 && !r; ++k) {
-    e = cudaEventCreate(&c->ev[k]);
+  for (int k = 0; k < 8 && !r; ++k) {
+    e = k < 7 ? cudaEventCreate(&c->ev[k]) : cudaEventCreateWithFlags(&c->ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) r = cuda_fail(e);
   }
   if (r) {
@@ -447,6 +602,54 @@ int tf_advance(tf_ctx* c, double* h, double t0, double t_end, double dt0, int ma
   info->attempts = a;
   info->t = t;
   info->dt = dt;
+  return TF_OK;
+}
+
+int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const double* t0,
+                        const double* t_end, const double* dt0, const int* max_attempts,
+                        tf_advance_info* info) {
+  if (n < 0 || (n > 0 && (!ctx || !h || !t0 || !t_end || !dt0 || !max_attempts || !info)))
+    return TF_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctx[i] || !h[i] || max_attempts[i] < 0 || !(dt0[i] > 0.0) || !isfinite(t0[i])) return TF_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctx[j] == ctx[i]) return TF_ERR_ARG;  // one context per film
+  }
+  std::vector<FilmRun> F((size_t)n);
+  int active = 0;
+  for (int i = 0; i < n; ++i) {
+    FilmRun& f = F[(size_t)i];
+    memset(&f, 0, sizeof(f));
+    f.c = ctx[i];
+    f.h = h[i];
+    f.t = t0[i];
+    f.t_end = t_end[i];
+    f.dt = dt0[i];
+    f.max_att = max_attempts[i];
+    f.info = &info[i];
+    memset(f.info, 0, sizeof(*f.info));
+    f.cur = h[i];
+    f.nxt = ctx[i]->ubuf2;
+    f.status = TF_ADV_MAX_ATTEMPTS;
+    int r = film_start_attempt(f);
+    if (r) return r;
+    if (!f.done) ++active;
+  }
+  while (active > 0) {
+    bool progressed = false;
+    for (FilmRun& f : F) {
+      if (f.done) continue;
+      const cudaError_t q = cudaEventQuery(f.c->ev[7]);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return cuda_fail(q);
+      progressed = true;
+      const int r = f.phase == 1 ? film_on_iteration(f) : film_on_stats(f);
+      if (r) return r;
+      if (f.done) --active;
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+  for (FilmRun& f : F) TF_CK(cudaStreamSynchronize(f.c->stream));
   return TF_OK;
 }
 

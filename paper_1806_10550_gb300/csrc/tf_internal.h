@@ -61,5 +61,5 @@ struct tf_ctx {
   tf::Scalars* dsc;
   tf::Scalars* hsc;  // pinned
   tf_timing timing;
-  cudaEvent_t ev[5];
+  cudaEvent_t ev[8];  // 0-4 iteration timing, 5-6 explicit-part timing, 7 work done (ensembles)
 };

@@ -22,6 +22,12 @@ model's own lambda_m and sigma_max, the flat heights of Sec. Validation:
   nlc8k     NLC (eq. NLC_paras: C = 0.0857, b = 0.01), h0 = 0.5
   pol8k     polymer (eq. Polymer_scales: C = 0.00581), h0 = 3.9
 with dt0 * sigma_max and dt_max * sigma_max equal to scale8k's.
+
+ensemble  256 independent films (SURVEY config 4): 64 each of N = 128, 256,
+          512, 1024, contact angle uniform in [10, 40] deg (numpy
+          default_rng(1240)), power law, h0 = 1, eps = 0.01, each on
+          16 lambda_m of its own (so N/16 cells per wavelength), dt0 =
+          1e-7/sigma_max, dt_max = 0.01/sigma_max, 30 attempts per film.
 """
 import json
 import math
@@ -63,6 +69,17 @@ def main():
         W[name] = dict(common, model=model, cap_C=C, b=bb, h0=h0, lambda_m=lv, sigma_max=sv,
                        N=8192, P=64, eps=0.01, seed=1239, dt0=1e-3 * sm / sv, T=1e30,
                        dt_max=0.01 / sv, steps=40, ds=64 * lv / 8192, rupture_h=0.0)
+    import numpy as np
+    rng = np.random.default_rng(1240)
+    films = []
+    for i, N in enumerate([128, 256, 512, 1024] * 64):
+        thc = float(rng.uniform(10.0, 40.0))
+        kv = O.kappa_from_contact_angle(math.radians(thc), b, n, m)
+        qv, sv = O.lsa(O.Model(nx=1, ny=1, ds=1.0, kappa=kv, b=b, n=n, m=m), 1.0)
+        lv = 2.0 * math.pi / qv
+        films.append(dict(N=N, theta_c_deg=thc, kappa=kv, lambda_m=lv, sigma_max=sv,
+                          ds=16.0 * lv / N, seed=2000 + i, dt0=1e-7 / sv, dt_max=0.01 / sv))
+    W["ensemble"] = dict(common, P=16, eps=0.01, attempts=30, films=films)
     out = os.path.join(os.path.dirname(__file__), "workloads.json")
     with open(out, "w") as f:
         json.dump(W, f, indent=1, sort_keys=True)

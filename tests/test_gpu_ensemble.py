@@ -1,0 +1,109 @@
+"""Ensembles of independent films (tf_ensemble_advance): every film must
+come out exactly as tf_advance leaves it -- the same attempts, decisions,
+iteration counts and bit-identical grids -- and, through that, match the
+oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1806_10550_gb300 as tf
+from paper_1806_10550_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    if not T.cuda.is_available():
+        pytest.skip("no CUDA device")
+    tf.library()
+    return T
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+# (nx, ny, contact angle [deg], seed, dt0 factor, t_end factor, attempts);
+# times in units of 1/sigma_max of the film's own flat state
+FILMS = [
+    (32, 24, 12.0, 1, 1e-3, 1e30, 25),
+    (48, 48, 20.0, 2, 1e-3, 1e30, 30),
+    (64, 40, 35.0, 3, 5.0, 1e30, 20),      # starts too large: rejections
+    (17, 33, 27.0, 4, 1e-3, 2e-3, 40),     # reaches t_end (clipped last step)
+    (96, 80, 16.0, 5, 1e-2, 1e30, 15),
+    (1, 40, 22.0, 6, 1e-3, 1e30, 20),
+    (40, 1, 22.0, 7, 1e-3, 1e30, 0),       # no attempts at all
+]
+
+
+def film_params(nx, ny, th, mode):
+    kappa = O.kappa_from_contact_angle(math.radians(th), 0.1, 3, 2)
+    qm, sm = O.lsa(O.Model(nx=1, ny=1, ds=1.0, kappa=kappa), 1.0)
+    ds = 2 * math.pi / qm / 8
+    p = tf.tf_params_default(nx=nx, ny=ny, ds=ds, contact_angle=math.radians(th), precision=mode)
+    return p, sm, kappa, ds
+
+
+@pytest.mark.parametrize("mode", [tf.TF_FP64, tf.TF_FP32_BULK])
+def test_ensemble_matches_per_film_advance(torch, mode):
+    ctxs, grids, h0s, t_end, dt0, att, params = [], [], [], [], [], [], []
+    for nx, ny, th, seed, fdt, fend, na in FILMS:
+        p, sm, _, _ = film_params(nx, ny, th, mode)
+        h = S.spinodal_film(nx, ny, 1.0, 0.01, seed=seed)
+        ctxs.append(tf.Context(p, stream=torch.cuda.Stream()))
+        grids.append(dev(torch, h))
+        h0s.append(h)
+        t_end.append(fend / sm)
+        dt0.append(fdt / sm)
+        att.append(na)
+        params.append(p)
+    infos = tf.tf_ensemble_advance(ctxs, grids, 0.0, t_end, dt0, att)
+    torch.cuda.synchronize()
+    for i, (info, g) in enumerate(zip(infos, grids)):
+        ctx = tf.Context(params[i])
+        ref = dev(torch, h0s[i])
+        rinfo, _ = tf.tf_advance(ctx, ref, 0.0, t_end[i], dt0[i], att[i], records=False)
+        assert info == rinfo, (i, info, rinfo)
+        assert np.array_equal(host(g), host(ref)), i
+    # the films exercise the paths they were chosen for
+    assert infos[2]["attempts"] > infos[2]["accepted"]          # rejections
+    assert infos[3]["status"] == tf.TF_ADV_DONE                  # reached t_end
+    assert infos[3]["t"] == t_end[3]
+    assert infos[6]["attempts"] == 0
+
+
+def test_ensemble_film_matches_oracle(torch):
+    nx, ny, th, seed, fdt, fend, na = FILMS[2]
+    p, sm, kappa, ds = film_params(nx, ny, th, tf.TF_FP64)
+    h = S.spinodal_film(nx, ny, 1.0, 0.01, seed=seed)
+    others = [FILMS[0], FILMS[4]]
+    ctxs = [tf.Context(p, stream=torch.cuda.Stream())]
+    grids = [dev(torch, h)]
+    for onx, ony, oth, osd, _, _, _ in others:
+        op, _, _, _ = film_params(onx, ony, oth, tf.TF_FP64)
+        ctxs.append(tf.Context(op, stream=torch.cuda.Stream()))
+        grids.append(dev(torch, S.spinodal_film(onx, ony, 1.0, 0.01, seed=osd)))
+    infos = tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, [fdt / sm, 1e-3 / sm, 1e-2 / sm], na)
+    om = O.Model(nx=nx, ny=ny, ds=ds, kappa=kappa)
+    ref = O.advance(om, O.Control(), h, 0.0, 1e30, fdt / sm, na)
+    assert infos[0]["attempts"] == len(ref.records)
+    assert infos[0]["accepted"] == sum(r["accepted"] for r in ref.records)
+    assert infos[0]["newton_iterations"] == sum(r["iterations"] for r in ref.records)
+    assert np.max(np.abs(host(grids[0]) - ref.h)) <= 1e-10
+
+
+def test_ensemble_rejects_shared_context(torch):
+    p, sm, _, _ = film_params(16, 16, 20.0, tf.TF_FP64)
+    ctx = tf.Context(p)
+    g1 = dev(torch, S.spinodal_film(16, 16, 1.0, 0.01, seed=1))
+    g2 = dev(torch, S.spinodal_film(16, 16, 1.0, 0.01, seed=2))
+    with pytest.raises(RuntimeError):
+        tf.tf_ensemble_advance([ctx, ctx], [g1, g2], 0.0, 1e30, 1e-3 / sm, 3)
