@@ -415,17 +415,23 @@ def run_ensemble(args, w):
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as O
         O.build()
-        f = next(x for x in w["films"] if x["N"] == 256)
-        M = O.Model(nx=256, ny=256, ds=f["ds"], kappa=f["kappa"], b=w["b"], n=w["n"], m=w["m"])
-        ctl = O.Control(tol=w["tol"], max_iter=w["max_iter"], dt_max=f["dt_max"])
-        h = S.spinodal_film(256, 256, w["h0"], w["eps"], f["seed"])
-        t = time.perf_counter()
-        r = O.advance(M, ctl, h, 0.0, 1e30, f["dt0"], 10)
-        el = time.perf_counter() - t
-        acc = sum(x["accepted"] for x in r.records)
-        line["cpu_baseline"] = dict(value=256 * 256 * acc / el, unit="cell-updates/s",
+        # films of the ensemble in order, all their attempts, until 10 s of CPU work
+        done_cells, el, nf = 0, 0.0, 0
+        for f in w["films"]:
+            M = O.Model(nx=f["N"], ny=f["N"], ds=f["ds"], kappa=f["kappa"], b=w["b"], n=w["n"],
+                        m=w["m"])
+            ctl = O.Control(tol=w["tol"], max_iter=w["max_iter"], dt_max=f["dt_max"])
+            h = S.spinodal_film(f["N"], f["N"], w["h0"], w["eps"], f["seed"])
+            t = time.perf_counter()
+            r = O.advance(M, ctl, h, 0.0, 1e30, f["dt0"], A)
+            el += time.perf_counter() - t
+            done_cells += f["N"] ** 2 * sum(x["accepted"] for x in r.records)
+            nf += 1
+            if el >= 10.0:
+                break
+        line["cpu_baseline"] = dict(value=done_cells / el, unit="cell-updates/s",
                                     cores=O.num_threads(), kind="oracle",
-                                    sample=f"10 attempts of one 256^2 film of the ensemble, {el:.1f} s")
+                                    sample=f"the first {nf} films of the ensemble, {A} attempts each, {el:.1f} s")
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
