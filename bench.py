@@ -452,6 +452,9 @@ def main():
     args = ap.parse_args()
     w = load_workload(args.workload)
     if args.workload == "ensemble" and args.impl == "ours":
+        # one hardware work queue per stream (up to 32) before CUDA starts,
+        # so that the films' streams do not share queues
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
         run_ensemble(args, w)
         return
     if args.impl == "reference":

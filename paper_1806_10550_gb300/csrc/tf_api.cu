@@ -635,20 +635,47 @@ int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const doubl
     if (r) return r;
     if (!f.done) ++active;
   }
-  while (active > 0) {
-    bool progressed = false;
-    for (FilmRun& f : F) {
-      if (f.done) continue;
-      const cudaError_t q = cudaEventQuery(f.c->ev[7]);
-      if (q == cudaErrorNotReady) continue;
-      if (q != cudaSuccess) return cuda_fail(q);
-      progressed = true;
-      const int r = f.phase == 1 ? film_on_iteration(f) : film_on_stats(f);
-      if (r) return r;
-      if (f.done) --active;
+  // Several host threads share the films (film i goes to thread i % T), so
+  // that launching the kernels of small films does not become the limit.
+  int dev = 0;
+  TF_CK(cudaGetDevice(&dev));
+  const int T = active < 1 ? 1 : (active < 4 ? active : 4);
+  std::vector<int> err((size_t)T, TF_OK);
+  auto worker = [&](int w) {
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      err[(size_t)w] = TF_ERR_CUDA;
+      return;
     }
-    if (!progressed) std::this_thread::yield();
-  }
+    int left = 0;
+    for (int i = w; i < n; i += T) left += F[(size_t)i].done ? 0 : 1;
+    while (left > 0) {
+      bool progressed = false;
+      for (int i = w; i < n; i += T) {
+        FilmRun& f = F[(size_t)i];
+        if (f.done) continue;
+        const cudaError_t q = cudaEventQuery(f.c->ev[7]);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) {
+          err[(size_t)w] = cuda_fail(q);
+          return;
+        }
+        progressed = true;
+        const int r = f.phase == 1 ? film_on_iteration(f) : film_on_stats(f);
+        if (r) {
+          err[(size_t)w] = r;
+          return;
+        }
+        if (f.done) --left;
+      }
+      if (!progressed) std::this_thread::yield();
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < T; ++w) pool.emplace_back(worker, w);
+  worker(0);
+  for (std::thread& t : pool) t.join();
+  for (int e : err)
+    if (e) return e;
   for (FilmRun& f : F) TF_CK(cudaStreamSynchronize(f.c->stream));
   return TF_OK;
 }
