@@ -297,6 +297,21 @@ def cpu_baseline_sample(w, h0):
                        f"of the {N}x{N} film on the host cores, {el:.1f} s")
 
 
+METRIC = "grid cell-updates/s per Newton-ADI step at 8192^2"
+
+
+def headline_config(w, world, head="f32b", replayed=True):
+    """The bench line's config (shared by both arms)."""
+    N = w["N"]
+    return dict(workload=(f"{N}x{N} spinodal film, {MODEL_NAMES[w.get('model', 0)]} model, "
+                          f"{w['P']} lambda_m square, seed {w['seed']}"),
+                mode=("FP32-bulk" if head == "f32b" else "FP64"),
+                dt_sequence=("replayed from the FP64 run" if head == "f32b" and replayed
+                             else "adaptive"),
+                global_batch=world, l2="working set larger than L2 (several 8192^2 grids)",
+                parallelism=f"replicas x{world}")
+
+
 def reference_arm(args, w):
     """The FP64 CPU oracle as the reference arm: each step is one oracle
     time step of a 512^2 sample of the workload (same spacing, same noise)."""
@@ -318,15 +333,17 @@ def reference_arm(args, w):
     el = time.perf_counter() - t0
     acc = len(res2.accepted())
     value = n * n * acc / el
-    line = dict(metric="grid cell-updates/s per Newton-ADI step", value=value,
+    line = dict(metric=METRIC, value=value,
                 unit="cell-updates/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=el * 1e3 / max(1, args.steps), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 impl="reference",
-                config=dict(workload=f"{n}x{n} sample of the 8192^2 spinodal film, 64 lambda_m "
-                                     f"spacing (ds={w['ds']:.6f})", global_batch=1),
+                config=headline_config(w, args.gpus, replayed="fp64" in args.modes),
                 cpu_baseline=dict(value=value, unit="cell-updates/s", cores=O.num_threads(),
-                                  kind="oracle", sample=f"{acc} accepted steps of a {n}^2 sample"),
+                                  kind="oracle",
+                                  sample=(f"{acc} accepted FP64 oracle steps of a {n}^2 sample of the "
+                                          f"workload (same spacing ds={w['ds']:.6f} and noise), "
+                                          f"adaptive dt after {args.warmup} warm-up attempts")),
                 e2e=dict(value=value, unit="cell-updates/s", h2d_bytes_per_step=0,
                          d2h_bytes_per_step=0))
     print(json.dumps(line))
@@ -493,19 +510,13 @@ def main():
     value = N * N * acc_all / (R["ms"] * 1e-3)
     lp = 4 if head == "f32b" else 8
     line = dict(
-        metric="grid cell-updates/s per Newton-ADI step at 8192^2",
+        metric=METRIC,
         value=value, unit="cell-updates/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=R["ms"] / max(1, R["info"]["attempts"]), higher_is_better=True,
         scaling="weak", vs_baseline=None,
         dtype=("f32 solves + f32x2 double-float residual, f64 state" if head == "f32b" else "f64"),
         data="synthetic",
-        config=dict(workload=(f"{N}x{N} spinodal film, {MODEL_NAMES[w.get('model', 0)]} model, "
-                              f"{w['P']} lambda_m square, seed {w['seed']}"),
-                    mode=("FP32-bulk" if head == "f32b" else "FP64"),
-                    dt_sequence=("replayed from the FP64 run" if head == "f32b" and "fp64" in res
-                                 else "adaptive"),
-                    global_batch=world, l2="working set larger than L2 (several 8192^2 grids)",
-                    parallelism=f"replicas x{world}"),
+        config=headline_config(w, world, head, replayed="fp64" in res),
         accepted_steps=acc_local, attempts=R["info"]["attempts"],
         newton_iterations=R["info"]["newton_iterations"],
         cell_iterations_per_s=N * N * R["info"]["newton_iterations"] * world / (R["ms"] * 1e-3),
