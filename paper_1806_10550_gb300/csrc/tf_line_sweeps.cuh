@@ -334,7 +334,6 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   const bool solver = warp < 2;
   const int p = threadIdx.x - 64;  // producer index (valid when !solver)
   const int nx = M.nx, ny = M.ny;
-  const size_t N = (size_t)nx * ny;
   const int i0 = blockIdx.x * 32;
   const int m = split_point<kRY>(ny);
   const bool twisted = m < ny;
@@ -414,7 +413,6 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
       if (q < nchh(h) && i0 + lane < nx) {
         const int r0 = r0_of(h, q), r1 = r1_of(h, q);
         const LP* B = &S.s.f.band[q & 1][h][0][0][0];
-        const int col = i0 + lane;
         lu_chunk<LP, kRY>(lu, B, lane, r1 - r0, fac + fac_slab<kRY>(blockIdx.x, h, q, nch) + lane, pivot_bad);
       }
     }
