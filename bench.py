@@ -455,6 +455,148 @@ def run_ensemble(args, w):
         dist.destroy_process_group()
 
 
+SPECTRUM_METRIC = "film cells analysed/s, radial Fourier analysis at 8192^2"
+
+
+def spectrum_film(w):
+    from paper_1806_10550_gb300 import synthetic as S
+    N = w["N"]
+    qm = 2 * math.pi / w["lambda_m"]
+    return S.ring_film(N, N, w["ds"], w["h0"], w["eps"], qm, w["spread"], w["modes"], w["noise"],
+                       seed=w["seed"])
+
+
+def spectrum_config(w, world):
+    N = w["N"]
+    return dict(workload=(f"{N}x{N} ring film about q_m ({w['modes']} modes, noise {w['noise']}), "
+                          f"spacing lambda_m/{round(w['lambda_m'] / w['ds'])}, q_cut = 5 q_m, "
+                          f"sigma {w['sigma']}, {w['points_per_interval']} points per interval, "
+                          f"{w['n_eval']} samples"),
+                global_batch=world, l2="input larger than L2 (512 MiB film)",
+                parallelism=f"replicas x{world}")
+
+
+def oracle_spectrum(w, h):
+    """One oracle analysis of the whole film; returns (seconds, result)."""
+    import oracle.radial_fourier as RF
+    t = time.perf_counter()
+    r = RF.analyse(h, w["ds"], w["h0"], w["q_cut"], w["sigma"], w["points_per_interval"], w["n_eval"])
+    return time.perf_counter() - t, r
+
+
+def run_spectrum(args, w):
+    """The radial Fourier analysis of an 8192^2 film per step (all ten
+    kernels), the film resident in HBM; e2e adds the copy of the film from
+    pinned host memory and the read-back of the dominant maximum."""
+    import torch
+    import paper_1806_10550_gb300 as tf
+    rank, world, local, dist = dist_setup()
+    tf.library(build_if_missing=True)
+    N = w["N"]
+    h_host = torch.from_numpy(spectrum_film(w)).pin_memory()
+    h = h_host.cuda()
+    sp = tf.tf_spectrum_params_default(H0=w["h0"], q_cut=w["q_cut"], sigma=w["sigma"],
+                                       points_per_interval=w["points_per_interval"],
+                                       n_eval=w["n_eval"])
+    stream = torch.cuda.current_stream()
+    plan = tf.SpectrumPlan(N, N, w["ds"], sp, stream)
+    for _ in range(args.warmup):
+        tf.tf_spectrum_run(plan, h, outputs=False)
+    K = args.steps if args.steps != 200 else w["steps"]
+    names = ["rows", "cols", "smooth_p", "smooth_q", "radial", "fit"]
+    kms = [0.0] * 6
+    barrier(dist)
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with clocks:
+        e0.record(stream)
+        for _ in range(K):
+            info = tf.tf_spectrum_run(plan, h, outputs=False)
+            kms = [a + b for a, b in zip(kms, tf.tf_spectrum_timing(plan))]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = e0.elapsed_time(e1)
+    value = job_rate(dist, N * N * K, ms)
+    # end to end: film from pinned host memory, result read back (inside the call)
+    hd = torch.empty_like(h)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    e2.record(stream)
+    for _ in range(K):
+        hd.copy_(h_host, non_blocking=True)
+        info_e = tf.tf_spectrum_run(plan, hd, outputs=False)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    assert info_e["q_dominant"] == info["q_dominant"]
+    pi = plan.info()
+    Pb = min(N, pi["n_p"] + math.ceil(3 * w["sigma"]))
+    per = {n: kms[i] / K for i, n in enumerate(names)}
+    dom = max(per, key=per.get)
+    # algorithmic bytes of the row transform: the film read once (8 B/cell)
+    # and the narrow FP32 block of wave indices written (4 B x N x Pb)
+    rows_bytes = N * N * 8 + N * Pb * 4
+    pk = peaks()
+    ach = rows_bytes / (per["rows"] * 1e-3) / 1e9
+    qm = 2 * math.pi / w["lambda_m"]
+    line = dict(
+        metric=SPECTRUM_METRIC, value=value, unit="cells/s", n_gpus=world, steps=K,
+        warmup=args.warmup, ms_per_step=ms / K, higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="f32 transform, f64 smoothing, grouping and fit",
+        data="synthetic", config=spectrum_config(w, world),
+        q_dominant=info["q_dominant"], q_m=qm, n_radii=pi["n_radii"], n_intervals=pi["n_intervals"],
+        n_peaks=info["n_peaks"], kernel_ms_per_step={k: round(v, 4) for k, v in per.items()},
+        roofline=dict(bound="hbm", kernel="rows", achieved=round(ach, 1), peak=pk["hbm_gbs"],
+                      unit="GB/s", frac=round(ach / pk["hbm_gbs"], 4), traffic=None,
+                      ms_per_launch=round(per["rows"], 4), algorithmic_bytes_per_launch=rows_bytes,
+                      peak_source=pk["source"], dominant_kernel=dom),
+        gpu_launches=10 * K,
+        e2e=dict(value=job_rate(dist, N * N * K, ms_e2e), unit="cells/s",
+                 h2d_bytes_per_step=N * N * 8, d2h_bytes_per_step=4 + 16),
+    )
+    cs = clocks.summary()
+    line["clocks"] = dict(sm_mhz=cs["sm_mhz"], sm_max_mhz=cs["sm_max_mhz"], reasons=cs["reasons"])
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+        el, r = oracle_spectrum(w, h_host.numpy())
+        line["cpu_baseline"] = dict(value=N * N / el, unit="cells/s", cores=O.num_threads(),
+                                    kind="oracle",
+                                    sample=f"one oracle analysis of the whole {N}x{N} film, {el:.1f} s")
+        line["oracle_q_dominant"] = r["q_dominant"]
+    if rank == 0:
+        print(json.dumps(line))
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def reference_spectrum(args, w):
+    """The oracle's radial Fourier analysis as the reference arm: each step
+    one analysis of the whole 8192^2 film on the host cores."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle as O
+    h = spectrum_film(w)
+    for _ in range(min(args.warmup, 1)):
+        oracle_spectrum(w, h)
+    K = min(args.steps, 3)
+    el = 0.0
+    for _ in range(K):
+        dt, r = oracle_spectrum(w, h)
+        el += dt
+    N = w["N"]
+    value = N * N * K / el
+    line = dict(metric=SPECTRUM_METRIC, value=value, unit="cells/s", n_gpus=args.gpus, steps=K,
+                warmup=args.warmup, ms_per_step=el * 1e3 / K, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=spectrum_config(w, args.gpus),
+                cpu_baseline=dict(value=value, unit="cells/s", cores=O.num_threads(), kind="oracle",
+                                  sample=f"{K} oracle analyses of the whole {N}x{N} film"),
+                e2e=dict(value=value, unit="cells/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,6 +610,9 @@ def main():
     ap.add_argument("--modes", default="fp64,f32b")
     args = ap.parse_args()
     w = load_workload(args.workload)
+    if args.workload == "spectrum8k":
+        (reference_spectrum if args.impl == "reference" else run_spectrum)(args, w)
+        return
     if args.workload == "ensemble" and args.impl == "ours":
         # one hardware work queue per stream (up to 32) before CUDA starts,
         # so that the films' streams do not share queues

@@ -262,6 +262,100 @@ int tf_timing_get(const tf_ctx* ctx, tf_timing* out);
 int tf_residual_noalloc(const tf_params* p, void* stream, const double* h_k,
                         const double* h_old, double dt, double* G, tf_norms* out);
 
+/* ---- radial Fourier analysis of a film (App. Radial Fourier Transform) ---
+ * The dominant wavenumber of a film pattern, all steps on the GPU, in the
+ * appendix's order:
+ *  1. zeta = h - H0; A[q][p] = |C[q][p]| / (nx ny), where C is the 2-D
+ *     DCT-II sum  sum_j sum_i zeta[j][i] cos(pi p (2i+1)/2nx)
+ *     cos(pi q (2j+1)/2ny): the FFT magnitude of the film reflected evenly
+ *     about its no-flux walls, normalised by the reflected film's size, at
+ *     wave vector (pi p / Lx, pi q / Ly), L = n ds.  (A cosine mode
+ *     eps cos(pi p x/Lx) cos(pi q y/Ly), p, q > 0, gives eps/4.)  FP32
+ *     transform; every later step in FP64.
+ *  2. Gaussian smoothing of A over (p, q): weights exp(-d^2 / 2 sigma^2),
+ *     |d| <= ceil(3 sigma), normalised; outside 0..n-1 the reflected film's
+ *     spectrum continues with period 2n (index -k is k, n is 0, n+k is n-k).
+ *  3-4. One radial point per distinct |q| <= q_cut (eq.
+ *     FFT_radial_averaging): the mean of the smoothed values with that |q|.
+ *     Equality is exact on the integer key (p ny/g)^2 + (q nx/g)^2,
+ *     g = gcd(nx, ny); the cut is key <= floor((q_cut/scale)^2) with
+ *     scale = pi g / (ds nx ny), |q| = scale sqrt(key).
+ *  5. Continuous piecewise-linear least squares (eq. PiecewiseFunction):
+ *     nodes t_0 = 0, t_j = |q| of radial point j*ppi (j = 1..K-1),
+ *     t_K = q_cut, K = max(1, ceil((M-1)/ppi)) for M radial points (every
+ *     interval but the last holds ppi points, the last 2..ppi+1); node
+ *     values a_0 = 0 and a_1..a_K fitted.
+ *  6. The fit at n_eval equispaced points of [0, q_cut], smoothed by moving
+ *     averages of half-widths 3, 2, 1 (windows cut at the ends).
+ *  7. Local maxima: derivative by second-order differences (one-sided at
+ *     the ends); a root in [q_e, q_e+1) where it is zero at q_e or changes
+ *     sign, placed by linear interpolation; a maximum where the second
+ *     derivative (the same differences of the derivative), interpolated to
+ *     the root, is negative.  Listed highest value first.
+ * Plans: nx, ny powers of two in 1..16384; ds > 0.  A plan allocates its
+ * device workspace and builds the radial grouping (geometry only) once;
+ * runs allocate nothing.  Every run synchronises the plan's stream.      */
+typedef struct {
+  double H0;               /* thickness subtracted before the transform         */
+  double q_cut;            /* wavenumbers analysed, |q| <= q_cut (the paper:
+                              5 q_m); > 0, at most 2^27 distinct keys below it */
+  double sigma;            /* Gaussian std. deviation in wave-index steps, 0..16
+                              (0 = no smoothing)                                */
+  int points_per_interval; /* radial points per fit interval (the paper: 10), >= 1 */
+  int n_eval;              /* samples of the fitted curve (the paper: 400), 3..4096 */
+} tf_spectrum_params;
+
+/* H0 = 1, q_cut = 0 (must be set), sigma = 1, points_per_interval = 10,
+ * n_eval = 400.                                                          */
+void tf_spectrum_params_default(tf_spectrum_params* sp);
+
+typedef struct tf_spectrum_plan tf_spectrum_plan;
+
+typedef struct {
+  int n_p, n_q;          /* wave-index block of the radial points: p < n_p, q < n_q */
+  int n_radii;           /* M: distinct |q| <= q_cut                          */
+  int n_intervals;       /* K                                                 */
+  int n_eval;            /* samples of the curve                              */
+  int n_peaks;           /* local maxima found (0 before a run)               */
+  double q_dominant;     /* wavenumber of the highest maximum (0 if none)     */
+  double value_dominant; /* its value                                         */
+} tf_spectrum_info;
+
+/* Outputs of a run: HOST buffers, each NULL (not copied) or holding the
+ * count stated (sizes from tf_spectrum_plan_info).                       */
+typedef struct {
+  double* amplitude;    /* [n_q][n_p]: step 1 (unsmoothed)                   */
+  double* smoothed;     /* [n_q][n_p]: step 2                                */
+  double* radial_q;     /* [n_radii], ascending                              */
+  double* radial_value; /* [n_radii]                                          */
+  double* node_q;       /* [n_intervals + 1]                                 */
+  double* node_value;   /* [n_intervals + 1], node_value[0] = 0              */
+  double* curve_q;      /* [n_eval]                                          */
+  double* curve_value;  /* [n_eval], after the moving averages               */
+  double* peak_q;       /* [peak_cap]: maxima, highest value first           */
+  double* peak_value;   /* [peak_cap]                                         */
+  int peak_cap;
+} tf_spectrum_out;
+
+/* stream: cudaStream_t (as void*) for every kernel of the plan.  Returns
+ * TF_OK, TF_ERR_ARG (sizes, parameters, or fewer than two radial points),
+ * TF_ERR_NOMEM or TF_ERR_CUDA; *out is NULL on error.                    */
+int tf_spectrum_plan_create(int nx, int ny, double ds, const tf_spectrum_params* sp, void* stream,
+                            tf_spectrum_plan** out);
+void tf_spectrum_plan_destroy(tf_spectrum_plan* plan);
+int tf_spectrum_plan_info(const tf_spectrum_plan* plan, tf_spectrum_info* info);
+
+/* Analyse the device grid h [ny][nx] (FP64).  out: NULL or host buffers.
+ * info: required.  Returns TF_OK, TF_ERR_ARG or TF_ERR_CUDA.             */
+int tf_spectrum_run(tf_spectrum_plan* plan, const double* h, tf_spectrum_out* out,
+                    tf_spectrum_info* info);
+
+/* Durations (ms, CUDA events) of the last run's kernels, in order: row
+ * DCTs, column DCTs, smoothing along p, smoothing along q, radial means,
+ * and the fit with sampling and maxima (five kernels).  n: entries wanted
+ * (up to 6).                                                             */
+int tf_spectrum_timing(const tf_spectrum_plan* plan, double* ms, int n);
+
 #ifdef __cplusplus
 }
 #endif

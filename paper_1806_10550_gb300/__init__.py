@@ -8,7 +8,10 @@ CPU fallback: without the built library or a CUDA device every call raises.
 
 Functions carry the names of the C ABI: ``tf_params_default``, ``tf_init``,
 ``tf_destroy``, ``tf_residual``, ``tf_newton_iteration``,
-``tf_newton_adi_step``, ``tf_advance``, ``tf_ensemble_advance``, ``tf_strerror``.
+``tf_newton_adi_step``, ``tf_advance``, ``tf_ensemble_advance``, ``tf_strerror``,
+and for the radial Fourier analysis ``tf_spectrum_params_default``,
+``tf_spectrum_plan_create``, ``tf_spectrum_run``, ``tf_spectrum_plan_info``,
+``tf_spectrum_timing``, ``tf_spectrum_plan_destroy``.
 """
 from __future__ import annotations
 
@@ -85,6 +88,23 @@ class TfTiming(C.Structure):
 _lib = None
 
 
+class TfSpectrumParams(C.Structure):
+    _fields_ = [("H0", C.c_double), ("q_cut", C.c_double), ("sigma", C.c_double),
+                ("points_per_interval", C.c_int), ("n_eval", C.c_int)]
+
+
+class TfSpectrumInfo(C.Structure):
+    _fields_ = [("n_p", C.c_int), ("n_q", C.c_int), ("n_radii", C.c_int), ("n_intervals", C.c_int),
+                ("n_eval", C.c_int), ("n_peaks", C.c_int), ("q_dominant", C.c_double),
+                ("value_dominant", C.c_double)]
+
+
+class TfSpectrumOut(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in (
+        "amplitude", "smoothed", "radial_q", "radial_value", "node_q", "node_value",
+        "curve_q", "curve_value", "peak_q", "peak_value")] + [("peak_cap", C.c_int)]
+
+
 def library(build_if_missing: bool = True):
     """Load ``libtfadi.so`` (building it with nvcc when it is missing)."""
     global _lib
@@ -115,8 +135,18 @@ def library(build_if_missing: bool = True):
                                       C.POINTER(TfAdvanceInfo)]
     L.tf_timing_enable.argtypes = [vp, C.c_int]
     L.tf_timing_get.argtypes = [vp, C.POINTER(TfTiming)]
+    L.tf_spectrum_params_default.argtypes = [C.POINTER(TfSpectrumParams)]
+    L.tf_spectrum_params_default.restype = None
+    L.tf_spectrum_plan_create.argtypes = [C.c_int, C.c_int, dp, C.POINTER(TfSpectrumParams), vp,
+                                          C.POINTER(vp)]
+    L.tf_spectrum_plan_destroy.argtypes = [vp]
+    L.tf_spectrum_plan_destroy.restype = None
+    L.tf_spectrum_plan_info.argtypes = [vp, C.POINTER(TfSpectrumInfo)]
+    L.tf_spectrum_run.argtypes = [vp, vp, C.POINTER(TfSpectrumOut), C.POINTER(TfSpectrumInfo)]
+    L.tf_spectrum_timing.argtypes = [vp, C.POINTER(dp), C.c_int]
     for f in ("tf_init", "tf_residual", "tf_newton_iteration", "tf_newton_adi_step", "tf_advance",
-              "tf_ensemble_advance", "tf_timing_enable", "tf_timing_get"):
+              "tf_ensemble_advance", "tf_timing_enable", "tf_timing_get", "tf_spectrum_plan_create",
+              "tf_spectrum_plan_info", "tf_spectrum_run", "tf_spectrum_timing"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -292,6 +322,108 @@ def tf_timing_get(ctx: Context) -> dict:
     return {k: getattr(t, k) for k, _ in TfTiming._fields_}
 
 
+def tf_spectrum_params_default(**overrides) -> TfSpectrumParams:
+    sp = TfSpectrumParams()
+    library().tf_spectrum_params_default(C.byref(sp))
+    for k, v in overrides.items():
+        if not hasattr(sp, k):
+            raise AttributeError(k)
+        setattr(sp, k, v)
+    return sp
+
+
+def _info_dict(i: TfSpectrumInfo) -> dict:
+    return {k: getattr(i, k) for k, _ in TfSpectrumInfo._fields_}
+
+
+class SpectrumPlan:
+    """Owns one ``tf_spectrum_plan``: the radial Fourier analysis of
+    ``(ny, nx)`` float64 CUDA grids with spacing ``ds``."""
+
+    def __init__(self, nx: int, ny: int, ds: float, params: TfSpectrumParams, stream=None):
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.shape = (ny, nx)
+        self.params = params
+        h = C.c_void_p()
+        _check(library().tf_spectrum_plan_create(int(nx), int(ny), float(ds), C.byref(params),
+                                                 C.c_void_p(stream.cuda_stream), C.byref(h)),
+               "tf_spectrum_plan_create")
+        self.handle = h
+
+    def info(self) -> dict:
+        i = TfSpectrumInfo()
+        _check(library().tf_spectrum_plan_info(self.handle, C.byref(i)), "tf_spectrum_plan_info")
+        return _info_dict(i)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            library().tf_spectrum_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tf_spectrum_plan_create(nx: int, ny: int, ds: float, params: TfSpectrumParams,
+                            stream=None) -> SpectrumPlan:
+    return SpectrumPlan(nx, ny, ds, params, stream)
+
+
+def tf_spectrum_plan_destroy(plan: SpectrumPlan):
+    plan.close()
+
+
+def tf_spectrum_plan_info(plan: SpectrumPlan) -> dict:
+    return plan.info()
+
+
+def tf_spectrum_run(plan: SpectrumPlan, h, outputs: bool = True, peak_cap: int = 64) -> dict:
+    """Analyse ``h``; returns the info fields and, with ``outputs``, every
+    stage as NumPy arrays (amplitude and smoothed [n_q, n_p], radial_q/_value,
+    node_q/_value, curve_q/_value, peaks [(q, value)], highest first)."""
+    import numpy as np
+    torch = _torch()
+    if not isinstance(h, torch.Tensor) or h.dtype != torch.float64 or not h.is_cuda:
+        raise TypeError("h must be a torch.float64 CUDA tensor")
+    if tuple(h.shape) != plan.shape or not h.is_contiguous():
+        raise ValueError(f"h must be contiguous with shape {plan.shape}")
+    i = TfSpectrumInfo()
+    if not outputs:
+        _check(library().tf_spectrum_run(plan.handle, C.c_void_p(h.data_ptr()), None, C.byref(i)),
+               "tf_spectrum_run")
+        return _info_dict(i)
+    pi = plan.info()
+    arrs = dict(amplitude=np.empty((pi["n_q"], pi["n_p"])), smoothed=np.empty((pi["n_q"], pi["n_p"])),
+                radial_q=np.empty(pi["n_radii"]), radial_value=np.empty(pi["n_radii"]),
+                node_q=np.empty(pi["n_intervals"] + 1), node_value=np.empty(pi["n_intervals"] + 1),
+                curve_q=np.empty(pi["n_eval"]), curve_value=np.empty(pi["n_eval"]),
+                peak_q=np.empty(max(1, peak_cap)), peak_value=np.empty(max(1, peak_cap)))
+    o = TfSpectrumOut(**{k: a.ctypes.data for k, a in arrs.items()}, peak_cap=int(peak_cap))
+    _check(library().tf_spectrum_run(plan.handle, C.c_void_p(h.data_ptr()), C.byref(o), C.byref(i)),
+           "tf_spectrum_run")
+    r = _info_dict(i)
+    npk = min(i.n_peaks, peak_cap)
+    pq, pv = arrs.pop("peak_q"), arrs.pop("peak_value")
+    r.update(arrs)
+    r["peaks"] = list(zip(pq[:npk].tolist(), pv[:npk].tolist()))
+    return r
+
+
+def tf_spectrum_timing(plan: SpectrumPlan) -> list:
+    """Kernel durations (ms) of the last run: row DCTs, column DCTs,
+    smoothing along p and q, radial means, and the fit with sampling and
+    maxima (five kernels)."""
+    ms = (C.c_double * 6)()
+    _check(library().tf_spectrum_timing(plan.handle, ms, 6), "tf_spectrum_timing")
+    return list(ms)
+
+
 def params_for_workload(w: dict, precision: int = TF_FP64, **overrides) -> TfParams:
     """tf_params of a workload description (see tests/golden/workloads.json)."""
     p = tf_params_default(
@@ -309,4 +441,4 @@ def params_for_workload(w: dict, precision: int = TF_FP64, **overrides) -> TfPar
 
 
 __all__ = [n for n in dir() if n.startswith(("tf_", "TF_", "Tf"))] + [
-    "Context", "library", "params_for_workload"]
+    "Context", "SpectrumPlan", "library", "params_for_workload"]

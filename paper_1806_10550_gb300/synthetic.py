@@ -13,6 +13,12 @@ the two sides see bit-identical inputs.
   overlap.
 * Single cosine modes ``h0 (1 + eps cos(kx x) cos(ky y))`` with
   ``k = pi p / L`` (compatible with the no-flux walls), for validation.
+* Ring films: a stand-in for a film whose spinodal pattern has developed
+  (Sec. Results, the films the radial Fourier analysis is applied to):
+  ``n_modes`` wall-compatible cosine modes whose wavenumbers scatter about
+  ``k0`` (relative spread ``spread``, uniform direction), seeded amplitudes
+  in [0, 1] and signs, scaled to ``eps`` at the largest excursion, plus
+  ``noise`` U[-1, 1] per cell.
 
 Cell ``(i, j)`` has its centre at ``((i + 1/2) ds, (j + 1/2) ds)``; arrays
 are row-major ``[ny, nx]``.
@@ -57,3 +63,18 @@ def mode_film(nx: int, ny: int, ds: float, h0: float, eps: float,
 def film_ensemble_sizes(n_films: int, choices, seed: int):
     rng = np.random.default_rng(seed)
     return [int(c) for c in rng.choice(np.asarray(choices), size=n_films)]
+
+
+def ring_film(nx: int, ny: int, ds: float, h0: float, eps: float, k0: float, spread: float,
+              n_modes: int, noise: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    k = k0 * (1.0 + spread * rng.standard_normal(n_modes))
+    ang = rng.uniform(0.0, 0.5 * np.pi, n_modes)
+    p = np.clip(np.rint(k * np.cos(ang) * nx * ds / np.pi), 0, nx - 1)
+    q = np.clip(np.rint(k * np.sin(ang) * ny * ds / np.pi), 0, ny - 1)
+    amp = rng.uniform(0.0, 1.0, n_modes) * rng.choice([-1.0, 1.0], n_modes)
+    cx = np.cos(np.pi * p[:, None] * cell_centres(nx, ds)[None, :] / (nx * ds))
+    cy = np.cos(np.pi * q[:, None] * cell_centres(ny, ds)[None, :] / (ny * ds))
+    pattern = cy.T @ (amp[:, None] * cx)
+    pattern /= np.max(np.abs(pattern))
+    return h0 * (1.0 + eps * pattern + noise * rng.uniform(-1.0, 1.0, size=(ny, nx)))

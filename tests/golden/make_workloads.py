@@ -23,11 +23,18 @@ model's own lambda_m and sigma_max, the flat heights of Sec. Validation:
   pol8k     polymer (eq. Polymer_scales: C = 0.00581), h0 = 3.9
 with dt0 * sigma_max and dt_max * sigma_max equal to scale8k's.
 
-ensemble  256 independent films (SURVEY config 4): 64 each of N = 128, 256,
+ensemble  256 independent films (the many-film statistics runs of Sec.
+          Results): 64 each of N = 128, 256,
           512, 1024, contact angle uniform in [10, 40] deg (numpy
           default_rng(1240)), power law, h0 = 1, eps = 0.01, each on
           16 lambda_m of its own (so N/16 cells per wavelength), dt0 =
           1e-7/sigma_max, dt_max = 0.01/sigma_max, 30 attempts per film.
+
+spectrum8k  the radial Fourier analysis (App. Radial Fourier Transform) of
+          an 8192^2 film at scale8k's spacing (lambda_m / 128): a ring film
+          (256 cosine modes about q_m, spread 5 %, amplitude 0.05 h0, noise
+          0.002 h0, seed 1241), q_cut = 5 q_m, sigma = 1, 10 points per
+          interval, 400 samples.
 """
 import json
 import math
@@ -80,6 +87,9 @@ def main():
         films.append(dict(N=N, theta_c_deg=thc, kappa=kv, lambda_m=lv, sigma_max=sv,
                           ds=16.0 * lv / N, seed=2000 + i, dt0=1e-7 / sv, dt_max=0.01 / sv))
     W["ensemble"] = dict(common, P=16, eps=0.01, attempts=30, films=films)
+    W["spectrum8k"] = dict(common, N=8192, P=64, ds=64 * lam / 8192, seed=1241, eps=0.05,
+                           spread=0.05, modes=256, noise=0.002, q_cut=5.0 * qm, sigma=1.0,
+                           points_per_interval=10, n_eval=400, steps=50)
     out = os.path.join(os.path.dirname(__file__), "workloads.json")
     with open(out, "w") as f:
         json.dump(W, f, indent=1, sort_keys=True)

@@ -46,6 +46,11 @@ int main(void) {
   O(tf_params, grow_after); O(tf_params, rupture_h); O(tf_params, precision);
   O(tf_params, nlc_K); O(tf_params, nlc_w); O(tf_params, pol_C); O(tf_params, pol_d);
   O(tf_step_record, accepted); O(tf_step_record, hmin); O(tf_advance_info, dt);
+  printf("tf_spectrum_params %zu\ntf_spectrum_info %zu\ntf_spectrum_out %zu\n",
+         sizeof(tf_spectrum_params), sizeof(tf_spectrum_info), sizeof(tf_spectrum_out));
+  O(tf_spectrum_params, sigma); O(tf_spectrum_params, n_eval);
+  O(tf_spectrum_info, n_peaks); O(tf_spectrum_info, q_dominant); O(tf_spectrum_info, value_dominant);
+  O(tf_spectrum_out, curve_value); O(tf_spectrum_out, peak_value); O(tf_spectrum_out, peak_cap);
   return 0;
 }
 '''
@@ -65,11 +70,15 @@ def test_struct_layouts_match_header():
     assert lay["tf_step_record"] == C.sizeof(tf.TfStepRecord)
     assert lay["tf_advance_info"] == C.sizeof(tf.TfAdvanceInfo)
     assert lay["tf_norms"] == C.sizeof(tf.TfNorms)
+    assert lay["tf_spectrum_params"] == C.sizeof(tf.TfSpectrumParams)
+    assert lay["tf_spectrum_info"] == C.sizeof(tf.TfSpectrumInfo)
+    assert lay["tf_spectrum_out"] == C.sizeof(tf.TfSpectrumOut)
     for key, v in lay.items():
         if "." in key:
             T, f = key.split(".")
             cls = {"tf_params": tf.TfParams, "tf_step_record": tf.TfStepRecord,
-                   "tf_advance_info": tf.TfAdvanceInfo}[T]
+                   "tf_advance_info": tf.TfAdvanceInfo, "tf_spectrum_params": tf.TfSpectrumParams,
+                   "tf_spectrum_info": tf.TfSpectrumInfo, "tf_spectrum_out": tf.TfSpectrumOut}[T]
             assert getattr(cls, f).offset == v, key
 
 
@@ -110,3 +119,30 @@ def test_no_cpu_fallback_without_gpu():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError, match="CUDA device is required"):
         tf.Context(tf.tf_params_default(nx=8, ny=8, ds=1.0))
+
+
+def test_spectrum_params_default():
+    sp = tf.tf_spectrum_params_default()
+    assert sp.H0 == 1.0 and sp.q_cut == 0.0 and sp.sigma == 1.0
+    assert sp.points_per_interval == 10 and sp.n_eval == 400
+
+
+@pytest.mark.parametrize("nx,ny,ds,bad", [
+    (48, 64, 1.0, {}), (64, 0, 1.0, {}), (32768, 64, 1.0, {}), (64, 64, 0.0, {}),
+    (64, 64, 1.0, dict(q_cut=0.0)), (64, 64, 1.0, dict(q_cut=float("inf"))),
+    (64, 64, 1.0, dict(sigma=-1.0)), (64, 64, 1.0, dict(sigma=17.0)),
+    (64, 64, 1.0, dict(points_per_interval=0)), (64, 64, 1.0, dict(n_eval=2)),
+    (64, 64, 1.0, dict(n_eval=5000)), (64, 64, 1.0, dict(H0=float("nan"))),
+    (16384, 16384, 1.0, dict(q_cut=1e6)),  # more than 2^27 keys
+])
+def test_spectrum_plan_rejects_bad_arguments(nx, ny, ds, bad):
+    sp = tf.tf_spectrum_params_default(q_cut=1.0)
+    for k, v in bad.items():
+        setattr(sp, k, v)
+    h = C.c_void_p(123)
+    assert tf.library().tf_spectrum_plan_create(nx, ny, ds, C.byref(sp), None, C.byref(h)) == tf.TF_ERR_ARG
+    assert h.value is None
+    L = tf.library()
+    assert L.tf_spectrum_run(None, None, None, None) == tf.TF_ERR_ARG
+    assert L.tf_spectrum_plan_info(None, None) == tf.TF_ERR_ARG
+    L.tf_spectrum_plan_destroy(None)
