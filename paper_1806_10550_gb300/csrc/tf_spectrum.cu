@@ -57,34 +57,59 @@ __device__ __forceinline__ int makhoul_slot(int i, int n) {
   return (i & 1) ? n - 1 - (i >> 1) : (i >> 1);
 }
 
-// zeta = h - H0 in FP32 without FP64 arithmetic (the FP64 pipe is narrow):
-// h = hi + lo, hi the float with h's sign, exponent and top 23 fraction bits
-// (exact), lo the remaining 29 bits times 2^(e-1075) rounded to 24 bits
-// (error below 2^-48 |h|); with H0 = H0hi + H0lo (H0hi = fl32(H0), the host
-// rounds the rest), (hi - H0hi) + (lo - H0lo) is within
-// 2^-24 |zeta| + 2^-47 (|h| + |H0|) of zeta.  Heights outside
-// [2^-74, 2^128) take the FP64 route.
-__device__ __forceinline__ float zeta_f32(double h, double H0, float H0hi, float H0lo) {
+// zeta = h - H0 in FP32 without FP64 arithmetic or conversions (the FP64
+// pipe is narrow): h = hi + lo, hi the float with h's sign, exponent and top
+// 23 fraction bits (exact), lo the next 23 fraction bits (exact: the 2^23
+// trick, 2^23 + m - 2^23, scaled by a power of two), the last 6 bits
+// dropped (below 2^-46 |h|).  With H0 = H0hi + H0lo (H0hi = fl32(H0), the
+// host rounds the rest), (hi - H0hi) + (lo - H0lo) is within
+// 2^-24 |zeta| + 2^-45 (|h| + |H0|) of zeta.  Heights outside
+// [2^-68, 2^128) take the FP64 route.
+// The fast path alone; ok is false where h needs the FP64 route.
+__device__ __forceinline__ float zeta_fast(double h, float H0hi, float H0lo, bool& ok) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(h);
   const unsigned hi32 = (unsigned)(bits >> 32), lo32 = (unsigned)bits;
   const int e = (int)((hi32 >> 20) & 0x7ffu);
-  if (e < 949 || e > 1150) return (float)(h - H0);
+  ok = e >= 955 && e <= 1150;
   const unsigned sign = hi32 & 0x80000000u;
   const float fh = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
-  const float sc = __uint_as_float(sign | ((unsigned)(e - 948) << 23));
-  const float fl = __uint2float_rn(lo32 & 0x1fffffffu) * sc;
-  return (fh - H0hi) + (fl - H0lo);
+  // bits 28..6 of the fraction, worth m 2^(e-1069)
+  const float m = __uint_as_float(0x4b000000u | ((lo32 >> 6) & 0x7fffffu)) - 8388608.0f;
+  const float sc = __uint_as_float(sign | ((unsigned)(e - 942) << 23));
+  return (fh - H0hi) + (m * sc - H0lo);
+}
+
+__device__ __forceinline__ float zeta_f32(double h, double H0, float H0hi, float H0lo) {
+  bool ok;
+  const float z = zeta_fast(h, H0hi, H0lo, ok);
+  return ok ? z : (float)(h - H0);
 }
 
 // Shared-memory index with one pad slot per 16 values, so that the strided
 // accesses of the early passes fall into different banks.
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
-// exp(-2 pi i m / 16), m < 8 (host-computed, rounded once).
-__constant__ float2 c_w16[8];
-
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// v * exp(-2 pi i k / 16) for k < 8; k is a constant once the callers'
+// loops are unrolled, so the switch folds to the one case, with the
+// products by 1, -i and sqrt(1/2) (1 - i) written out.
+__device__ __forceinline__ float2 mul_w16(float2 v, int k) {
+  const float C1 = 0.92387953251128674f;  // cos(pi/8)
+  const float S1 = 0.38268343236508977f;  // sin(pi/8)
+  const float R2 = 0.70710678118654752f;  // sqrt(1/2)
+  switch (k) {
+    case 0: return v;
+    case 1: return make_float2(C1 * v.x + S1 * v.y, C1 * v.y - S1 * v.x);
+    case 2: return make_float2(R2 * (v.x + v.y), R2 * (v.y - v.x));
+    case 3: return make_float2(S1 * v.x + C1 * v.y, S1 * v.y - C1 * v.x);
+    case 4: return make_float2(v.y, -v.x);
+    case 5: return make_float2(C1 * v.y - S1 * v.x, -S1 * v.y - C1 * v.x);
+    case 6: return make_float2(R2 * (v.y - v.x), -R2 * (v.x + v.y));
+    default: return make_float2(S1 * v.y - C1 * v.x, -C1 * v.y - S1 * v.x);
+  }
 }
 
 // In-register forward DFT of length R (2, 4, 8 or 16): radix-2 decimation
@@ -106,8 +131,7 @@ __device__ __forceinline__ void dft_regs(float2 (&v)[R]) {
     for (int i = 0; i < R; ++i) {
       if ((i & m) == 0) {
         const int pos = i & (m - 1);
-        const float2 w = c_w16[pos * (8 / m)];  // exp(-2 pi i pos / 2m)
-        const float2 t = cmul(w, x[i + m]);
+        const float2 t = mul_w16(x[i + m], pos * (8 / m));  // times exp(-2 pi i pos / 2m)
         x[i + m] = make_float2(x[i].x - t.x, x[i].y - t.y);
         x[i] = make_float2(x[i].x + t.x, x[i].y + t.y);
       }
@@ -137,9 +161,10 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int n, int lg, int p,
     const int base = g << lg;
 #pragma unroll
     for (int r = 0; r < R; ++r) v[jj][r] = buf[pad16(base + j + r * cols)];
-    if (p > 1) {  // twiddles exp(-2 pi i r k / pR) = tw[r k n / pR]
+    if (p > 1) {  // twiddles exp(-2 pi i r k / pR) = tw[r k n / pR]: powers
+                  // 1, 2, 4, 8 from the table, the others as their products
       const int step = k * (n / (p * R));
-      float2 w1 = __ldg(&tw[step]);
+      const float2 w1 = __ldg(&tw[step]);
       v[jj][1] = cmul(v[jj][1], w1);
       if (R > 2) {
         const float2 w2 = __ldg(&tw[2 * step]);
@@ -182,9 +207,11 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int n, int lg, int p,
 
 // Forward FFT of every length-n line in buf (16 * THREADS values in all),
 // natural order in and out.  tw[k] = exp(-2 pi i k / n), k < n.
+// The passes start after the first l0 bits (sub-transforms of length 2^l0
+// already formed).
 template <int THREADS>
-__device__ __forceinline__ void fft_lines(float2* buf, int n, int lg, const float2* __restrict__ tw) {
-  int p = 1, l = 0;
+__device__ __forceinline__ void fft_lines(float2* buf, int n, int lg, const float2* __restrict__ tw, int l0 = 0) {
+  int p = 1 << l0, l = l0;
   for (; l + 4 <= lg; l += 4, p <<= 4) stockham_pass<16, THREADS>(buf, n, lg, p, tw);
   switch (lg - l) {
     case 1: stockham_pass<2, THREADS>(buf, n, lg, p, tw); break;
@@ -217,32 +244,55 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_dct_rows(const doub
   extern __shared__ float2 zbuf[];
   const int G = (16 * THREADS) >> lg;
   const int pair0 = blockIdx.x * G;
-  if (nx >= 2 && (reinterpret_cast<uintptr_t>(h) & 15) == 0) {
-    // 16-byte loads of value pairs (i, i+1), i even, four per row in flight
-    // per thread; Makhoul slots i/2 and n-1-i/2
+  int l0 = 0;
+  if (nx >= 4 && (reinterpret_cast<uintptr_t>(h) & 15) == 0) {
+    // Makhoul order v[j] = x[2j], v[n-1-j] = x[2j+1].  The value pairs at 2j
+    // and n-2-2j (j < n/4) give v[j], v[n-1-j], v[n/2-1-j] and v[n/2+j]:
+    // both inputs of the first radix-2 pass for columns j and n/2-1-j, done
+    // here in registers (Stockham, p = 1: outputs 2c and 2c+1 of column c).
     const double2* h2 = reinterpret_cast<const double2*>(h);
-    const int half = nx >> 1;
+    const int half = nx >> 1, quarter = nx >> 2;
 #pragma unroll 1
-    for (int q0 = 0; q0 < 8; q0 += 4) {
-      double2 va[4], vb[4];
+    for (int q0 = 0; q0 < 4; q0 += 2) {
+      double2 a0[2], b0[2], a1[2], b1[2];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e2 = threadIdx.x + (q0 + q) * THREADS;
-        const int g = e2 >> (lg - 1), i2 = e2 & (half - 1);
+      for (int q = 0; q < 2; ++q) {
+        const int e4 = threadIdx.x + (q0 + q) * THREADS;
+        const int g = e4 >> (lg - 2), j = e4 & (quarter - 1);
         const int r0 = 2 * (pair0 + g), r1 = r0 + 1;
-        va[q] = r0 < ny ? h2[(size_t)r0 * half + i2] : make_double2(H0, H0);
-        vb[q] = r1 < ny ? h2[(size_t)r1 * half + i2] : make_double2(H0, H0);
+        const double2 fill = make_double2(H0, H0);
+        a0[q] = r0 < ny ? h2[(size_t)r0 * half + j] : fill;
+        b0[q] = r0 < ny ? h2[(size_t)r0 * half + half - 1 - j] : fill;
+        a1[q] = r1 < ny ? h2[(size_t)r1 * half + j] : fill;
+        b1[q] = r1 < ny ? h2[(size_t)r1 * half + half - 1 - j] : fill;
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e2 = threadIdx.x + (q0 + q) * THREADS;
-        const int g = e2 >> (lg - 1), i2 = e2 & (half - 1);
-        const int base = g << lg;
-        zbuf[pad16(base + i2)] = make_float2(zeta_f32(va[q].x, H0, H0hi, H0lo), zeta_f32(vb[q].x, H0, H0hi, H0lo));
-        zbuf[pad16(base + nx - 1 - i2)] =
-            make_float2(zeta_f32(va[q].y, H0, H0hi, H0lo), zeta_f32(vb[q].y, H0, H0hi, H0lo));
+      for (int q = 0; q < 2; ++q) {
+        const int e4 = threadIdx.x + (q0 + q) * THREADS;
+        const int g = e4 >> (lg - 2), j = e4 & (quarter - 1);
+        const int base = g << lg, jc = half - 1 - j;
+        // (row r0 real, row r1 imaginary); the FP64 route only when a lane
+        // of the warp needs it (a uniform branch, not run otherwise)
+        bool ok[8];
+        float2 vj = make_float2(zeta_fast(a0[q].x, H0hi, H0lo, ok[0]), zeta_fast(a1[q].x, H0hi, H0lo, ok[1]));
+        float2 vn = make_float2(zeta_fast(a0[q].y, H0hi, H0lo, ok[2]), zeta_fast(a1[q].y, H0hi, H0lo, ok[3]));
+        float2 vc = make_float2(zeta_fast(b0[q].x, H0hi, H0lo, ok[4]), zeta_fast(b1[q].x, H0hi, H0lo, ok[5]));
+        float2 vh = make_float2(zeta_fast(b0[q].y, H0hi, H0lo, ok[6]), zeta_fast(b1[q].y, H0hi, H0lo, ok[7]));
+        const bool all_ok = ok[0] && ok[1] && ok[2] && ok[3] && ok[4] && ok[5] && ok[6] && ok[7];
+        if (__any_sync(0xffffffffu, !all_ok)) {
+          vj = make_float2(zeta_f32(a0[q].x, H0, H0hi, H0lo), zeta_f32(a1[q].x, H0, H0hi, H0lo));
+          vn = make_float2(zeta_f32(a0[q].y, H0, H0hi, H0lo), zeta_f32(a1[q].y, H0, H0hi, H0lo));
+          vc = make_float2(zeta_f32(b0[q].x, H0, H0hi, H0lo), zeta_f32(b1[q].x, H0, H0hi, H0lo));
+          vh = make_float2(zeta_f32(b0[q].y, H0, H0hi, H0lo), zeta_f32(b1[q].y, H0, H0hi, H0lo));
+        }
+        // column j: v[j] +- v[j + n/2] (= vh); column jc: v[jc] (= vc) +- v[jc + n/2] (= vn)
+        zbuf[pad16(base + 2 * j)] = make_float2(vj.x + vh.x, vj.y + vh.y);
+        zbuf[pad16(base + 2 * j + 1)] = make_float2(vj.x - vh.x, vj.y - vh.y);
+        zbuf[pad16(base + 2 * jc)] = make_float2(vc.x + vn.x, vc.y + vn.y);
+        zbuf[pad16(base + 2 * jc + 1)] = make_float2(vc.x - vn.x, vc.y - vn.y);
       }
     }
+    l0 = 1;
   } else {
     for (int e = threadIdx.x; e < G * nx; e += THREADS) {
       const int g = e >> lg, i = e & (nx - 1);
@@ -254,7 +304,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_dct_rows(const doub
     }
   }
   __syncthreads();
-  fft_lines<THREADS>(zbuf, nx, lg, tw);
+  fft_lines<THREADS>(zbuf, nx, lg, tw, l0);
   for (int e = threadIdx.x; e < G * Pb; e += THREADS) {
     const int g = e / Pb, k = e - g * Pb;
     const int r0 = 2 * (pair0 + g), r1 = r0 + 1;
@@ -457,11 +507,15 @@ __device__ __forceinline__ int interval_end(int j, int K, int M, int ppi) {
   return j == K - 1 ? M : (j + 1) * ppi;
 }
 
-// Second-order difference of y at e (central inside, one-sided at the ends).
-__device__ __forceinline__ double diff2(const double* y, int e, int n, double dq) {
-  if (e == 0) return (-3.0 * y[0] + 4.0 * y[1] - y[2]) / (2.0 * dq);
-  if (e == n - 1) return (3.0 * y[n - 1] - 4.0 * y[n - 2] + y[n - 3]) / (2.0 * dq);
-  return (y[e + 1] - y[e - 1]) / (2.0 * dq);
+// 1/k for the moving-average windows (k = 1..7).
+__constant__ double c_inv_count[8] = {0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7};
+
+// Second-order difference of y at e (central inside, one-sided at the
+// ends); i2dq = 1 / (2 dq).
+__device__ __forceinline__ double diff2(const double* y, int e, int n, double i2dq) {
+  if (e == 0) return (-3.0 * y[0] + 4.0 * y[1] - y[2]) * i2dq;
+  if (e == n - 1) return (3.0 * y[n - 1] - 4.0 * y[n - 2] + y[n - 3]) * i2dq;
+  return (y[e + 1] - y[e - 1]) * i2dq;
 }
 
 // Nodes and normal equations of the hat-function basis, one thread per
@@ -510,7 +564,7 @@ __global__ void k_fit_assemble(FitArgs f) {
 // separators); that leaves a tridiagonal Schur complement on the
 // separators, solved by parallel cyclic reduction in one block; every
 // interior unknown is then recovered from its two separators.
-constexpr int kReduced = 128;
+constexpr int kReduced = 512;
 
 __host__ __device__ __forceinline__ int fit_chunk(int K) { return max(2, (K + 1 + kReduced - 1) / kReduced); }
 
@@ -526,29 +580,42 @@ __global__ void k_fit_blocks(FitArgs f) {
   double* __restrict__ zz = f.zz;
   double* __restrict__ za = f.za;
   double* __restrict__ zb = f.zb;
-  double cpv = 0.0, zv = 0.0, av = 0.0, bv = 0.0;
+  // forward sweep, the next row's inputs loaded one row ahead
+  double cpv = 0.0, zv = 0.0, av = 0.0, bv = 0.0, sub = 0.0;
+  double dn = dg[first], rn = rh[first], on = first < last ? of[first] : 0.0;
   for (int u = first; u <= last; ++u) {
-    const double sub = u > first ? of[u - 1] : 0.0;
-    const double inv = 1.0 / (dg[u] - sub * cpv);
-    cpv = (u < last ? of[u] : 0.0) * inv;
-    zv = (rh[u] - sub * zv) * inv;
+    const double d = dn, r = rn, o = on;
+    if (u < last) {
+      dn = dg[u + 1];
+      rn = rh[u + 1];
+      on = u + 1 < last ? of[u + 1] : 0.0;
+    }
+    const double inv = 1.0 / (d - sub * cpv);
+    cpv = o * inv;
+    zv = (r - sub * zv) * inv;
     av = ((u == first ? of[first - 1] : 0.0) - sub * av) * inv;
     bv = ((u == last ? of[last] : 0.0) - sub * bv) * inv;
     cp[u] = cpv;
     zz[u] = zv;
     za[u] = av;
     zb[u] = bv;
+    sub = o;  // the next row's sub-diagonal is this row's coupling
   }
+  // back substitution, the row below carried in registers
+  double zn = zz[last], an = za[last], bnx = zb[last];
   for (int u = last - 1; u >= first; --u) {
     const double cu = cp[u];
-    zz[u] -= cu * zz[u + 1];
-    za[u] -= cu * za[u + 1];
-    zb[u] -= cu * zb[u + 1];
+    zn = zz[u] - cu * zn;
+    an = za[u] - cu * an;
+    bnx = zb[u] - cu * bnx;
+    zz[u] = zn;
+    za[u] = an;
+    zb[u] = bnx;
   }
 }
 
 __global__ void __launch_bounds__(kReduced) k_fit_reduced(FitArgs f) {
-  __shared__ double sl[kReduced], sd[kReduced], su[kReduced], sr[kReduced];
+  __shared__ double sl[kReduced], sd[kReduced], su[kReduced], sr[kReduced], si[kReduced];
   const int K = f.K, c = fit_chunk(K), S = K / c;
   const int b = threadIdx.x + 1;  // separator b (row b - 1 of the reduced system)
   if (threadIdx.x == 0) f.a[0] = 0.0;
@@ -572,18 +639,20 @@ __global__ void __launch_bounds__(kReduced) k_fit_reduced(FitArgs f) {
   __syncthreads();
   const int i = threadIdx.x;
   for (int st = 1; st < S; st <<= 1) {
+    if (i < S) si[i] = 1.0 / sd[i];
+    __syncthreads();
     double nl = 0.0, nd = 0.0, nu = 0.0, nr = 0.0;
     if (i < S) {
       nd = sd[i];
       nr = sr[i];
       if (i - st >= 0) {
-        const double al = -sl[i] / sd[i - st];
+        const double al = -sl[i] * si[i - st];
         nd += al * su[i - st];
         nr += al * sr[i - st];
         nl = al * sl[i - st];
       }
       if (i + st < S) {
-        const double ga = -su[i] / sd[i + st];
+        const double ga = -su[i] * si[i + st];
         nd += ga * sl[i + st];
         nr += ga * sr[i + st];
         nu = ga * su[i + st];
@@ -644,20 +713,20 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_peaks(FitArgs f) {
       const int lo = max(0, e - P), hi = min(n - 1, e + P);
       double acc = 0.0;
       for (int i = lo; i <= hi; ++i) acc += src[i];
-      dst[e] = acc / (double)(hi - lo + 1);
+      dst[e] = acc * c_inv_count[hi - lo + 1];
     }
     __syncthreads();
     double* tmp = src;
     src = dst;
     dst = tmp;
   }
-  const double dq = f.q_cut / (double)(n - 1);
+  const double i2dq = (double)(n - 1) / (2.0 * f.q_cut);
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     f.cv[e] = src[e];
-    f.d[e] = diff2(src, e, n, dq);
+    f.d[e] = diff2(src, e, n, i2dq);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < n; e += blockDim.x) f.s[e] = diff2(f.d, e, n, dq);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) f.s[e] = diff2(f.d, e, n, i2dq);
   __syncthreads();
   // maxima: candidates in any order (w0, w1), then each placed by its rank
   // (highest value first, ties by wavenumber)
@@ -962,15 +1031,7 @@ int tf_spectrum_plan_create(int nx, int ny, double ds, const tf_spectrum_params*
   P->K = std::max(1, (P->M - 1 + sp->points_per_interval - 1) / sp->points_per_interval);
 
   // opt-in shared memory of the FFT blocks (padded 16 THREADS values)
-  {
-    float2 w16[8];
-    for (int m = 0; m < 8; ++m) {
-      const double a = -2.0 * 3.14159265358979323846 * m / 16.0;
-      w16[m] = make_float2((float)cos(a), (float)sin(a));
-    }
-    e = cudaMemcpyToSymbol(c_w16, w16, sizeof(w16));
-  }
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dct_rows<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(512));
+  e = cudaFuncSetAttribute(k_dct_rows<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(512));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dct_cols<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(512));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dct_rows<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(1024));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dct_cols<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(1024));

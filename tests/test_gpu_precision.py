@@ -6,8 +6,10 @@ FP64-class fixed point.  On a 1024^2 film at the nucleation workload's
 spacing (lambda_m / 32), with 1e-4 noise plus Gaussian depressions of depth
 0.3 h0 and width lambda_m / 4, FP64 runs the adaptive controller to 6/sigma_max
 (or rupture) and FP32-bulk replays its step sizes.  Required: relative mass
-error <= 1e-6 in both modes, the same dominant wavenumber (radial DCT
-spectrum) in both, and that wavenumber near the linear-stability k_m.
+error <= 1e-6 in both modes, the same dominant wavenumber in both (the
+radial Fourier analysis of App. Radial Fourier Transform, on the GPU,
+checked against the oracle's), and that wavenumber near the
+linear-stability k_m.
 """
 import json
 import math
@@ -16,8 +18,8 @@ import os
 import numpy as np
 import pytest
 
+import oracle.radial_fourier as RF
 import paper_1806_10550_gb300 as tf
-from paper_1806_10550_gb300 import analysis as A
 from paper_1806_10550_gb300 import synthetic as S
 
 pytestmark = pytest.mark.gpu
@@ -55,10 +57,14 @@ def test_fp32_bulk_keeps_mass_and_dominant_wavelength(torch):
     m0 = h0.sum()
     assert abs(a64.sum() - m0) <= 1e-6 * m0
     assert abs(a32.sum() - m0) <= 1e-6 * m0
-    k64 = A.dominant_wavenumber(a64, w["ds"])
-    k32 = A.dominant_wavenumber(a32, w["ds"])
-    assert k64 == k32
     km = 2 * math.pi / lam
+    q_cut = 5 * km
+    plan = tf.SpectrumPlan(N, N, w["ds"], tf.tf_spectrum_params_default(H0=w["h0"], q_cut=q_cut))
+    k64 = tf.tf_spectrum_run(plan, h64, outputs=False)["q_dominant"]
+    k32 = tf.tf_spectrum_run(plan, h32, outputs=False)["q_dominant"]
+    ko = RF.analyse(a64, w["ds"], w["h0"], q_cut)["q_dominant"]
+    assert abs(k64 - ko) <= 1e-6 * q_cut
+    assert abs(k64 - k32) <= 1e-3 * km
     assert abs(k64 - km) <= 0.25 * km
     # the film itself: FP32-bulk within Newton-tolerance accumulation of FP64
     assert np.max(np.abs(a32 - a64)) <= 1e-5

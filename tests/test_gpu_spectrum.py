@@ -43,10 +43,10 @@ def dev(torch, a):
 
 def fft_bound(h, H0):
     # FP32 transform (see the module docstring) plus the formation of zeta
-    # in FP32 pieces: within 2^-24 |zeta| + 2^-47 (|h| + |H0|) per cell
+    # in FP32 pieces: within 2^-24 |zeta| + 2^-45 (|h| + |H0|) per cell
     ny, nx = h.shape
     rms = math.sqrt(np.mean((h - H0) ** 2))
-    return (math.log2(nx * ny) + 6) * 8 * U32 * rms + 2.0 ** -47 * (np.max(np.abs(h)) + abs(H0))
+    return (math.log2(nx * ny) + 6) * 8 * U32 * rms + 2.0 ** -45 * (np.max(np.abs(h)) + abs(H0))
 
 
 def run_gpu(torch, h, ds, **kw):
@@ -198,3 +198,15 @@ def test_full_size_workload(torch):
     pk = RF.local_maxima(*RF.sample_and_smooth(r["node_q"], r["node_value"], q_cut))
     assert abs(r["q_dominant"] - pk[0][0]) <= 1e-9 * q_cut
     assert abs(r["q_dominant"] - qm) <= 0.05 * qm
+
+
+def test_heights_outside_the_fast_conversion_range(torch):
+    # zero, negative and tiny heights take the FP64 route for zeta (the
+    # transform is FP32: heights beyond its range are not representable)
+    nx, ny, ds = 128, 64, 1.0
+    h = S.ring_film(nx, ny, ds, 1.0, 0.05, 2 * math.pi / 8, 0.05, 32, 0.002, seed=21)
+    h[3, 5], h[10, 77], h[40, 1], h[63, 127], h[0, 0] = 0.0, -0.5, 1e-25, 1e30, 2.0 ** -70
+    q_cut = 0.5 * math.pi / ds
+    _, r = run_gpu(torch, h, ds, H0=1.0, q_cut=q_cut)
+    A = RF.amplitude(h, 1.0, r["n_p"], r["n_q"])
+    assert np.max(np.abs(r["amplitude"] - A)) <= fft_bound(h, 1.0)
