@@ -8,7 +8,9 @@ The arithmetic lives in ``tf_oracle.c`` (plain C, IEEE double, no FMA
 contraction).  This module compiles it on first use with ``gcc`` and wraps it
 with ``ctypes`` over NumPy float64 arrays in row-major ``[ny, nx]`` layout.
 The radial Fourier analysis of films (App. Radial Fourier Transform) is
-``oracle.radial_fourier`` (NumPy/SciPy, FP64).
+``oracle.radial_fourier`` (NumPy/SciPy, FP64); the discrete adjoint of the
+unrolled time step is ``oracle.adjoint`` (complex steps through a NumPy
+restatement of the forward map).
 
 Paper: Lam, Cummings & Kondic, "Computing dynamics of thin films via large
 scale GPU-based simulations" -- Sec. Numerical Method (flux form, eq.
