@@ -597,6 +597,144 @@ def reference_spectrum(args, w):
     print(json.dumps(line))
 
 
+ADJOINT_METRIC = "adjoint film cell-steps/s (forward + reverse of the 3-iteration step) at 1024^2"
+
+# FP64 flops (2 per DFMA, 1 per DADD/DMUL) per cell of the dominant adjoint
+# kernels, from the ncu capture summarised in profiles/adjoint_kernels_adjoint1k.md
+# (the counts do not depend on the grid size).  None until captured for the
+# kernels as they are.
+ADJ_FLOPS_PER_CELL = {"line_x": None, "line_y": None, "D": None}
+
+
+def adjoint_config(w, world):
+    N = w["N"]
+    return dict(workload=(f"{N}x{N} spinodal film, power-law model, {w['P']} lambda_m square, "
+                          f"seed {w['seed']}, dt {w['dt_fixed']}, {w['fixed_iter']} Newton iterations unrolled"),
+                mode="FP64", global_batch=world, l2="working set larger than L2 (about 20 grids of 8 MiB)",
+                parallelism=f"replicas x{world}")
+
+
+def oracle_adjoint_sample(w, n=12):
+    """The oracle's adjoint (complex-step Jacobian, transposed) on an n x n
+    sample of the workload (same spacing, dt and noise)."""
+    import oracle as O
+    import oracle.adjoint as AD
+    from paper_1806_10550_gb300 import synthetic as S
+    M = O.Model(nx=n, ny=n, ds=w["ds"], kappa=w["kappa"], b=w["b"], n=w["n"], m=w["m"], cap_C=w["cap_C"],
+                theta=w["theta"])
+    u = S.spinodal_film(n, n, w["h0"], w["eps"], w["seed"])
+    g = np.random.default_rng(1).standard_normal((n, n))
+    t = time.perf_counter()
+    AD.vjp(M, u, w["dt_fixed"], w["fixed_iter"], g)
+    return time.perf_counter() - t, n
+
+
+def run_adjoint(args, w):
+    """Forward and reverse of the fixed-iteration step per timed step
+    (tf_adjoint_step), grids resident in HBM; e2e adds the copies of the film
+    and the cotangent from pinned host memory and of the result back."""
+    import torch
+    import paper_1806_10550_gb300 as tf
+    from paper_1806_10550_gb300 import synthetic as S
+    rank, world, local, dist = dist_setup()
+    tf.library(build_if_missing=True)
+    N, K, dt = w["N"], w["fixed_iter"], w["dt_fixed"]
+    ctx = tf.Context(tf.params_for_workload(w, tf.TF_FP64))
+    h_host = torch.from_numpy(S.spinodal_film(N, N, w["h0"], w["eps"], w["seed"])).pin_memory()
+    g_host = torch.from_numpy(np.random.default_rng(5).standard_normal((N, N))).pin_memory()
+    h, g = h_host.cuda(), g_host.cuda()
+    gh = torch.empty_like(h)
+    for _ in range(args.warmup):
+        tf.tf_adjoint_step(ctx, h, dt, K, g, g_h=gh)
+    S_ = args.steps if args.steps != 200 else 10
+    groups = {k: 0.0 for k in tf.ADJOINT_GROUPS}
+    barrier(dist)
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with clocks:
+        e0.record()
+        for _ in range(S_):
+            r = tf.tf_adjoint_step(ctx, h, dt, K, g, g_h=gh)
+            for k, v in tf.tf_adjoint_timing().items():
+                groups[k] += v
+        e1.record()
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = e0.elapsed_time(e1)
+    value = job_rate(dist, N * N * S_, ms)
+    # end to end from pinned host buffers
+    hd, gd, out = torch.empty_like(h), torch.empty_like(g), torch.empty_like(h_host).pin_memory()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(S_):
+        hd.copy_(h_host, non_blocking=True)
+        gd.copy_(g_host, non_blocking=True)
+        tf.tf_adjoint_step(ctx, hd, dt, K, gd, g_h=gh)
+        out.copy_(gh, non_blocking=True)
+    e3.record()
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    per = {k: v / S_ for k, v in groups.items()}
+    launches = {"forward": None, "band": 2 * K, "solve_t": 2 * K, "line_x": K, "line_y": K, "D": K + 1,
+                "kappa": 3 * K + 1}
+    dom = max(("line_x", "line_y", "D"), key=lambda k: per[k])
+    n_l = launches[dom]
+    ms_launch = per[dom] / n_l
+    fpc = ADJ_FLOPS_PER_CELL.get(dom)
+    ach = None if fpc is None else fpc * N * N / (ms_launch * 1e-3) / 1e12
+    roof = dict(bound="alu", kernel=dom, unit="TFLOP/s", peak=FP64_TFLOPS,
+                peak_source="measured FP64 FMA throughput probe", ms_per_launch=round(ms_launch, 3),
+                achieved=None if ach is None else round(ach, 4),
+                frac=None if ach is None else round(ach / FP64_TFLOPS, 4),
+                flops_per_cell=fpc, traffic=None)
+    line = dict(
+        metric=ADJOINT_METRIC, value=value, unit="cell-steps/s", n_gpus=world, steps=S_, warmup=args.warmup,
+        ms_per_step=ms / S_, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+        data="synthetic", config=adjoint_config(w, world), g_kappa=r["g_kappa"],
+        group_ms_per_step={k: round(v, 3) for k, v in per.items()}, roofline=roof,
+        # per step: forward 6 per iteration (explicit part, residual, x and y
+        # sweeps, finalize, film statistics); reverse 2K band, 2K solve, 2K
+        # line, K+1 D, 3K+1 kappa and 2K+1 axpy kernels
+        gpu_launches=S_ * (18 * K + 3),
+        e2e=dict(value=job_rate(dist, N * N * S_, ms_e2e), unit="cell-steps/s",
+                 h2d_bytes_per_step=2 * N * N * 8, d2h_bytes_per_step=N * N * 8),
+    )
+    cs = clocks.summary()
+    line["clocks"] = dict(sm_mhz=cs["sm_mhz"], sm_max_mhz=cs["sm_max_mhz"], reasons=cs["reasons"])
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+        el, n = oracle_adjoint_sample(w)
+        line["cpu_baseline"] = dict(value=n * n / el, unit="cell-steps/s", cores=O.num_threads(), kind="oracle",
+                                    sample=(f"the oracle's adjoint of a {n}x{n} sample (complex-step Jacobian: "
+                                            f"{n * n} forward steps), {el:.1f} s"))
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def reference_adjoint(args, w):
+    """The oracle's adjoint as the reference arm: each step one oracle adjoint
+    of a 12 x 12 sample of the workload."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle as O
+    K = min(args.steps, 3)
+    el = 0.0
+    for _ in range(K):
+        dt_, n = oracle_adjoint_sample(w)
+        el += dt_
+    value = n * n * K / el
+    line = dict(metric=ADJOINT_METRIC, value=value, unit="cell-steps/s", n_gpus=args.gpus, steps=K,
+                warmup=args.warmup, ms_per_step=el * 1e3 / K, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=adjoint_config(w, args.gpus),
+                cpu_baseline=dict(value=value, unit="cell-steps/s", cores=O.num_threads(), kind="oracle",
+                                  sample=f"{K} oracle adjoints of a {n}x{n} sample"),
+                e2e=dict(value=value, unit="cell-steps/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -612,6 +750,9 @@ def main():
     w = load_workload(args.workload)
     if args.workload == "spectrum8k":
         (reference_spectrum if args.impl == "reference" else run_spectrum)(args, w)
+        return
+    if args.workload == "adjoint1k":
+        (reference_adjoint if args.impl == "reference" else run_adjoint)(args, w)
         return
     if args.workload == "ensemble" and args.impl == "ours":
         # one hardware work queue per stream (up to 32) before CUDA starts,

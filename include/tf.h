@@ -262,6 +262,35 @@ int tf_timing_get(const tf_ctx* ctx, tf_timing* out);
 int tf_residual_noalloc(const tf_params* p, void* stream, const double* h_k,
                         const double* h_old, double dt, double* G, tf_norms* out);
 
+/* ---- discrete adjoint of the fixed-iteration time step -------------------
+ * The time step with exactly K Newton iterations at step size dt (Sec.
+ * Numerical Method, no convergence test) is a smooth map
+ *   u^n -> u^K:  b = u^n - (1-theta) dt D(u^n),  u_0 = u^n,
+ *   (I + theta dt J_x(u_k)) w_k = -G(u_k),  (I + theta dt J_y(u_k)) v_k = w_k,
+ *   u_{k+1} = u_k + v_k.
+ * tf_adjoint_step runs it forward (the FP64 path, keeping every u_k, w_k,
+ * v_k) and then its reverse: given the cotangent g of u^K it returns
+ * g_h = (du^K/du^n)^T g and g_kappa = (du^K/dkappa)^T g, through transposed
+ * line solves (y lines, then x lines, each iteration in reverse order) and
+ * the transposed derivatives of D and of the line operators' dependence on
+ * u (forward-mode dual numbers, one gather per cell, no atomics).
+ * The context must be TF_FP64 with the power-law or linear model.
+ * h_old, g: device grids; h_new: device grid or NULL (receives u^K);
+ * g_h: device output grid (not aliasing h_old, g or h_new); g_kappa,
+ * g_theta: host outputs or NULL (g_theta = g_kappa dkappa/dtheta_c when
+ * kappa was derived from the contact angle, else 0).  K: 1..64.
+ * Workspace (3K + 12 grids) is allocated on first use and kept by the
+ * context.  Synchronises the context's stream.  Returns TF_OK, TF_ERR_ARG,
+ * TF_ERR_NOMEM or TF_ERR_CUDA (or a forward iteration's error).         */
+int tf_adjoint_step(tf_ctx* ctx, const double* h_old, double dt, int K, const double* g,
+                    double* h_new, double* g_h, double* g_kappa, double* g_theta);
+
+/* Kernel time (ms, CUDA events) of the last tf_adjoint_step in this
+ * process, by group: forward iterations, band assembly, transposed line
+ * solves, x-line coefficient derivatives, y-line coefficient derivatives,
+ * D derivatives, kappa terms.  n: entries wanted (up to 7).              */
+int tf_adjoint_timing(double* ms, int n);
+
 /* ---- radial Fourier analysis of a film (App. Radial Fourier Transform) ---
  * The dominant wavenumber of a film pattern, all steps on the GPU, in the
  * appendix's order:

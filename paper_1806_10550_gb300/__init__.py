@@ -9,7 +9,8 @@ CPU fallback: without the built library or a CUDA device every call raises.
 Functions carry the names of the C ABI: ``tf_params_default``, ``tf_init``,
 ``tf_destroy``, ``tf_residual``, ``tf_newton_iteration``,
 ``tf_newton_adi_step``, ``tf_advance``, ``tf_ensemble_advance``, ``tf_strerror``,
-and for the radial Fourier analysis ``tf_spectrum_params_default``,
+``tf_adjoint_step`` (the reverse of the fixed-iteration step), and for the
+radial Fourier analysis ``tf_spectrum_params_default``,
 ``tf_spectrum_plan_create``, ``tf_spectrum_run``, ``tf_spectrum_plan_info``,
 ``tf_spectrum_timing``, ``tf_spectrum_plan_destroy``.
 """
@@ -135,6 +136,8 @@ def library(build_if_missing: bool = True):
                                       C.POINTER(TfAdvanceInfo)]
     L.tf_timing_enable.argtypes = [vp, C.c_int]
     L.tf_timing_get.argtypes = [vp, C.POINTER(TfTiming)]
+    L.tf_adjoint_step.argtypes = [vp, vp, dp, C.c_int, vp, vp, vp, C.POINTER(dp), C.POINTER(dp)]
+    L.tf_adjoint_timing.argtypes = [C.POINTER(dp), C.c_int]
     L.tf_spectrum_params_default.argtypes = [C.POINTER(TfSpectrumParams)]
     L.tf_spectrum_params_default.restype = None
     L.tf_spectrum_plan_create.argtypes = [C.c_int, C.c_int, dp, C.POINTER(TfSpectrumParams), vp,
@@ -145,7 +148,9 @@ def library(build_if_missing: bool = True):
     L.tf_spectrum_run.argtypes = [vp, vp, C.POINTER(TfSpectrumOut), C.POINTER(TfSpectrumInfo)]
     L.tf_spectrum_timing.argtypes = [vp, C.POINTER(dp), C.c_int]
     for f in ("tf_init", "tf_residual", "tf_newton_iteration", "tf_newton_adi_step", "tf_advance",
-              "tf_ensemble_advance", "tf_timing_enable", "tf_timing_get", "tf_spectrum_plan_create",
+              "tf_ensemble_advance", "tf_timing_enable", "tf_timing_get", "tf_adjoint_step",
+              "tf_adjoint_timing",
+              "tf_spectrum_plan_create",
               "tf_spectrum_plan_info", "tf_spectrum_run", "tf_spectrum_timing"):
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -310,6 +315,30 @@ def tf_ensemble_advance(ctxs, hs, t0, t_end, dt0, max_attempts):
            "tf_ensemble_advance")
     return [dict(status=i.status, attempts=i.attempts, accepted=i.accepted,
                  newton_iterations=i.newton_iterations, t=i.t, dt=i.dt) for i in infos[:n]]
+
+
+def tf_adjoint_step(ctx: Context, h_old, dt: float, K: int, g, g_h=None, h_new=None) -> dict:
+    """Reverse of the K-iteration time step from ``h_old``: returns dict with
+    ``g_h`` (the cotangent of h_old, a CUDA tensor), ``g_kappa``, ``g_theta``
+    and ``h_new`` (u^K) when given or requested."""
+    torch = _torch()
+    if g_h is None:
+        g_h = torch.empty_like(g)
+    gk, gt = C.c_double(), C.c_double()
+    _check(library().tf_adjoint_step(ctx.handle, ctx.ptr(h_old, "h_old"), float(dt), int(K),
+                                     ctx.ptr(g, "g"), ctx.ptr(h_new, "h_new"), ctx.ptr(g_h, "g_h"),
+                                     C.byref(gk), C.byref(gt)), "tf_adjoint_step")
+    return dict(g_h=g_h, g_kappa=gk.value, g_theta=gt.value, h_new=h_new)
+
+
+ADJOINT_GROUPS = ("forward", "band", "solve_t", "line_x", "line_y", "D", "kappa")
+
+
+def tf_adjoint_timing() -> dict:
+    """Kernel time (ms) of the last tf_adjoint_step by group."""
+    ms = (C.c_double * len(ADJOINT_GROUPS))()
+    _check(library().tf_adjoint_timing(ms, len(ADJOINT_GROUPS)), "tf_adjoint_timing")
+    return dict(zip(ADJOINT_GROUPS, list(ms)))
 
 
 def tf_timing_enable(ctx: Context, on: bool = True):

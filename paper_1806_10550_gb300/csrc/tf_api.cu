@@ -359,6 +359,7 @@ const char* tf_strerror(int code) {
 
 void tf_destroy(tf_ctx* c) {
   if (!c) return;
+  if (c->adj_ws) cudaFree(c->adj_ws);
   cudaFree(c->bn);
   cudaFree(c->w);
   cudaFree(c->ulp);

@@ -62,4 +62,6 @@ struct tf_ctx {
   tf::Scalars* hsc;  // pinned
   tf_timing timing;
   cudaEvent_t ev[8];  // 0-4 iteration timing, 5-6 explicit-part timing, 7 work done (ensembles)
+  void* adj_ws;       // workspace of tf_adjoint_step (grown on demand)
+  size_t adj_bytes;
 };
