@@ -603,7 +603,7 @@ ADJOINT_METRIC = "adjoint film cell-steps/s (forward + reverse of the 3-iteratio
 # kernels, from the ncu capture summarised in profiles/adjoint_kernels_adjoint1k.md
 # (the counts do not depend on the grid size).  None until captured for the
 # kernels as they are.
-ADJ_FLOPS_PER_CELL = {"line_x": 15426.0, "line_y": 15242.0, "D": 11030.0}
+ADJ_FLOPS_PER_CELL = {"line_x": 1940.2, "line_y": 1726.9, "D": 930.0}
 
 
 def adjoint_config(w, world):

@@ -331,6 +331,34 @@ def tf_adjoint_step(ctx: Context, h_old, dt: float, K: int, g, g_h=None, h_new=N
     return dict(g_h=g_h, g_kappa=gk.value, g_theta=gt.value, h_new=h_new)
 
 
+def unrolled_step(h, ctx: Context, dt: float, K: int):
+    """u^K of the time step with exactly K Newton iterations from ``h``, as a
+    differentiable torch operation: the forward runs K tf_newton_iteration
+    calls, the backward tf_adjoint_step (which recomputes the forward, so
+    only h is kept between the two).  ``ctx``: an FP64 context."""
+    torch = _torch()
+
+    class _UnrolledStep(torch.autograd.Function):
+        @staticmethod
+        def forward(actx, x):
+            u = x.detach().contiguous()
+            cur = u
+            w, v = torch.empty_like(u), torch.empty_like(u)
+            for _ in range(int(K)):
+                nxt = torch.empty_like(u)
+                tf_newton_iteration(ctx, cur, u, dt, nxt, w=w, v=v)
+                cur = nxt
+            actx.save_for_backward(u)
+            return cur
+
+        @staticmethod
+        def backward(actx, g):
+            (u,) = actx.saved_tensors
+            return tf_adjoint_step(ctx, u, dt, int(K), g.contiguous())["g_h"]
+
+    return _UnrolledStep.apply(h)
+
+
 ADJOINT_GROUPS = ("forward", "band", "solve_t", "line_x", "line_y", "D", "kappa")
 
 
@@ -470,4 +498,4 @@ def params_for_workload(w: dict, precision: int = TF_FP64, **overrides) -> TfPar
 
 
 __all__ = [n for n in dir() if n.startswith(("tf_", "TF_", "Tf"))] + [
-    "Context", "SpectrumPlan", "library", "params_for_workload"]
+    "Context", "SpectrumPlan", "library", "params_for_workload", "unrolled_step"]

@@ -14,7 +14,10 @@
 // and finally ubar += bbar - (1-theta) dt D'(u^n)^T bbar; the kappa
 // cotangent collects the same terms' kappa derivatives.
 //
-// Derivatives: forward-mode dual numbers.  The value of D at a cell depends
+// Derivatives: forward-mode dual numbers over per-iterate tables (the
+// mobilities with two derivatives and the Laplacian, formed once per
+// iterate), so a seeded evaluation only propagates the seeded cell's known
+// partials.  The value of D at a cell depends
 // on u within the 13-cell diamond |dx| + |dy| <= 2 around it, and a row of
 // A_x(u) w on u within the box |dx| <= 2, |dy| <= 1 (A_y: transposed).  So
 // the transposed product at cell j is a gather over the cells c whose
@@ -40,57 +43,93 @@ __device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual{a.v + b.
 __device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual{a.v - b.v, a.d - b.d}; }
 __device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual{a.v * b.v, a.v * b.d + a.d * b.v}; }
 __device__ __forceinline__ Dual operator*(double s, Dual a) { return Dual{s * a.v, s * a.d}; }
-__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
-  const double q = a.v / b.v;
-  return Dual{q, (a.d - q * b.d) / b.v};
-}
-__device__ __forceinline__ Dual pow_i(Dual x, int k) {
-  Dual r = mk(1.0);
-  for (int i = 0; i < k; ++i) r = r * x;
-  return r;
-}
 
 struct AdjK {
   int nx, ny, model, n, m;
   double ds, inv_ds, C, b, c0, c1, kappa, tdt;  // tdt = theta dt
 };
 
-// The film seen by one evaluation: u with cell (pi, pj) seeded (seed 1) or
-// none (pi = -1); kappa seeded separately.
-struct Film {
-  const double* u;
-  int nx, pi, pj;
-  __device__ __forceinline__ Dual at(int i, int j) const {
-    return Dual{u[(size_t)j * nx + i], (i == pi && j == pj) ? 1.0 : 0.0};
-  }
+// Per-cell values of the iterate, formed once per iterate (FP64):
+// f0, f1, f0', f1', f0'', f1'' (Sec. Thin Film Models: f0 = C h^3,
+// f1 = h^3 Pi'(h), Pi = kappa[(b/h)^n - (b/h)^m]) and the Laplacian.
+struct Tables {
+  double *f0, *f1, *d0, *d1, *e0, *e1, *lap;
 };
+
+__global__ void k_tables(AdjK M, const double* __restrict__ u, Tables T) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= M.nx) return;
+  const size_t c = (size_t)j * M.nx + i;
+  const double h = u[c];
+  if (M.model == TF_MODEL_LINEAR) {
+    T.f0[c] = M.c0;
+    T.f1[c] = M.c1;
+    T.d0[c] = T.d1[c] = T.e0[c] = T.e1[c] = 0.0;
+  } else {
+    // Pi' = kappa (m r^m - n r^n)/h, Pi'' = kappa (n(n+1) r^n - m(m+1) r^m)/h^2,
+    // Pi''' = kappa (m(m+1)(m+2) r^m - n(n+1)(n+2) r^n)/h^3, r = b/h
+    const double ih = 1.0 / h, r = M.b * ih;
+    double rm = 1.0, rn = 1.0;
+    for (int q = 0; q < M.m; ++q) rm *= r;
+    for (int q = 0; q < M.n; ++q) rn *= r;
+    const double n = M.n, m = M.m;
+    const double p1 = M.kappa * (m * rm - n * rn) * ih;
+    const double p2 = M.kappa * (n * (n + 1.0) * rn - m * (m + 1.0) * rm) * ih * ih;
+    const double p3 = M.kappa * (m * (m + 1.0) * (m + 2.0) * rm - n * (n + 1.0) * (n + 2.0) * rn) * ih * ih * ih;
+    const double h2 = h * h, h3 = h2 * h;
+    T.f0[c] = M.C * h3;
+    T.f1[c] = h3 * p1;
+    T.d0[c] = 3.0 * M.C * h2;
+    T.d1[c] = 3.0 * h2 * p1 + h3 * p2;
+    T.e0[c] = 6.0 * M.C * h;
+    T.e1[c] = 6.0 * h * p1 + 6.0 * h2 * p2 + h3 * p3;
+  }
+  double sl = 0.0;
+  if (i + 1 < M.nx) sl += u[c + 1] - h;
+  if (i > 0) sl += u[c - 1] - h;
+  if (j + 1 < M.ny) sl += u[c + M.nx] - h;
+  if (j > 0) sl += u[c - M.nx] - h;
+  T.lap[c] = sl * M.inv_ds * M.inv_ds;
+}
 
 struct Mob {
   Dual f0, f1, d0, d1;
 };
 
-// Sec. Thin Film Models: f0 = C h^3, f1 = h^3 Pi'(h) with Pi = kappa[(b/h)^n -
-// (b/h)^m], and their derivatives; or the linear model's constants.
-__device__ Mob mobility(const AdjK& M, Dual h, Dual kap) {
-  if (M.model == TF_MODEL_LINEAR) return Mob{mk(M.c0), mk(M.c1), mk(0.0), mk(0.0)};
-  const Dual r = mk(M.b) / h;
-  const Dual rm = pow_i(r, M.m), rn = pow_i(r, M.n);
-  const Dual dpi = kap * ((double)M.m * rm - (double)M.n * rn) / h;
-  const Dual d2pi = kap * ((double)(M.n * (M.n + 1)) * rn - (double)(M.m * (M.m + 1)) * rm) / (h * h);
-  const Dual h2 = h * h, h3 = h2 * h;
-  return Mob{M.C * h3, h3 * dpi, (3.0 * M.C) * h2, 3.0 * (h2 * dpi) + h3 * d2pi};
-}
-
-// Five-point Laplacian with even reflection (a missing neighbour adds 0).
-__device__ Dual laplacian(const AdjK& M, const Film& F, int i, int j) {
-  const Dual c = F.at(i, j);
-  Dual s = mk(0.0);
-  if (i + 1 < M.nx) s = s + (F.at(i + 1, j) - c);
-  if (i > 0) s = s + (F.at(i - 1, j) - c);
-  if (j + 1 < M.ny) s = s + (F.at(i, j + 1) - c);
-  if (j > 0) s = s + (F.at(i, j - 1) - c);
-  return (M.inv_ds * M.inv_ds) * s;
-}
+// The film seen by one evaluation: values from the tables, derivatives
+// with respect to the one seeded quantity -- u at cell (pi, pj) (pi < 0:
+// none) or kappa (kseed; f1 and f1' are linear in kappa).
+struct Film {
+  const double* u;
+  Tables T;
+  int nx, ny, pi, pj;
+  bool kseed;
+  double inv_kappa, inv_ds2;
+  __device__ __forceinline__ bool seeded(int i, int j) const { return i == pi && j == pj; }
+  __device__ __forceinline__ Dual at(int i, int j) const {
+    return Dual{u[(size_t)j * nx + i], seeded(i, j) ? 1.0 : 0.0};
+  }
+  __device__ __forceinline__ Mob mob(int i, int j) const {
+    const size_t c = (size_t)j * nx + i;
+    const double f0 = T.f0[c], f1 = T.f1[c], d0 = T.d0[c], d1 = T.d1[c];
+    if (kseed) return Mob{mk(f0), mk(f1, f1 * inv_kappa), mk(d0), mk(d1, d1 * inv_kappa)};
+    if (!seeded(i, j)) return Mob{mk(f0), mk(f1), mk(d0), mk(d1)};
+    return Mob{mk(f0, d0), mk(f1, d1), mk(d0, T.e0[c]), mk(d1, T.e1[c])};
+  }
+  // Five-point Laplacian with even reflection; its derivative with respect
+  // to the seeded cell is -(neighbours)/ds^2 at that cell, 1/ds^2 next to it.
+  __device__ __forceinline__ Dual lap(int i, int j) const {
+    const double v = T.lap[(size_t)j * nx + i];
+    if (pi < 0) return mk(v);
+    const int di = pi - i, dj = pj - j;
+    if (di == 0 && dj == 0) {
+      const int cnt = (i + 1 < nx) + (i > 0) + (j + 1 < ny) + (j > 0);
+      return mk(v, -(double)cnt * inv_ds2);
+    }
+    const int ad = (di < 0 ? -di : di) + (dj < 0 ? -dj : dj);
+    return mk(v, ad == 1 ? inv_ds2 : 0.0);
+  }
+};
 
 // Flux through the face from cell p to its +x or +y neighbour q:
 // F = fbar0 (L_q - L_p)/ds + fbar1 (u_q - u_p)/ds, fbar the two cells' mean.
@@ -99,26 +138,14 @@ __device__ Dual face_flux(const AdjK& M, Dual up, Dual uq, Dual lp, Dual lq, con
 }
 
 // D at cell (i, j) (eq. GovEqnCell2, zero wall fluxes).
-__device__ Dual D_cell(const AdjK& M, const Film& F, int i, int j, Dual kap) {
-  const Dual uc = F.at(i, j), lc = laplacian(M, F, i, j);
-  const Mob mc = mobility(M, uc, kap);
+__device__ Dual D_cell(const AdjK& M, const Film& F, int i, int j) {
+  const Dual uc = F.at(i, j), lc = F.lap(i, j);
+  const Mob mc = F.mob(i, j);
   Dual acc = mk(0.0);
-  if (i + 1 < M.nx) {
-    const Dual uq = F.at(i + 1, j);
-    acc = acc + face_flux(M, uc, uq, lc, laplacian(M, F, i + 1, j), mc, mobility(M, uq, kap));
-  }
-  if (i > 0) {
-    const Dual up = F.at(i - 1, j);
-    acc = acc - face_flux(M, up, uc, laplacian(M, F, i - 1, j), lc, mobility(M, up, kap), mc);
-  }
-  if (j + 1 < M.ny) {
-    const Dual uq = F.at(i, j + 1);
-    acc = acc + face_flux(M, uc, uq, lc, laplacian(M, F, i, j + 1), mc, mobility(M, uq, kap));
-  }
-  if (j > 0) {
-    const Dual up = F.at(i, j - 1);
-    acc = acc - face_flux(M, up, uc, laplacian(M, F, i, j - 1), lc, mobility(M, up, kap), mc);
-  }
+  if (i + 1 < M.nx) acc = acc + face_flux(M, uc, F.at(i + 1, j), lc, F.lap(i + 1, j), mc, F.mob(i + 1, j));
+  if (i > 0) acc = acc - face_flux(M, F.at(i - 1, j), uc, F.lap(i - 1, j), lc, F.mob(i - 1, j), mc);
+  if (j + 1 < M.ny) acc = acc + face_flux(M, uc, F.at(i, j + 1), lc, F.lap(i, j + 1), mc, F.mob(i, j + 1));
+  if (j > 0) acc = acc - face_flux(M, F.at(i, j - 1), uc, F.lap(i, j - 1), lc, F.mob(i, j - 1), mc);
   return M.inv_ds * acc;
 }
 
@@ -139,7 +166,7 @@ __device__ __forceinline__ double dlap_line(int c, int col, int n) {
 // over columns p-1..p+2, and -+fbar1/ds on p, q; row p gets +theta dt dF/ds,
 // row q -theta dt dF/ds.
 template <int DIR>
-__device__ void row_band(const AdjK& M, const Film& F, int i, int j, Dual kap, Dual (&band)[5]) {
+__device__ void row_band(const AdjK& M, const Film& F, int i, int j, Dual (&band)[5]) {
   const int n = DIR == 0 ? M.nx : M.ny, t = DIR == 0 ? i : j;
   for (int d = 0; d < 5; ++d) band[d] = mk(d == 2 ? 1.0 : 0.0);
   auto cell = [&](int s, int& ci, int& cj) {
@@ -153,8 +180,8 @@ __device__ void row_band(const AdjK& M, const Film& F, int i, int j, Dual kap, D
     cell(p, pi, pj);
     cell(q, qi, qj);
     const Dual up = F.at(pi, pj), uq = F.at(qi, qj);
-    const Dual lp = laplacian(M, F, pi, pj), lq = laplacian(M, F, qi, qj);
-    const Mob mp = mobility(M, up, kap), mq = mobility(M, uq, kap);
+    const Dual lp = F.lap(pi, pj), lq = F.lap(qi, qj);
+    const Mob mp = F.mob(pi, pj), mq = F.mob(qi, qj);
     const Dual fb0 = 0.5 * (mp.f0 + mq.f0), fb1 = 0.5 * (mp.f1 + mq.f1);
     const Dual gL = M.inv_ds * (lq - lp), gU = M.inv_ds * (uq - up);
     const double sgn = side == 0 ? -1.0 : 1.0;  // row t is q (side 0) or p (side 1)
@@ -173,9 +200,9 @@ __device__ void row_band(const AdjK& M, const Film& F, int i, int j, Dual kap, D
 
 // (A(u) w) at cell (i, j) along direction DIR.
 template <int DIR>
-__device__ Dual row_times(const AdjK& M, const Film& F, const double* __restrict__ w, int i, int j, Dual kap) {
+__device__ Dual row_times(const AdjK& M, const Film& F, const double* __restrict__ w, int i, int j) {
   Dual band[5];
-  row_band<DIR>(M, F, i, j, kap, band);
+  row_band<DIR>(M, F, i, j, band);
   const int n = DIR == 0 ? M.nx : M.ny, t = DIR == 0 ? i : j;
   Dual acc = mk(0.0);
   for (int d = 0; d < 5; ++d) {
@@ -187,13 +214,18 @@ __device__ Dual row_times(const AdjK& M, const Film& F, const double* __restrict
   return acc;
 }
 
+__device__ __forceinline__ Film make_film(const AdjK& M, const double* u, const Tables& T, int pi, int pj,
+                                          bool kseed) {
+  return Film{u, T, M.nx, M.ny, pi, pj, kseed, M.model == TF_MODEL_LINEAR ? 0.0 : 1.0 / M.kappa,
+              M.inv_ds * M.inv_ds};
+}
+
 // ubar_j += scale * sum_{c: |c - j|_1 <= 2} lambda_c dD_c/du_j
-__global__ void k_adj_D(AdjK M, const double* __restrict__ u, const double* __restrict__ lam, double scale,
-                        double* __restrict__ ubar) {
+__global__ void k_adj_D(AdjK M, const double* __restrict__ u, Tables T, const double* __restrict__ lam,
+                        double scale, double* __restrict__ ubar) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= M.nx) return;
-  const Film F{u, M.nx, i, j};
-  const Dual kap = mk(M.kappa);
+  const Film F = make_film(M, u, T, i, j, false);
   double acc = 0.0;
   for (int dy = -2; dy <= 2; ++dy) {
     const int cj = j + dy;
@@ -202,7 +234,7 @@ __global__ void k_adj_D(AdjK M, const double* __restrict__ u, const double* __re
     for (int dx = -r; dx <= r; ++dx) {
       const int ci = i + dx;
       if (ci < 0 || ci >= M.nx) continue;
-      acc += lam[(size_t)cj * M.nx + ci] * D_cell(M, F, ci, cj, kap).d;
+      acc += lam[(size_t)cj * M.nx + ci] * D_cell(M, F, ci, cj).d;
     }
   }
   ubar[(size_t)j * M.nx + i] += scale * acc;
@@ -211,12 +243,11 @@ __global__ void k_adj_D(AdjK M, const double* __restrict__ u, const double* __re
 // ubar_j += scale * sum_{c in box(j)} lambda_c d(A(u) w)_c/du_j, box |dx| <= 2,
 // |dy| <= 1 along x (transposed along y).
 template <int DIR>
-__global__ void k_adj_line(AdjK M, const double* __restrict__ u, const double* __restrict__ w,
+__global__ void k_adj_line(AdjK M, const double* __restrict__ u, Tables T, const double* __restrict__ w,
                            const double* __restrict__ lam, double scale, double* __restrict__ ubar) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= M.nx) return;
-  const Film F{u, M.nx, i, j};
-  const Dual kap = mk(M.kappa);
+  const Film F = make_film(M, u, T, i, j, false);
   const int rx = DIR == 0 ? 2 : 1, ry = DIR == 0 ? 1 : 2;
   double acc = 0.0;
   for (int dy = -ry; dy <= ry; ++dy) {
@@ -225,7 +256,7 @@ __global__ void k_adj_line(AdjK M, const double* __restrict__ u, const double* _
     for (int dx = -rx; dx <= rx; ++dx) {
       const int ci = i + dx;
       if (ci < 0 || ci >= M.nx) continue;
-      acc += lam[(size_t)cj * M.nx + ci] * row_times<DIR>(M, F, w, ci, cj, kap).d;
+      acc += lam[(size_t)cj * M.nx + ci] * row_times<DIR>(M, F, w, ci, cj).d;
     }
   }
   ubar[(size_t)j * M.nx + i] += scale * acc;
@@ -236,7 +267,7 @@ __global__ void k_adj_line(AdjK M, const double* __restrict__ u, const double* _
 // by a fixed tree.
 constexpr int kKapThreads = 256;
 __global__ void __launch_bounds__(kKapThreads) k_adj_kappa(AdjK M, int kind, const double* __restrict__ u,
-                                                            const double* __restrict__ w,
+                                                            Tables T, const double* __restrict__ w,
                                                             const double* __restrict__ lam,
                                                             double* __restrict__ part) {
   __shared__ double s[kKapThreads];
@@ -245,10 +276,9 @@ __global__ void __launch_bounds__(kKapThreads) k_adj_kappa(AdjK M, int kind, con
   double v = 0.0;
   if (c < N) {
     const int i = (int)(c % M.nx), j = (int)(c / M.nx);
-    const Film F{u, M.nx, -1, -1};
-    const Dual kap = mk(M.kappa, 1.0);
-    const Dual val = kind == 0 ? D_cell(M, F, i, j, kap)
-                               : (kind == 1 ? row_times<0>(M, F, w, i, j, kap) : row_times<1>(M, F, w, i, j, kap));
+    const Film F = make_film(M, u, T, -1, -1, true);
+    const Dual val = kind == 0 ? D_cell(M, F, i, j)
+                               : (kind == 1 ? row_times<0>(M, F, w, i, j) : row_times<1>(M, F, w, i, j));
     v = lam[c] * val.d;
   }
   s[threadIdx.x] = v;
@@ -262,12 +292,12 @@ __global__ void __launch_bounds__(kKapThreads) k_adj_kappa(AdjK M, int kind, con
 
 // Band of A along DIR at every cell: band[d * N + c] (values only).
 template <int DIR>
-__global__ void k_band(AdjK M, const double* __restrict__ u, double* __restrict__ band) {
+__global__ void k_band(AdjK M, const double* __restrict__ u, Tables T, double* __restrict__ band) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= M.nx) return;
-  const Film F{u, M.nx, -1, -1};
+  const Film F = make_film(M, u, T, -1, -1, false);
   Dual b[5];
-  row_band<DIR>(M, F, i, j, mk(M.kappa), b);
+  row_band<DIR>(M, F, i, j, b);
   const size_t N = (size_t)M.nx * M.ny, c = (size_t)j * M.nx + i;
   for (int d = 0; d < 5; ++d) band[d * N + c] = b[d].v;
 }
@@ -413,7 +443,7 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
   const int kb = (int)((N + kKapThreads - 1) / kKapThreads);
   // workspace: u_1..u_K, w_0..w_{K-1}, v_0..v_{K-1}, band (5), lam_y, lam_x,
   // bbar, scratch (4), kappa partials
-  const size_t grids = (size_t)3 * K + 5 + 3 + 4;
+  const size_t grids = (size_t)3 * K + 5 + 3 + 4 + 7;
   const size_t bytes = grids * N * sizeof(double) + (size_t)kb * sizeof(double) * 8;
   if (c->adj_bytes < bytes) {
     if (c->adj_ws) cudaFree(c->adj_ws);
@@ -439,6 +469,15 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
   off += N;
   double* scratch = base + off;
   off += 4 * N;
+  Tables Tb;
+  Tb.f0 = base + off;
+  Tb.f1 = Tb.f0 + N;
+  Tb.d0 = Tb.f1 + N;
+  Tb.d1 = Tb.d0 + N;
+  Tb.e0 = Tb.d1 + N;
+  Tb.e1 = Tb.e0 + N;
+  Tb.lap = Tb.e1 + N;
+  off += 7 * N;
   double* part = base + off;  // 8 kinds of partials, kb each
 
   GroupTimer T;
@@ -478,7 +517,7 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
   // kappa terms are summed on the host after each launch (fixed order)
   auto kappa_term = [&](int kind, const double* u, const double* w, const double* lam, double scale) -> int {
     const int tk = T.begin(kGKappa);
-    k_adj_kappa<<<kb, kKapThreads, 0, st>>>(M, kind, u, w, lam, part);
+    k_adj_kappa<<<kb, kKapThreads, 0, st>>>(M, kind, u, Tb, w, lam, part);
     T.end(tk);
     if (cudaMemcpyAsync(hp.data(), part, kb * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -497,31 +536,32 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
     const double* uk = U[k];
     // v_k = A_y(u_k)^-1 w_k
     int t = T.begin(kGBand);
-    k_band<1><<<g2, b2, 0, st>>>(M, uk, band);
+    k_tables<<<g2, b2, 0, st>>>(M, uk, Tb);
+    k_band<1><<<g2, b2, 0, st>>>(M, uk, Tb, band);
     T.end(t);
     t = T.begin(kGSolve);
     k_solve_t<1><<<nl_y, 128, 0, st>>>(nx, ny, band, g_h, lam_y, scratch);
     T.end(t);
     t = T.begin(kGLineY);
-    k_adj_line<1><<<g2, b2, 0, st>>>(M, uk, V[k], lam_y, -1.0, g_h);
+    k_adj_line<1><<<g2, b2, 0, st>>>(M, uk, Tb, V[k], lam_y, -1.0, g_h);
     T.end(t);
     if (kappa_on && kappa_term(2, uk, V[k], lam_y, -1.0)) return TF_ERR_CUDA;
     // w_k = A_x(u_k)^-1 (-G(u_k))
     t = T.begin(kGBand);
-    k_band<0><<<g2, b2, 0, st>>>(M, uk, band);
+    k_band<0><<<g2, b2, 0, st>>>(M, uk, Tb, band);
     T.end(t);
     t = T.begin(kGSolve);
     k_solve_t<0><<<nl_x, 128, 0, st>>>(nx, ny, band, lam_y, lam_x, scratch);
     T.end(t);
     t = T.begin(kGLineX);
-    k_adj_line<0><<<g2, b2, 0, st>>>(M, uk, W[k], lam_x, -1.0, g_h);
+    k_adj_line<0><<<g2, b2, 0, st>>>(M, uk, Tb, W[k], lam_x, -1.0, g_h);
     T.end(t);
     if (kappa_on && kappa_term(1, uk, W[k], lam_x, -1.0)) return TF_ERR_CUDA;
     // -G(u_k) = -u_k - theta dt D(u_k) + b
     k_axpy<<<nb, 256, 0, st>>>(N, -1.0, lam_x, g_h);
     k_axpy<<<nb, 256, 0, st>>>(N, 1.0, lam_x, bbar);
     t = T.begin(kGD);
-    k_adj_D<<<g2, b2, 0, st>>>(M, uk, lam_x, -M.tdt, g_h);
+    k_adj_D<<<g2, b2, 0, st>>>(M, uk, Tb, lam_x, -M.tdt, g_h);
     T.end(t);
     if (kappa_on && kappa_term(0, uk, nullptr, lam_x, -M.tdt)) return TF_ERR_CUDA;
   }
@@ -530,7 +570,7 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
   k_axpy<<<nb, 256, 0, st>>>(N, 1.0, bbar, g_h);
   {
     const int t = T.begin(kGD);
-    k_adj_D<<<g2, b2, 0, st>>>(M, h_old, bbar, -ex, g_h);
+    k_adj_D<<<g2, b2, 0, st>>>(M, h_old, Tb, bbar, -ex, g_h);  // tables of u_0 = h_old
     T.end(t);
   }
   if (kappa_on && kappa_term(0, h_old, nullptr, bbar, -ex)) return TF_ERR_CUDA;

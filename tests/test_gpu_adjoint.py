@@ -118,3 +118,15 @@ def test_adjoint_workload_against_central_differences(torch):
     tf.tf_newton_adi_step(ctx_m, u, out_m, dt)
     fdk = float(torch.sum(g * (out_p - out_m))) / (2 * hk)
     assert abs(fdk - r["g_kappa"]) <= 1e-6 * abs(r["g_kappa"])
+
+
+def test_unrolled_step_is_differentiable_in_torch(torch):
+    # torch.autograd.gradcheck: the backward (tf_adjoint_step) against the
+    # forward's finite differences, every input direction of a small film
+    M, p, dt = setup(6, 5)
+    ctx = tf.Context(p)
+    h = dev(torch, S.spinodal_film(6, 5, 1.0, 0.05, seed=12)).requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda x: tf.unrolled_step(x, ctx, dt, 3), (h,), eps=1e-6, atol=1e-8,
+                                     rtol=1e-6)
+    out = tf.unrolled_step(h, ctx, dt, 3)
+    assert np.max(np.abs(out.detach().cpu().numpy() - AD.step_fixed(M, h.detach().cpu().numpy(), dt, 3))) <= 1e-13
