@@ -323,61 +323,91 @@ __global__ void k_solve_t(int nx, int ny, const double* __restrict__ band, const
     up1 = B(t + 1, 1);
     up2 = B(t + 2, 0);
   };
-  double* sd = scratch;          // eliminated diagonal
+  double* sd = scratch;          // reciprocal of the eliminated diagonal
   double* s1 = scratch + N;      // eliminated first super-diagonal
   double* s2 = scratch + 2 * N;  // second super-diagonal
   double* sy = scratch + 3 * N;  // eliminated right side
-  // window: rows k (a*), k+1 (b*), k+2 (c*)
+  // window: rows k (a*), k+1 (b*), k+2 (c*); rows k+2..k+5 are loaded four
+  // steps ahead into a ring (slot = row mod 4) so that the loads overlap the
+  // elimination chain
   double a_lo2, a_lo1, a_dg, a_u1, a_u2, a_y;
   double b_lo2 = 0.0, b_lo1 = 0.0, b_dg = 1.0, b_u1 = 0.0, b_u2 = 0.0, b_y = 0.0;
   double c_lo2 = 0.0, c_lo1 = 0.0, c_dg = 1.0, c_u1 = 0.0, c_u2 = 0.0, c_y = 0.0;
+  double p_lo2[4], p_lo1[4], p_dg[4], p_u1[4], p_u2[4], p_y[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p_lo2[q] = p_lo1[q] = p_u1[q] = p_u2[q] = p_y[q] = 0.0;
+    p_dg[q] = 1.0;
+  }
   trow(0, a_lo2, a_lo1, a_dg, a_u1, a_u2);
   a_y = r[idx(0)];
   if (n > 1) {
     trow(1, b_lo2, b_lo1, b_dg, b_u1, b_u2);
     b_y = r[idx(1)];
   }
-  for (int k = 0; k < n; ++k) {
-    if (k + 2 < n) {
-      trow(k + 2, c_lo2, c_lo1, c_dg, c_u1, c_u2);
-      c_y = r[idx(k + 2)];
+#pragma unroll
+  for (int q = 2; q < 6; ++q) {
+    if (q < n) {
+      trow(q, p_lo2[q & 3], p_lo1[q & 3], p_dg[q & 3], p_u1[q & 3], p_u2[q & 3]);
+      p_y[q & 3] = r[idx(q)];
     }
-    const double inv = 1.0 / a_dg;
-    if (k + 1 < n) {
-      const double l = b_lo1 * inv;
-      b_dg -= l * a_u1;
-      b_u1 -= l * a_u2;
-      b_y -= l * a_y;
+  }
+  for (int k0 = 0; k0 < n; k0 += 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + q, sl = (q + 2) & 3;  // ring slot of row k + 2
+      if (k < n) {
+        if (k + 2 < n) {
+          c_lo2 = p_lo2[sl];
+          c_lo1 = p_lo1[sl];
+          c_dg = p_dg[sl];
+          c_u1 = p_u1[sl];
+          c_u2 = p_u2[sl];
+          c_y = p_y[sl];
+        }
+        if (k + 6 < n) {
+          trow(k + 6, p_lo2[sl], p_lo1[sl], p_dg[sl], p_u1[sl], p_u2[sl]);
+          p_y[sl] = r[idx(k + 6)];
+        }
+        const double inv = 1.0 / a_dg;
+        if (k + 1 < n) {
+          const double l = b_lo1 * inv;
+          b_dg -= l * a_u1;
+          b_u1 -= l * a_u2;
+          b_y -= l * a_y;
+        }
+        if (k + 2 < n) {
+          const double l = c_lo2 * inv;
+          c_lo1 -= l * a_u1;
+          c_dg -= l * a_u2;
+          c_y -= l * a_y;
+        }
+        const size_t ck = idx(k);
+        sd[ck] = inv;
+        s1[ck] = a_u1;
+        s2[ck] = a_u2;
+        sy[ck] = a_y;
+        // shift the window
+        a_lo2 = b_lo2;
+        a_lo1 = b_lo1;
+        a_dg = b_dg;
+        a_u1 = b_u1;
+        a_u2 = b_u2;
+        a_y = b_y;
+        b_lo2 = c_lo2;
+        b_lo1 = c_lo1;
+        b_dg = c_dg;
+        b_u1 = c_u1;
+        b_u2 = c_u2;
+        b_y = c_y;
+      }
     }
-    if (k + 2 < n) {
-      const double l = c_lo2 * inv;
-      c_lo1 -= l * a_u1;
-      c_dg -= l * a_u2;
-      c_y -= l * a_y;
-    }
-    const size_t ck = idx(k);
-    sd[ck] = a_dg;
-    s1[ck] = a_u1;
-    s2[ck] = a_u2;
-    sy[ck] = a_y;
-    // shift the window
-    a_lo2 = b_lo2;
-    a_lo1 = b_lo1;
-    a_dg = b_dg;
-    a_u1 = b_u1;
-    a_u2 = b_u2;
-    a_y = b_y;
-    b_lo2 = c_lo2;
-    b_lo1 = c_lo1;
-    b_dg = c_dg;
-    b_u1 = c_u1;
-    b_u2 = c_u2;
-    b_y = c_y;
   }
   double x1 = 0.0, x2 = 0.0;  // x_{k+1}, x_{k+2}
+#pragma unroll 4
   for (int k = n - 1; k >= 0; --k) {
     const size_t ck = idx(k);
-    const double xv = (sy[ck] - s1[ck] * x1 - s2[ck] * x2) / sd[ck];
+    const double xv = (sy[ck] - s1[ck] * x1 - s2[ck] * x2) * sd[ck];
     x[ck] = xv;
     x2 = x1;
     x1 = xv;
@@ -510,7 +540,8 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
   M.tdt = theta * dt;
 
   const dim3 g2((nx + 127) / 128, ny), b2(128);
-  const int nl_x = (ny + 127) / 128, nl_y = (nx + 127) / 128;
+  // one thread per line, 32 per block so that the lines spread over many SMs
+  const int nl_x = (ny + 31) / 32, nl_y = (nx + 31) / 32;
   const int nb = (int)((N + 255) / 256);
   std::vector<double> hp((size_t)kb);
   double kbar = 0.0;
@@ -540,7 +571,7 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
     k_band<1><<<g2, b2, 0, st>>>(M, uk, Tb, band);
     T.end(t);
     t = T.begin(kGSolve);
-    k_solve_t<1><<<nl_y, 128, 0, st>>>(nx, ny, band, g_h, lam_y, scratch);
+    k_solve_t<1><<<nl_y, 32, 0, st>>>(nx, ny, band, g_h, lam_y, scratch);
     T.end(t);
     t = T.begin(kGLineY);
     k_adj_line<1><<<g2, b2, 0, st>>>(M, uk, Tb, V[k], lam_y, -1.0, g_h);
@@ -551,7 +582,7 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
     k_band<0><<<g2, b2, 0, st>>>(M, uk, Tb, band);
     T.end(t);
     t = T.begin(kGSolve);
-    k_solve_t<0><<<nl_x, 128, 0, st>>>(nx, ny, band, lam_y, lam_x, scratch);
+    k_solve_t<0><<<nl_x, 32, 0, st>>>(nx, ny, band, lam_y, lam_x, scratch);
     T.end(t);
     t = T.begin(kGLineX);
     k_adj_line<0><<<g2, b2, 0, st>>>(M, uk, Tb, W[k], lam_x, -1.0, g_h);
