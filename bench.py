@@ -599,11 +599,13 @@ def reference_spectrum(args, w):
 
 ADJOINT_METRIC = "adjoint film cell-steps/s (forward + reverse of the 3-iteration step) at 1024^2"
 
-# FP64 flops (2 per DFMA, 1 per DADD/DMUL) per cell of the dominant adjoint
-# kernels, from the ncu capture summarised in profiles/adjoint_kernels_adjoint1k.md
-# (the counts do not depend on the grid size).  None until captured for the
-# kernels as they are.
-ADJ_FLOPS_PER_CELL = {"line_x": 1940.2, "line_y": 1726.9, "D": 930.0}
+# Algorithmic bytes per cell of one launch of each adjoint kernel group:
+# the transposed solve reads the five band diagonals and the right side and
+# writes the solution (56 B); a line derivative reads u_k, w, lambda and
+# updates the cotangent (40 B); the D derivative the same without w (32 B).
+# The per-iterate tables, the elimination scratch and the Laplacian
+# cotangent pass are implementation traffic.
+ADJ_BYTES_PER_CELL = {"solve_t": 56.0, "line_x": 40.0, "line_y": 40.0, "D": 32.0}
 
 
 def adjoint_config(w, world):
@@ -675,27 +677,24 @@ def run_adjoint(args, w):
     torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3)
     per = {k: v / S_ for k, v in groups.items()}
-    launches = {"forward": None, "band": 2 * K, "solve_t": 2 * K, "line_x": K, "line_y": K, "D": K + 1,
-                "kappa": 3 * K + 1}
-    dom = max(("line_x", "line_y", "D"), key=lambda k: per[k])
-    n_l = launches[dom]
-    ms_launch = per[dom] / n_l
-    fpc = ADJ_FLOPS_PER_CELL.get(dom)
-    ach = None if fpc is None else fpc * N * N / (ms_launch * 1e-3) / 1e12
-    roof = dict(bound="alu", kernel=dom, unit="TFLOP/s", peak=FP64_TFLOPS,
-                peak_source="measured FP64 FMA throughput probe", ms_per_launch=round(ms_launch, 3),
-                achieved=None if ach is None else round(ach, 4),
-                frac=None if ach is None else round(ach / FP64_TFLOPS, 4),
-                flops_per_cell=fpc, traffic=None)
+    launches = {"solve_t": 2 * K, "line_x": K, "line_y": K, "D": K + 1}
+    dom = max(launches, key=lambda k: per[k])
+    ms_launch = per[dom] / launches[dom]
+    pk = peaks()
+    ach = ADJ_BYTES_PER_CELL[dom] * N * N / (ms_launch * 1e-3) / 1e9
+    roof = dict(bound="hbm", kernel=dom, unit="GB/s", peak=pk["hbm_gbs"], peak_source=pk["source"],
+                ms_per_launch=round(ms_launch, 4), achieved=round(ach, 1), frac=round(ach / pk["hbm_gbs"], 4),
+                algorithmic_bytes_per_launch=int(ADJ_BYTES_PER_CELL[dom] * N * N), traffic=None)
     line = dict(
         metric=ADJOINT_METRIC, value=value, unit="cell-steps/s", n_gpus=world, steps=S_, warmup=args.warmup,
         ms_per_step=ms / S_, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
         data="synthetic", config=adjoint_config(w, world), g_kappa=r["g_kappa"],
         group_ms_per_step={k: round(v, 3) for k, v in per.items()}, roofline=roof,
         # per step: forward 6 per iteration (explicit part, residual, x and y
-        # sweeps, finalize, film statistics); reverse 2K band, 2K solve, 2K
-        # line, K+1 D, 3K+1 kappa and 2K+1 axpy kernels
-        gpu_launches=S_ * (18 * K + 3),
+        # sweeps, finalize, film statistics); reverse per iteration 1 tables,
+        # 2 band, 2 solve, 2 line and 1 D derivative, 3 Laplacian-transpose
+        # and 2 axpy kernels, then 1 axpy, 1 D derivative, 1 Laplacian-transpose
+        gpu_launches=S_ * (19 * K + 3),
         e2e=dict(value=job_rate(dist, N * N * S_, ms_e2e), unit="cell-steps/s",
                  h2d_bytes_per_step=2 * N * N * 8, d2h_bytes_per_step=N * N * 8),
     )

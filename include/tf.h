@@ -273,7 +273,7 @@ int tf_residual_noalloc(const tf_params* p, void* stream, const double* h_k,
  * g_h = (du^K/du^n)^T g and g_kappa = (du^K/dkappa)^T g, through transposed
  * line solves (y lines, then x lines, each iteration in reverse order) and
  * the transposed derivatives of D and of the line operators' dependence on
- * u (forward-mode dual numbers, one gather per cell, no atomics).
+ * u (face-by-face partial derivatives, gathered per cell, no atomics).
  * The context must be TF_FP64 with the power-law or linear model.
  * h_old, g: device grids; h_new: device grid or NULL (receives u^K);
  * g_h: device output grid (not aliasing h_old, g or h_new); g_kappa,
@@ -286,9 +286,10 @@ int tf_adjoint_step(tf_ctx* ctx, const double* h_old, double dt, int K, const do
                     double* h_new, double* g_h, double* g_kappa, double* g_theta);
 
 /* Kernel time (ms, CUDA events) of the last tf_adjoint_step in this
- * process, by group: forward iterations, band assembly, transposed line
- * solves, x-line coefficient derivatives, y-line coefficient derivatives,
- * D derivatives, kappa terms.  n: entries wanted (up to 7).              */
+ * process, by group: forward iterations, per-iterate tables and band
+ * assembly, transposed line solves, x-line coefficient derivatives, y-line
+ * coefficient derivatives, D derivatives, the copy of the kappa partial
+ * sums.  n: entries wanted (up to 7).                                     */
 int tf_adjoint_timing(double* ms, int n);
 
 /* ---- radial Fourier analysis of a film (App. Radial Fourier Transform) ---

@@ -14,16 +14,16 @@
 // and finally ubar += bbar - (1-theta) dt D'(u^n)^T bbar; the kappa
 // cotangent collects the same terms' kappa derivatives.
 //
-// Derivatives: forward-mode dual numbers over per-iterate tables (the
+// Derivatives: hand-derived face by face from per-iterate tables (the
 // mobilities with two derivatives and the Laplacian, formed once per
-// iterate), so a seeded evaluation only propagates the seeded cell's known
-// partials.  The value of D at a cell depends
-// on u within the 13-cell diamond |dx| + |dy| <= 2 around it, and a row of
-// A_x(u) w on u within the box |dx| <= 2, |dy| <= 1 (A_y: transposed).  So
-// the transposed product at cell j is a gather over the cells c whose
-// dependence set holds j: one thread per j evaluates each such F_c with u_j
-// seeded and sums lambda_c dF_c/du_j.  No atomics; every sum runs in a fixed
-// order.  FP64 throughout; the power-law and linear models.
+// iterate); see the comment above k_vjp_D.  Every face term depends on u
+// directly at its two cells and through the Laplacian at those cells, so
+// each transposed product is two gathers: one thread per cell over the
+// faces that touch it, then the transposed five-point Laplacian of the
+// collected Laplacian cotangents.  No atomics; every sum runs in a fixed
+// order.  FP64 throughout; the power-law and linear models.  The band
+// values for the transposed solves come from the row formula (row_band,
+// evaluated with no seeded cell).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
@@ -131,24 +131,6 @@ struct Film {
   }
 };
 
-// Flux through the face from cell p to its +x or +y neighbour q:
-// F = fbar0 (L_q - L_p)/ds + fbar1 (u_q - u_p)/ds, fbar the two cells' mean.
-__device__ Dual face_flux(const AdjK& M, Dual up, Dual uq, Dual lp, Dual lq, const Mob& mp, const Mob& mq) {
-  return (0.5 * M.inv_ds) * ((mp.f0 + mq.f0) * (lq - lp) + (mp.f1 + mq.f1) * (uq - up));
-}
-
-// D at cell (i, j) (eq. GovEqnCell2, zero wall fluxes).
-__device__ Dual D_cell(const AdjK& M, const Film& F, int i, int j) {
-  const Dual uc = F.at(i, j), lc = F.lap(i, j);
-  const Mob mc = F.mob(i, j);
-  Dual acc = mk(0.0);
-  if (i + 1 < M.nx) acc = acc + face_flux(M, uc, F.at(i + 1, j), lc, F.lap(i + 1, j), mc, F.mob(i + 1, j));
-  if (i > 0) acc = acc - face_flux(M, F.at(i - 1, j), uc, F.lap(i - 1, j), lc, F.mob(i - 1, j), mc);
-  if (j + 1 < M.ny) acc = acc + face_flux(M, uc, F.at(i, j + 1), lc, F.lap(i, j + 1), mc, F.mob(i, j + 1));
-  if (j > 0) acc = acc - face_flux(M, F.at(i, j - 1), uc, F.lap(i, j - 1), lc, F.mob(i, j - 1), mc);
-  return M.inv_ds * acc;
-}
-
 // d(along-line second difference at line cell c)/d(u at line cell col),
 // reflection at the ends of a line of n cells, times ds^2.
 __device__ __forceinline__ double dlap_line(int c, int col, int n) {
@@ -198,96 +180,179 @@ __device__ void row_band(const AdjK& M, const Film& F, int i, int j, Dual (&band
   }
 }
 
-// (A(u) w) at cell (i, j) along direction DIR.
-template <int DIR>
-__device__ Dual row_times(const AdjK& M, const Film& F, const double* __restrict__ w, int i, int j) {
-  Dual band[5];
-  row_band<DIR>(M, F, i, j, band);
-  const int n = DIR == 0 ? M.nx : M.ny, t = DIR == 0 ? i : j;
-  Dual acc = mk(0.0);
-  for (int d = 0; d < 5; ++d) {
-    const int s = t + d - 2;
-    if (s < 0 || s >= n) continue;
-    const double ws = DIR == 0 ? w[(size_t)j * M.nx + s] : w[(size_t)s * M.nx + i];
-    acc = acc + ws * band[d];
-  }
-  return acc;
-}
-
 __device__ __forceinline__ Film make_film(const AdjK& M, const double* u, const Tables& T, int pi, int pj,
                                           bool kseed) {
   return Film{u, T, M.nx, M.ny, pi, pj, kseed, M.model == TF_MODEL_LINEAR ? 0.0 : 1.0 / M.kappa,
               M.inv_ds * M.inv_ds};
 }
 
-// ubar_j += scale * sum_{c: |c - j|_1 <= 2} lambda_c dD_c/du_j
-__global__ void k_adj_D(AdjK M, const double* __restrict__ u, Tables T, const double* __restrict__ lam,
-                        double scale, double* __restrict__ ubar) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  if (i >= M.nx) return;
-  const Film F = make_film(M, u, T, i, j, false);
-  double acc = 0.0;
-  for (int dy = -2; dy <= 2; ++dy) {
-    const int cj = j + dy;
-    if (cj < 0 || cj >= M.ny) continue;
-    const int r = 2 - (dy < 0 ? -dy : dy);
-    for (int dx = -r; dx <= r; ++dx) {
-      const int ci = i + dx;
-      if (ci < 0 || ci >= M.nx) continue;
-      acc += lam[(size_t)cj * M.nx + ci] * D_cell(M, F, ci, cj).d;
-    }
-  }
-  ubar[(size_t)j * M.nx + i] += scale * acc;
+// ---- transposed derivative products, hand-derived (two passes) ----------
+// Face between cells p and q (q the +x or +y neighbour), values from the
+// tables: fb0 = (f0_p + f0_q)/2, fb1 = (f1_p + f1_q)/2, gL = (L_q - L_p)/ds,
+// gU = (u_q - u_p)/ds.
+//
+// D: the face flux F = fb0 gL + fb1 gU enters D_p with +1/ds and D_q with
+// -1/ds, so its cotangent weight is mu = (lambda_p - lambda_q)/ds and
+//   dF/du_p = f0'_p gL/2 + f1'_p gU/2 - fb1/ds,  dF/du_q = f0'_q gL/2 + f1'_q gU/2 + fb1/ds,
+//   dF/dL_q = -dF/dL_p = fb0/ds,                 dF/dkappa = fb1 gU / kappa.
+//
+// A line row (I + theta dt J) w: the face's part of rows p (+) and q (-),
+// times theta dt/ds, is
+//   Phi = fb0 W3 + gL (f0'_p w_p + f0'_q w_q)/2 + gU (f1'_p w_p + f1'_q w_q)/2 + fb1 (w_q - w_p)/ds,
+// W3 = sum over columns p-1..p+2 of the along-line third difference of w
+// (a constant), so with mu = theta dt (lambda_p - lambda_q)/ds
+//   dPhi/du_p = f0'_p W3/2 + gL f0''_p w_p/2 + gU f1''_p w_p/2 + f1'_p (w_q - w_p)/(2 ds)
+//               - (f1'_p w_p + f1'_q w_q)/(2 ds),
+//   dPhi/du_q = f0'_q W3/2 + gL f0''_q w_q/2 + gU f1''_q w_q/2 + f1'_q (w_q - w_p)/(2 ds)
+//               + (f1'_p w_p + f1'_q w_q)/(2 ds),
+//   dPhi/dL_q = -dPhi/dL_p = (f0'_p w_p + f0'_q w_q)/(2 ds),
+//   dPhi/dkappa = [gU (f1'_p w_p + f1'_q w_q)/2 + fb1 (w_q - w_p)/ds] / kappa.
+//
+// Pass 1 (one thread per cell j, over the faces that touch j): the direct
+// u_j terms go to ubar_j, the L_j terms to Lbar_j, and the kappa terms of
+// the faces whose p is j to a per-block sum.  Pass 2: ubar_j += the
+// transposed five-point Laplacian of Lbar (symmetric, with reflection).
+
+struct FaceVals {
+  double up, uq, f0p, f0q, f1p, f1q, d0p, d0q, d1p, d1q, e0p, e0q, e1p, e1q, gL, gU;
+};
+
+__device__ __forceinline__ FaceVals face_vals(const AdjK& M, const double* __restrict__ u, const Tables& T,
+                                              size_t p, size_t q) {
+  FaceVals v;
+  v.up = u[p];
+  v.uq = u[q];
+  v.f0p = T.f0[p];
+  v.f0q = T.f0[q];
+  v.f1p = T.f1[p];
+  v.f1q = T.f1[q];
+  v.d0p = T.d0[p];
+  v.d0q = T.d0[q];
+  v.d1p = T.d1[p];
+  v.d1q = T.d1[q];
+  v.e0p = T.e0[p];
+  v.e0q = T.e0[q];
+  v.e1p = T.e1[p];
+  v.e1q = T.e1[q];
+  v.gL = (T.lap[q] - T.lap[p]) * M.inv_ds;
+  v.gU = (v.uq - v.up) * M.inv_ds;
+  return v;
 }
 
-// ubar_j += scale * sum_{c in box(j)} lambda_c d(A(u) w)_c/du_j, box |dx| <= 2,
-// |dy| <= 1 along x (transposed along y).
-template <int DIR>
-__global__ void k_adj_line(AdjK M, const double* __restrict__ u, Tables T, const double* __restrict__ w,
-                           const double* __restrict__ lam, double scale, double* __restrict__ ubar) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  if (i >= M.nx) return;
-  const Film F = make_film(M, u, T, i, j, false);
-  const int rx = DIR == 0 ? 2 : 1, ry = DIR == 0 ? 1 : 2;
-  double acc = 0.0;
-  for (int dy = -ry; dy <= ry; ++dy) {
-    const int cj = j + dy;
-    if (cj < 0 || cj >= M.ny) continue;
-    for (int dx = -rx; dx <= rx; ++dx) {
-      const int ci = i + dx;
-      if (ci < 0 || ci >= M.nx) continue;
-      acc += lam[(size_t)cj * M.nx + ci] * row_times<DIR>(M, F, w, ci, cj).d;
-    }
-  }
-  ubar[(size_t)j * M.nx + i] += scale * acc;
-}
+constexpr int kVjpThreads = 128;
 
-// Per-block partial sums of lambda_c dF_c/dkappa for F = D (kind 0), A_x w
-// (kind 1) or A_y w (kind 2): blocks of 256 cells in row-major order, summed
-// by a fixed tree.
-constexpr int kKapThreads = 256;
-__global__ void __launch_bounds__(kKapThreads) k_adj_kappa(AdjK M, int kind, const double* __restrict__ u,
-                                                            Tables T, const double* __restrict__ w,
-                                                            const double* __restrict__ lam,
-                                                            double* __restrict__ part) {
-  __shared__ double s[kKapThreads];
-  const size_t N = (size_t)M.nx * M.ny;
-  const size_t c = (size_t)blockIdx.x * kKapThreads + threadIdx.x;
-  double v = 0.0;
-  if (c < N) {
-    const int i = (int)(c % M.nx), j = (int)(c / M.nx);
-    const Film F = make_film(M, u, T, -1, -1, true);
-    const Dual val = kind == 0 ? D_cell(M, F, i, j)
-                               : (kind == 1 ? row_times<0>(M, F, w, i, j) : row_times<1>(M, F, w, i, j));
-    v = lam[c] * val.d;
-  }
+__device__ __forceinline__ void block_sum_to(double v, double* __restrict__ part) {
+  __shared__ double s[kVjpThreads];
   s[threadIdx.x] = v;
   __syncthreads();
-  for (int h = kKapThreads / 2; h > 0; h >>= 1) {
+  for (int h = kVjpThreads / 2; h > 0; h >>= 1) {
     if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s[0];
+}
+
+// D: ubar_j += scale (D'^T lambda)_j (direct part), Lbar_j = its L_j part,
+// part[block] = scale lambda^T dD/dkappa over the block's cells.
+__global__ void __launch_bounds__(kVjpThreads) k_vjp_D(AdjK M, const double* __restrict__ u, Tables T,
+                                                        const double* __restrict__ lam, double scale,
+                                                        double* __restrict__ ubar, double* __restrict__ Lbar,
+                                                        double* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  double du = 0.0, dL = 0.0, dk = 0.0;
+  if (i < M.nx) {
+    const size_t c = (size_t)j * M.nx + i;
+    const double inv_kappa = M.model == TF_MODEL_LINEAR ? 0.0 : 1.0 / M.kappa;
+    // faces (c-dir, c) with c as q and (c, c+dir) with c as p, dir = x, y
+    for (int dir = 0; dir < 2; ++dir) {
+      const bool has_lo = dir == 0 ? i > 0 : j > 0;
+      const bool has_hi = dir == 0 ? i + 1 < M.nx : j + 1 < M.ny;
+      const size_t step = dir == 0 ? 1 : (size_t)M.nx;
+      for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? !has_lo : !has_hi) continue;
+        const size_t p = side == 0 ? c - step : c, q = p + step;
+        const FaceVals v = face_vals(M, u, T, p, q);
+        const double fb0 = 0.5 * (v.f0p + v.f0q), fb1 = 0.5 * (v.f1p + v.f1q);
+        const double mu = scale * (lam[p] - lam[q]) * M.inv_ds;
+        if (side == 0) {  // c is q
+          du += mu * (0.5 * v.d0q * v.gL + 0.5 * v.d1q * v.gU + fb1 * M.inv_ds);
+          dL += mu * fb0 * M.inv_ds;
+        } else {  // c is p
+          du += mu * (0.5 * v.d0p * v.gL + 0.5 * v.d1p * v.gU - fb1 * M.inv_ds);
+          dL -= mu * fb0 * M.inv_ds;
+          dk += mu * fb1 * v.gU * inv_kappa;
+        }
+      }
+    }
+    ubar[c] += du;
+    Lbar[c] = dL;
+  }
+  block_sum_to(dk, part);
+}
+
+// A line row along DIR: ubar_j += scale ([d_u (A(u) w)]^T lambda)_j (direct
+// part), Lbar_j = its L_j part, part[block] = scale lambda^T d(A w)/dkappa.
+template <int DIR>
+__global__ void __launch_bounds__(kVjpThreads) k_vjp_line(AdjK M, const double* __restrict__ u, Tables T,
+                                                           const double* __restrict__ w,
+                                                           const double* __restrict__ lam, double scale,
+                                                           double* __restrict__ ubar, double* __restrict__ Lbar,
+                                                           double* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  double du = 0.0, dL = 0.0, dk = 0.0;
+  if (i < M.nx) {
+    const size_t c = (size_t)j * M.nx + i;
+    const int n = DIR == 0 ? M.nx : M.ny, t = DIR == 0 ? i : j;
+    const size_t step = DIR == 0 ? 1 : (size_t)M.nx;
+    const double inv_kappa = M.model == TF_MODEL_LINEAR ? 0.0 : 1.0 / M.kappa;
+    const double ids3 = M.inv_ds * M.inv_ds * M.inv_ds;
+    for (int side = 0; side < 2; ++side) {
+      const int pt = side == 0 ? t - 1 : t, qt = pt + 1;  // line indices of p, q
+      if (pt < 0 || qt >= n) continue;
+      const size_t p = c - (size_t)(t - pt) * step, q = p + step;
+      const FaceVals v = face_vals(M, u, T, p, q);
+      const double wp = w[p], wq = w[q];
+      // W3: the along-line third difference of w over columns p-1..p+2
+      double W3 = 0.0;
+      for (int a = 0; a < 4; ++a) {
+        const int col = pt - 1 + a;
+        if (col < 0 || col >= n) continue;
+        const double dl = (dlap_line(qt, col, n) - dlap_line(pt, col, n)) * ids3;
+        W3 += dl * w[(size_t)((long long)c + (long long)(col - t) * (long long)step)];
+      }
+      const double fb1 = 0.5 * (v.f1p + v.f1q);
+      const double s0 = v.d0p * wp + v.d0q * wq, s1 = v.d1p * wp + v.d1q * wq;
+      const double mu = scale * M.tdt * (lam[p] - lam[q]) * M.inv_ds;
+      if (side == 0) {  // c is q
+        du += mu * (0.5 * v.d0q * W3 + 0.5 * v.gL * v.e0q * wq + 0.5 * v.gU * v.e1q * wq +
+                    0.5 * v.d1q * (wq - wp) * M.inv_ds + 0.5 * s1 * M.inv_ds);
+        dL += mu * 0.5 * s0 * M.inv_ds;
+      } else {  // c is p
+        du += mu * (0.5 * v.d0p * W3 + 0.5 * v.gL * v.e0p * wp + 0.5 * v.gU * v.e1p * wp +
+                    0.5 * v.d1p * (wq - wp) * M.inv_ds - 0.5 * s1 * M.inv_ds);
+        dL -= mu * 0.5 * s0 * M.inv_ds;
+        dk += mu * (0.5 * v.gU * s1 + fb1 * (wq - wp) * M.inv_ds) * inv_kappa;
+      }
+    }
+    ubar[c] += du;
+    Lbar[c] = dL;
+  }
+  block_sum_to(dk, part);
+}
+
+// ubar_j += (sum over neighbours k of Lbar_k - (neighbours) Lbar_j) / ds^2:
+// the transpose of the five-point Laplacian with reflection.
+__global__ void k_lap_t(AdjK M, const double* __restrict__ Lbar, double* __restrict__ ubar) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= M.nx) return;
+  const size_t c = (size_t)j * M.nx + i;
+  const double lc = Lbar[c];
+  double s = 0.0;
+  if (i + 1 < M.nx) s += Lbar[c + 1] - lc;
+  if (i > 0) s += Lbar[c - 1] - lc;
+  if (j + 1 < M.ny) s += Lbar[c + M.nx] - lc;
+  if (j > 0) s += Lbar[c - M.nx] - lc;
+  ubar[c] += s * M.inv_ds * M.inv_ds;
 }
 
 // Band of A along DIR at every cell: band[d * N + c] (values only).
@@ -414,6 +479,8 @@ __global__ void k_solve_t(int nx, int ny, const double* __restrict__ band, const
   }
 }
 
+constexpr int kSolveLines = 4;
+
 __global__ void k_axpy(size_t N, double a, const double* __restrict__ x, double* __restrict__ y) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c < N) y[c] += a * x[c];
@@ -470,11 +537,12 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
   const int nx = c->p.nx, ny = c->p.ny;
   const size_t N = c->N;
   cudaStream_t st = c->stream;
-  const int kb = (int)((N + kKapThreads - 1) / kKapThreads);
+  // kappa partial sums: one per 128-cell block of a row, per derivative launch
+  const int npart = ((nx + kVjpThreads - 1) / kVjpThreads) * ny, nkl = 3 * K + 1;
   // workspace: u_1..u_K, w_0..w_{K-1}, v_0..v_{K-1}, band (5), lam_y, lam_x,
-  // bbar, scratch (4), kappa partials
+  // bbar, scratch (4; its first grid is also Lbar), tables (7), kappa partials
   const size_t grids = (size_t)3 * K + 5 + 3 + 4 + 7;
-  const size_t bytes = grids * N * sizeof(double) + (size_t)kb * sizeof(double) * 8;
+  const size_t bytes = grids * N * sizeof(double) + (size_t)npart * nkl * sizeof(double);
   if (c->adj_bytes < bytes) {
     if (c->adj_ws) cudaFree(c->adj_ws);
     c->adj_ws = nullptr;
@@ -508,7 +576,8 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
   Tb.e1 = Tb.e0 + N;
   Tb.lap = Tb.e1 + N;
   off += 7 * N;
-  double* part = base + off;  // 8 kinds of partials, kb each
+  double* part = base + off;  // nkl x npart kappa partials
+  double* Lbar = scratch;      // free once a transposed solve has finished
 
   GroupTimer T;
   T.st = st;
@@ -540,25 +609,13 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
   M.tdt = theta * dt;
 
   const dim3 g2((nx + 127) / 128, ny), b2(128);
-  // one thread per line, 32 per block so that the lines spread over many SMs
-  const int nl_x = (ny + 31) / 32, nl_y = (nx + 31) / 32;
+  const dim3 gv((nx + kVjpThreads - 1) / kVjpThreads, ny), bv(kVjpThreads);
+  // one thread per line, kSolveLines per block: the elimination is a chain of
+  // dependent FP64 operations, and a warp's FP64 instruction takes longer the
+  // more lanes it carries, so few lines per warp over many SMs run faster
+  const int nl_x = (ny + kSolveLines - 1) / kSolveLines, nl_y = (nx + kSolveLines - 1) / kSolveLines;
   const int nb = (int)((N + 255) / 256);
-  std::vector<double> hp((size_t)kb);
-  double kbar = 0.0;
-  // kappa terms are summed on the host after each launch (fixed order)
-  auto kappa_term = [&](int kind, const double* u, const double* w, const double* lam, double scale) -> int {
-    const int tk = T.begin(kGKappa);
-    k_adj_kappa<<<kb, kKapThreads, 0, st>>>(M, kind, u, Tb, w, lam, part);
-    T.end(tk);
-    if (cudaMemcpyAsync(hp.data(), part, kb * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return TF_ERR_CUDA;
-    double s = 0.0;
-    for (int q = 0; q < kb; ++q) s += hp[q];
-    kbar += scale * s;
-    return TF_OK;
-  };
-  const bool kappa_on = M.model == TF_MODEL_POWERLAW;
+  int kl = 0;  // derivative launches so far (each writes one row of partials)
 
   if (cudaMemcpyAsync(g_h, g, N * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(bbar, 0, N * sizeof(double), st) != cudaSuccess)
@@ -571,43 +628,53 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
     k_band<1><<<g2, b2, 0, st>>>(M, uk, Tb, band);
     T.end(t);
     t = T.begin(kGSolve);
-    k_solve_t<1><<<nl_y, 32, 0, st>>>(nx, ny, band, g_h, lam_y, scratch);
+    k_solve_t<1><<<nl_y, kSolveLines, 0, st>>>(nx, ny, band, g_h, lam_y, scratch);
     T.end(t);
     t = T.begin(kGLineY);
-    k_adj_line<1><<<g2, b2, 0, st>>>(M, uk, Tb, V[k], lam_y, -1.0, g_h);
+    k_vjp_line<1><<<gv, bv, 0, st>>>(M, uk, Tb, V[k], lam_y, -1.0, g_h, Lbar, part + (size_t)(kl++) * npart);
+    k_lap_t<<<g2, b2, 0, st>>>(M, Lbar, g_h);
     T.end(t);
-    if (kappa_on && kappa_term(2, uk, V[k], lam_y, -1.0)) return TF_ERR_CUDA;
     // w_k = A_x(u_k)^-1 (-G(u_k))
     t = T.begin(kGBand);
     k_band<0><<<g2, b2, 0, st>>>(M, uk, Tb, band);
     T.end(t);
     t = T.begin(kGSolve);
-    k_solve_t<0><<<nl_x, 32, 0, st>>>(nx, ny, band, lam_y, lam_x, scratch);
+    k_solve_t<0><<<nl_x, kSolveLines, 0, st>>>(nx, ny, band, lam_y, lam_x, scratch);
     T.end(t);
     t = T.begin(kGLineX);
-    k_adj_line<0><<<g2, b2, 0, st>>>(M, uk, Tb, W[k], lam_x, -1.0, g_h);
+    k_vjp_line<0><<<gv, bv, 0, st>>>(M, uk, Tb, W[k], lam_x, -1.0, g_h, Lbar, part + (size_t)(kl++) * npart);
+    k_lap_t<<<g2, b2, 0, st>>>(M, Lbar, g_h);
     T.end(t);
-    if (kappa_on && kappa_term(1, uk, W[k], lam_x, -1.0)) return TF_ERR_CUDA;
     // -G(u_k) = -u_k - theta dt D(u_k) + b
     k_axpy<<<nb, 256, 0, st>>>(N, -1.0, lam_x, g_h);
     k_axpy<<<nb, 256, 0, st>>>(N, 1.0, lam_x, bbar);
     t = T.begin(kGD);
-    k_adj_D<<<g2, b2, 0, st>>>(M, uk, Tb, lam_x, -M.tdt, g_h);
+    k_vjp_D<<<gv, bv, 0, st>>>(M, uk, Tb, lam_x, -M.tdt, g_h, Lbar, part + (size_t)(kl++) * npart);
+    k_lap_t<<<g2, b2, 0, st>>>(M, Lbar, g_h);
     T.end(t);
-    if (kappa_on && kappa_term(0, uk, nullptr, lam_x, -M.tdt)) return TF_ERR_CUDA;
   }
-  // b = u^n - (1-theta) dt D(u^n)
+  // b = u^n - (1-theta) dt D(u^n); the tables hold u_0 = h_old
   const double ex = (1.0 - theta) * dt;
   k_axpy<<<nb, 256, 0, st>>>(N, 1.0, bbar, g_h);
   {
     const int t = T.begin(kGD);
-    k_adj_D<<<g2, b2, 0, st>>>(M, h_old, Tb, bbar, -ex, g_h);  // tables of u_0 = h_old
+    k_vjp_D<<<gv, bv, 0, st>>>(M, h_old, Tb, bbar, -ex, g_h, Lbar, part + (size_t)(kl++) * npart);
+    k_lap_t<<<g2, b2, 0, st>>>(M, Lbar, g_h);
     T.end(t);
   }
-  if (kappa_on && kappa_term(0, h_old, nullptr, bbar, -ex)) return TF_ERR_CUDA;
+  // kappa: the partial sums added on the host in a fixed order
+  std::vector<double> hp((size_t)nkl * npart);
+  {
+    const int t = T.begin(kGKappa);
+    const cudaError_t e = cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    T.end(t);
+    if (e != cudaSuccess) return TF_ERR_CUDA;
+  }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return TF_ERR_CUDA;
   if (T.err != cudaSuccess) return TF_ERR_CUDA;
   T.collect(g_adj_ms);
+  double kbar = 0.0;
+  for (double v : hp) kbar += v;
   if (g_kappa) *g_kappa = kbar;
   if (g_theta) {
     // kappa = (1 - cos theta_c)/(b M) when derived from the contact angle
