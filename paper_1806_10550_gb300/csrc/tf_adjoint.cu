@@ -21,9 +21,7 @@
 // each transposed product is two gathers: one thread per cell over the
 // faces that touch it, then the transposed five-point Laplacian of the
 // collected Laplacian cotangents.  No atomics; every sum runs in a fixed
-// order.  FP64 throughout; the power-law and linear models.  The band
-// values for the transposed solves come from the row formula (row_band,
-// evaluated with no seeded cell).
+// order.  FP64 throughout; the power-law and linear models.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
@@ -34,15 +32,6 @@
 #include "tf_internal.h"
 
 namespace {
-
-struct Dual {
-  double v, d;
-};
-__device__ __forceinline__ Dual mk(double v, double d = 0.0) { return Dual{v, d}; }
-__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual{a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual{a.v - b.v, a.d - b.d}; }
-__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual{a.v * b.v, a.v * b.d + a.d * b.v}; }
-__device__ __forceinline__ Dual operator*(double s, Dual a) { return Dual{s * a.v, s * a.d}; }
 
 struct AdjK {
   int nx, ny, model, n, m;
@@ -92,45 +81,6 @@ __global__ void k_tables(AdjK M, const double* __restrict__ u, Tables T) {
   T.lap[c] = sl * M.inv_ds * M.inv_ds;
 }
 
-struct Mob {
-  Dual f0, f1, d0, d1;
-};
-
-// The film seen by one evaluation: values from the tables, derivatives
-// with respect to the one seeded quantity -- u at cell (pi, pj) (pi < 0:
-// none) or kappa (kseed; f1 and f1' are linear in kappa).
-struct Film {
-  const double* u;
-  Tables T;
-  int nx, ny, pi, pj;
-  bool kseed;
-  double inv_kappa, inv_ds2;
-  __device__ __forceinline__ bool seeded(int i, int j) const { return i == pi && j == pj; }
-  __device__ __forceinline__ Dual at(int i, int j) const {
-    return Dual{u[(size_t)j * nx + i], seeded(i, j) ? 1.0 : 0.0};
-  }
-  __device__ __forceinline__ Mob mob(int i, int j) const {
-    const size_t c = (size_t)j * nx + i;
-    const double f0 = T.f0[c], f1 = T.f1[c], d0 = T.d0[c], d1 = T.d1[c];
-    if (kseed) return Mob{mk(f0), mk(f1, f1 * inv_kappa), mk(d0), mk(d1, d1 * inv_kappa)};
-    if (!seeded(i, j)) return Mob{mk(f0), mk(f1), mk(d0), mk(d1)};
-    return Mob{mk(f0, d0), mk(f1, d1), mk(d0, T.e0[c]), mk(d1, T.e1[c])};
-  }
-  // Five-point Laplacian with even reflection; its derivative with respect
-  // to the seeded cell is -(neighbours)/ds^2 at that cell, 1/ds^2 next to it.
-  __device__ __forceinline__ Dual lap(int i, int j) const {
-    const double v = T.lap[(size_t)j * nx + i];
-    if (pi < 0) return mk(v);
-    const int di = pi - i, dj = pj - j;
-    if (di == 0 && dj == 0) {
-      const int cnt = (i + 1 < nx) + (i > 0) + (j + 1 < ny) + (j > 0);
-      return mk(v, -(double)cnt * inv_ds2);
-    }
-    const int ad = (di < 0 ? -di : di) + (dj < 0 ? -dj : dj);
-    return mk(v, ad == 1 ? inv_ds2 : 0.0);
-  }
-};
-
 // d(along-line second difference at line cell c)/d(u at line cell col),
 // reflection at the ends of a line of n cells, times ds^2.
 __device__ __forceinline__ double dlap_line(int c, int col, int n) {
@@ -148,42 +98,29 @@ __device__ __forceinline__ double dlap_line(int c, int col, int n) {
 // over columns p-1..p+2, and -+fbar1/ds on p, q; row p gets +theta dt dF/ds,
 // row q -theta dt dF/ds.
 template <int DIR>
-__device__ void row_band(const AdjK& M, const Film& F, int i, int j, Dual (&band)[5]) {
+__device__ void row_band(const AdjK& M, const double* __restrict__ u, const Tables& T, int i, int j,
+                         double (&band)[5]) {
   const int n = DIR == 0 ? M.nx : M.ny, t = DIR == 0 ? i : j;
-  for (int d = 0; d < 5; ++d) band[d] = mk(d == 2 ? 1.0 : 0.0);
-  auto cell = [&](int s, int& ci, int& cj) {
-    ci = DIR == 0 ? s : i;
-    cj = DIR == 0 ? j : s;
-  };
+  const size_t c = (size_t)j * M.nx + i, step = DIR == 0 ? 1 : (size_t)M.nx;
+  for (int d = 0; d < 5; ++d) band[d] = d == 2 ? 1.0 : 0.0;
   for (int side = 0; side < 2; ++side) {
     const int p = side == 0 ? t - 1 : t, q = p + 1;
     if (p < 0 || q >= n) continue;
-    int pi, pj, qi, qj;
-    cell(p, pi, pj);
-    cell(q, qi, qj);
-    const Dual up = F.at(pi, pj), uq = F.at(qi, qj);
-    const Dual lp = F.lap(pi, pj), lq = F.lap(qi, qj);
-    const Mob mp = F.mob(pi, pj), mq = F.mob(qi, qj);
-    const Dual fb0 = 0.5 * (mp.f0 + mq.f0), fb1 = 0.5 * (mp.f1 + mq.f1);
-    const Dual gL = M.inv_ds * (lq - lp), gU = M.inv_ds * (uq - up);
+    const size_t cp = side == 0 ? c - step : c, cq = cp + step;
+    const double fb0 = 0.5 * (T.f0[cp] + T.f0[cq]), fb1 = 0.5 * (T.f1[cp] + T.f1[cq]);
+    const double gL = M.inv_ds * (T.lap[cq] - T.lap[cp]), gU = M.inv_ds * (u[cq] - u[cp]);
     const double sgn = side == 0 ? -1.0 : 1.0;  // row t is q (side 0) or p (side 1)
     const double coef = sgn * M.tdt * M.inv_ds;
     for (int a = 0; a < 4; ++a) {
       const int col = p - 1 + a;
       if (col < 0 || col >= n) continue;
       const double dl = (dlap_line(q, col, n) - dlap_line(p, col, n)) * M.inv_ds * M.inv_ds * M.inv_ds;
-      Dual v = dl * fb0;
-      if (col == p) v = v + 0.5 * (mp.d0 * gL) + 0.5 * (mp.d1 * gU) - M.inv_ds * fb1;
-      if (col == q) v = v + 0.5 * (mq.d0 * gL) + 0.5 * (mq.d1 * gU) + M.inv_ds * fb1;
-      band[col - t + 2] = band[col - t + 2] + coef * v;
+      double v = dl * fb0;
+      if (col == p) v += 0.5 * T.d0[cp] * gL + 0.5 * T.d1[cp] * gU - M.inv_ds * fb1;
+      if (col == q) v += 0.5 * T.d0[cq] * gL + 0.5 * T.d1[cq] * gU + M.inv_ds * fb1;
+      band[col - t + 2] += coef * v;
     }
   }
-}
-
-__device__ __forceinline__ Film make_film(const AdjK& M, const double* u, const Tables& T, int pi, int pj,
-                                          bool kseed) {
-  return Film{u, T, M.nx, M.ny, pi, pj, kseed, M.model == TF_MODEL_LINEAR ? 0.0 : 1.0 / M.kappa,
-              M.inv_ds * M.inv_ds};
 }
 
 // ---- transposed derivative products, hand-derived (two passes) ----------
@@ -360,11 +297,10 @@ template <int DIR>
 __global__ void k_band(AdjK M, const double* __restrict__ u, Tables T, double* __restrict__ band) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= M.nx) return;
-  const Film F = make_film(M, u, T, -1, -1, false);
-  Dual b[5];
-  row_band<DIR>(M, F, i, j, b);
+  double b[5];
+  row_band<DIR>(M, u, T, i, j, b);
   const size_t N = (size_t)M.nx * M.ny, c = (size_t)j * M.nx + i;
-  for (int d = 0; d < 5; ++d) band[d * N + c] = b[d].v;
+  for (int d = 0; d < 5; ++d) band[d * N + c] = b[d];
 }
 
 // Transposed pentadiagonal solves A^T x = r along every line of direction
