@@ -61,3 +61,19 @@ def test_reference_arm_prints_one_line_on_rank0_only():
                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True,
                         env=env1, timeout=600)
     assert r1.returncode == 0 and r1.stdout.strip() == ""
+
+
+@pytest.mark.parametrize("workload", ["adjoint1k", "spectrum8k", "ensemble", "nlc8k"])
+def test_reference_arm_of_every_workload(workload):
+    # three warm-up attempts, as the driver runs it (the first attempts of an
+    # adaptive run may be rejected while dt settles)
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", workload, "--steps", "1", "--warmup", "3"], capture_output=True,
+                       text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["ms_per_step"] > 0
+    for k in ("metric", "unit", "n_gpus", "steps", "warmup", "higher_is_better", "cpu_baseline", "e2e",
+              "config"):
+        assert k in line
