@@ -223,20 +223,24 @@ def run_mode(tf, torch, w, h0, mode, warmup, steps, dist, replay=None, e2e_steps
 
 
 def kernel_table(res, N, lp):
-    """Per-kernel launches, mean duration and algorithmic bytes per launch.
+    """Per-kernel launches, total duration and algorithmic bytes per launch.
 
     Algorithmic bytes per cell of one Newton iteration are those of the
     method's two passes: pass A reads u_k (8) and b^n (HP, 8) and writes w
     (LP); pass B reads w (LP) and u_k (8) and writes u_{k+1} (8), i.e. 40 B
     per cell in FP32-bulk and 48 B in FP64.  Pass A runs here as the residual
     kernel (reads u_k and b^n) and the x sweep (writes w); pass B is the y
-    sweep.  Everything else -- the right side and the FP32 film handed from
-    the residual kernel to the sweeps, LU-factor spills, halo re-reads -- is
-    implementation traffic, counted by ncu but not in the numerator.
+    sweep.  The explicit part reads u^n and writes b^n (16 B) once per step;
+    in tf_advance it also forms the first iteration's right side from the
+    same D(u^n), so that iteration has no residual launch.  Everything else
+    -- the right side and the FP32 film handed from the residual kernel to
+    the sweeps, LU-factor spills, halo re-reads -- is implementation
+    traffic, counted by ncu but not in the numerator.
     """
     t = res["timing"]
     cells = N * N
     return {
+        "explicit": (t["explicit_launches"], t["explicit_ms"], cells * 16),
         "rhs": (t["rhs_launches"], t["rhs_ms"], cells * 16),
         "x_sweep": (t["x_launches"], t["x_ms"], cells * lp),
         "y_sweep": (t["y_launches"], t["y_ms"], cells * (16 + lp)),
@@ -247,7 +251,7 @@ def kernel_table(res, N, lp):
 # from the ncu capture summarised in profiles/iteration_kernels_f32b_prof4k.md
 # (4096^2; traffic scales with the cells).  Valid for the kernels as
 # captured; set an entry to None when that kernel changes.
-TRAFFIC_PER_CELL_F32B = {"rhs": 22.26, "x_sweep": 31.45, "y_sweep": 44.54}
+TRAFFIC_PER_CELL_F32B = {"rhs": 22.26, "x_sweep": 31.45, "y_sweep": 44.54, "explicit": None}
 
 
 def roofline_hbm(res, N, lp_bytes, pk, traffic_per_cell=None):
@@ -260,16 +264,18 @@ def roofline_hbm(res, N, lp_bytes, pk, traffic_per_cell=None):
     ach = b / (per * 1e-3) / 1e9
     tpc = (traffic_per_cell or {}).get(name)
     traffic = None if tpc is None else round(tpc * N * N)
+    # the whole Newton loop (explicit parts included) per Newton iteration
     iters = max(1, tab["y_sweep"][0])
     it_ms = sum(v[1] for v in tab.values()) / iters
-    it_b = sum(v[2] for v in tab.values())
+    it_b = sum(v[0] * v[2] for v in tab.values()) / iters
     it_ach = it_b / (it_ms * 1e-3) / 1e9
     return dict(bound="hbm", kernel=name, achieved=round(ach, 1), peak=pk["hbm_gbs"],
                 unit="GB/s", frac=round(ach / pk["hbm_gbs"], 4), traffic=traffic,
                 ms_per_launch=round(per, 4), algorithmic_bytes_per_launch=b,
                 peak_source=pk["source"],
-                iteration=dict(ms=round(it_ms, 4), algorithmic_bytes=it_b,
-                               achieved=round(it_ach, 1), frac=round(it_ach / pk["hbm_gbs"], 4)))
+                iteration=dict(ms=round(it_ms, 4), algorithmic_bytes=round(it_b),
+                               achieved=round(it_ach, 1), frac=round(it_ach / pk["hbm_gbs"], 4),
+                               scope="every kernel of the Newton loop, explicit parts included"))
 
 
 MODEL_NAMES = {0: "power-law", 1: "linear", 2: "NLC", 3: "polymer"}

@@ -227,7 +227,10 @@ int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const doubl
 typedef struct {
   int enabled;
   int launches;          /* kernels launched while enabled (all kinds)       */
-  int explicit_launches; /* b^n stencil launches                             */
+  int explicit_launches; /* b^n launches (in tf_newton_adi_step, tf_advance and
+                            ensembles they also form the right side of the
+                            step's first iteration, which then has no
+                            residual launch of its own)                    */
   int rhs_launches;      /* residual (right side of the x solve) launches    */
   int x_launches;        /* x-line sweep launches                            */
   int y_launches;        /* y-line sweep launches                            */

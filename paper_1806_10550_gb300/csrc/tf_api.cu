@@ -52,11 +52,14 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 // One pseudo-Newton ADI iteration from u_k (b^n already formed):
 // residual -> x sweep -> y sweep -> reductions, queued on the context's
 // stream; iterate_collect() reads the result once the stream has reached it.
+// rhs_ready: the residual of this iteration was formed with b^n (the first
+// iteration of a step, explicit_launch with rhs0).
 int iterate_launch(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_out,
-                   double* v_out) {
+                   double* v_out, bool rhs_ready = false) {
   const bool tm = c.timing.enabled;
+  c.rhs_fused = rhs_ready;
   if (tm) TF_CK(cudaEventRecord(c.ev[0], c.stream));
-  TF_CK(c.ops->rhs(c, u_k, dt));
+  if (!rhs_ready) TF_CK(c.ops->rhs(c, u_k, dt));
   if (tm) TF_CK(cudaEventRecord(c.ev[1], c.stream));
   TF_CK(c.ops->xsweep(c, dt, u_k));
   if (tm) TF_CK(cudaEventRecord(c.ev[2], c.stream));
@@ -68,31 +71,35 @@ int iterate_launch(tf_ctx& c, const double* u_k, double dt, double* u_next, doub
 }
 void iterate_collect(tf_ctx& c, bool w_out, Scalars* s) {
   if (c.timing.enabled) {
-    c.timing.rhs_ms += elapsed(c.ev[0], c.ev[1]);
+    if (!c.rhs_fused) {
+      c.timing.rhs_ms += elapsed(c.ev[0], c.ev[1]);
+      c.timing.rhs_launches++;
+    }
     c.timing.x_ms += elapsed(c.ev[1], c.ev[2]);
     c.timing.y_ms += elapsed(c.ev[3], c.ev[4]);
-    c.timing.rhs_launches++;
     c.timing.x_launches++;
     c.timing.y_launches++;
-    c.timing.launches += 4 + (w_out && c.ops->lp_bytes != sizeof(double) ? 1 : 0);
+    c.timing.launches += (c.rhs_fused ? 3 : 4) + (w_out && c.ops->lp_bytes != sizeof(double) ? 1 : 0);
   }
   *s = *c.hsc;
 }
 int iterate(tf_ctx& c, const double* u_k, double dt, double* u_next, double* w_out, double* v_out,
-            Scalars* s) {
-  int r = iterate_launch(c, u_k, dt, u_next, w_out, v_out);
+            Scalars* s, bool rhs_ready = false) {
+  int r = iterate_launch(c, u_k, dt, u_next, w_out, v_out, rhs_ready);
   if (r) return r;
   TF_CK(cudaStreamSynchronize(c.stream));
   iterate_collect(c, w_out != nullptr, s);
   return TF_OK;
 }
 
-// The explicit part of a step; with timing on, its events (5, 6) are read
-// by explicit_collect() once the stream has passed them.
-int explicit_launch(tf_ctx& c, const double* h_old, double dt) {
+// The explicit part of a step -- with rhs0, also the right side of the
+// step's first iteration from u_0 = h_old (one kernel in FP32-bulk, where
+// D(h_old) serves both); with timing on, its events (5, 6) are read by
+// explicit_collect() once the stream has passed them.
+int explicit_launch(tf_ctx& c, const double* h_old, double dt, bool rhs0 = false) {
   const bool tm = c.timing.enabled;
   if (tm) TF_CK(cudaEventRecord(c.ev[5], c.stream));
-  TF_CK(c.ops->explicit_part(c, h_old, dt));
+  TF_CK(rhs0 ? c.ops->explicit_rhs0(c, h_old, dt) : c.ops->explicit_part(c, h_old, dt));
   if (tm) TF_CK(cudaEventRecord(c.ev[6], c.stream));
   return TF_OK;
 }
@@ -100,7 +107,7 @@ void explicit_collect(tf_ctx& c) {
   if (!c.timing.enabled) return;
   c.timing.explicit_ms += elapsed(c.ev[5], c.ev[6]);
   c.timing.explicit_launches++;
-  c.timing.launches++;
+  c.timing.launches += c.expl_kernels;
 }
 
 // Mass and min h of a film (once per step), into s->mass and s->hmin:
@@ -145,7 +152,7 @@ void fill_info(tf_step_info* info, int status, int it, const Scalars& s) {
 // A time step with an explicit fixed-iteration override (0 = none).
 // The iterate ping-pongs between h_new and c.ubuf; the result is in h_new.
 int step(tf_ctx& c, const double* h_old, double* h_new, double dt, int fixed_iter, tf_step_info* info) {
-  int re = explicit_launch(c, h_old, dt);
+  int re = explicit_launch(c, h_old, dt, true);
   if (re) return re;
   const int kmax = fixed_iter > 0 ? fixed_iter : c.p.newton_max_iter;
   const double* uk = h_old;
@@ -155,7 +162,7 @@ int step(tf_ctx& c, const double* h_old, double* h_new, double dt, int fixed_ite
   int status = TF_STEP_NOT_CONVERGED, it = 0;
   for (int k = 0; k < kmax; ++k) {
     double* un = bufs[k & 1];
-    int r = iterate(c, uk, dt, un, nullptr, nullptr, &s);
+    int r = iterate(c, uk, dt, un, nullptr, nullptr, &s, k == 0);
     if (r) return r;
     if (k == 0) explicit_collect(c);
     it = k + 1;
@@ -225,7 +232,7 @@ int film_start_attempt(FilmRun& F) {
   } else {
     F.step_dt = F.dt;
   }
-  int r = explicit_launch(c, F.cur, F.step_dt);
+  int r = explicit_launch(c, F.cur, F.step_dt, true);
   if (r) return r;
   F.kmax = F.fixed > 0 ? F.fixed : c.p.newton_max_iter;
   F.k = 0;
@@ -235,7 +242,7 @@ int film_start_attempt(FilmRun& F) {
   memset(&F.s, 0, sizeof(F.s));
   F.sstatus = TF_STEP_NOT_CONVERGED;
   F.it = 0;
-  r = iterate_launch(c, F.uk, F.step_dt, F.bufs[0], nullptr, nullptr);
+  r = iterate_launch(c, F.uk, F.step_dt, F.bufs[0], nullptr, nullptr, true);
   if (r) return r;
   TF_CK(cudaEventRecord(c.ev[7], c.stream));
   F.phase = 1;

@@ -21,6 +21,8 @@ struct Ops {
   size_t hp_bytes, lp_bytes;
   cudaError_t (*prepare)();
   cudaError_t (*explicit_part)(tf_ctx& c, const double* u_old, double dt);
+  // explicit part plus the first iteration's right side (u_0 = u_old)
+  cudaError_t (*explicit_rhs0)(tf_ctx& c, const double* u_old, double dt);
   cudaError_t (*residual_g)(tf_ctx& c, const double* u_k, double dt, double* G);
   cudaError_t (*rhs)(tf_ctx& c, const double* u_k, double dt);
   cudaError_t (*xsweep)(tf_ctx& c, double dt, const double* u_k);
@@ -62,6 +64,8 @@ struct tf_ctx {
   tf::Scalars* hsc;  // pinned
   tf_timing timing;
   cudaEvent_t ev[8];  // 0-4 iteration timing, 5-6 explicit-part timing, 7 work done (ensembles)
+  bool rhs_fused;     // the iteration in flight had its residual formed with b^n
+  int expl_kernels;   // kernels the last explicit-part launch queued
   void* adj_ws;       // workspace of tf_adjoint_step (grown on demand)
   size_t adj_bytes;
 };

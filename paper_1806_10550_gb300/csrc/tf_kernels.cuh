@@ -193,16 +193,18 @@ template <class T> inline LineK<T> line_consts(const ModelK& M, const StepK& K) 
 template <class T> struct RhsK {
   MobC<T> mc;
   T inv_ds2, four;
-  T gscale;  // theta dt/(2 ds^2), or (1 - theta) dt/(2 ds^2) for the explicit part
+  T gscale;   // theta dt/(2 ds^2), or (1 - theta) dt/(2 ds^2) for the explicit part
+  T gscale2;  // theta dt/(2 ds^2) (the residual's, when one kernel forms both)
 };
 // gscale: theta dt/(2 ds^2) for the residual, (1 - theta) dt/(2 ds^2) for
-// the explicit part (expl).
+// the explicit part (expl); gscale2 always the residual's.
 template <class T> inline RhsK<T> rhs_consts(const ModelK& M, const StepK& K, bool expl = false) {
   RhsK<T> R;
   R.mc = mob_consts<T>(M);
   R.inv_ds2 = from_f64<T>(M.inv_ds2);
   R.four = from_f64<T>(4.0);
   R.gscale = from_f64<T>(0.5 * M.inv_ds2 * (expl ? K.expl_dt : K.theta_dt));
+  R.gscale2 = from_f64<T>(0.5 * M.inv_ds2 * K.theta_dt);
   return R;
 }
 

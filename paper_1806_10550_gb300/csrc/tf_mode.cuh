@@ -41,18 +41,22 @@ template <class Mode> struct Launch {
     if ((e = cudaFuncSetAttribute(k_rhs<Mode, true>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if constexpr (kF32B) {
       const int sp = (int)sizeof(RhsPackedSmem);
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<false>, A, sp))) return e;
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<true>, A, sp))) return e;
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<false>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<true>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+      const int maxc = (int)cudaSharedmemCarveoutMaxShared;
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsResidual>, A, sp))) return e;
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsExplicit>, A, sp))) return e;
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsBoth>, A, sp))) return e;
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsResidual>, C, maxc))) return e;
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsExplicit>, C, maxc))) return e;
+      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsBoth>, C, maxc))) return e;
     }
     return cudaFuncSetAttribute(k_rhs<Mode, false>, C, (int)cudaSharedmemCarveoutMaxShared);
   }
 
   static cudaError_t explicit_part_c(tf_ctx& c, const double* u_old, double dt) {
+    c.expl_kernels = 1;
     if constexpr (kF32B) {
       if (c.packed_rhs) {
-        k_rhs_packed<true><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
+        k_rhs_packed<kRhsExplicit><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
             c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, nullptr, nullptr, nullptr);
         return cudaGetLastError();
       }
@@ -71,7 +75,7 @@ template <class Mode> struct Launch {
   static cudaError_t rhs_c(tf_ctx& c, const double* u_k, double dt) {
     if constexpr (kF32B) {
       if (c.packed_rhs) {
-        k_rhs_packed<false><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
+        k_rhs_packed<kRhsResidual><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
             c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px);
         return cudaGetLastError();
       }
@@ -81,6 +85,24 @@ template <class Mode> struct Launch {
                                                    (HP*)c.bn, (LP*)c.w,
                                                    (LP*)c.ulp, c.px);
     return cudaGetLastError();
+  }
+  // b^n of a step and the right side of its first iteration (u_0 = u^n):
+  // one packed kernel in FP32-bulk (D(u^n) formed once), else the two
+  // kernels in turn.  Results equal explicit_part_c then rhs_c.
+  static cudaError_t explicit_rhs0_c(tf_ctx& c, const double* u_old, double dt) {
+    c.expl_kernels = 2;
+    if constexpr (kF32B) {
+      if (c.packed_rhs) {
+        c.expl_kernels = 1;
+        k_rhs_packed<kRhsBoth><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
+            c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px);
+        return cudaGetLastError();
+      }
+    }
+    cudaError_t e = explicit_part_c(c, u_old, dt);
+    if (e != cudaSuccess) return e;
+    c.expl_kernels = 2;
+    return rhs_c(c, u_old, dt);
   }
   // film the sweeps stage: u_k itself in FP64, its FP32 copy (written by
   // k_rhs of the same iteration) in FP32-bulk
@@ -116,6 +138,7 @@ template <class Mode> Ops make_ops() {
   o.lp_bytes = sizeof(typename Mode::LP);
   o.prepare = &L::prepare;
   o.explicit_part = &L::explicit_part_c;
+  o.explicit_rhs0 = &L::explicit_rhs0_c;
   o.residual_g = &L::residual_c;
   o.rhs = &L::rhs_c;
   o.xsweep = &L::xsweep_c;

@@ -123,7 +123,12 @@ __device__ __forceinline__ df2 mid2(df2 A, df2 B) {
   return d2(make_float2(A.hi.y, B.hi.x), make_float2(A.lo.y, B.lo.x));
 }
 
-template <bool EXPL>
+// KIND: kRhsResidual (G from u_k and the stored b^n), kRhsExplicit (b^n from
+// u^n) or kRhsBoth (b^n from u^n, stored, and G of the first iteration,
+// u_0 = u^n, from the same stored b^n -- what kRhsResidual would compute).
+enum { kRhsResidual = 0, kRhsExplicit = 1, kRhsBoth = 2 };
+
+template <int KIND>
 __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per SM: up to 64 registers
     k_rhs_packed(ModelK M, RhsK<df64> RK, const double* __restrict__ u, df64* __restrict__ bn,
                  float* __restrict__ rhs, float* __restrict__ ulp, PartX* __restrict__ part) {
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per 
   constexpr int W4 = kPC / 2, N4 = kPR * W4 / kPT;
   static_assert(kPR * W4 == N4 * kPT, "stage 4 gives every thread the same number of pairs");
   df64 bnr[N4][2];
-  if constexpr (!EXPL) {
+  if constexpr (KIND == kRhsResidual) {
 #pragma unroll
     for (int e = 0; e < N4; ++e) {
       const int k = tid + e * kPT, r = k / W4, c = 2 * (k - r * W4);
@@ -256,14 +261,23 @@ __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per 
                             d2_sub_u(ld2(S.fyh[r + 1], S.fyl[r + 1], c), ld2(S.fyh[r], S.fyl[r], c)));
     const df2 uc = ld2(S.uh[r + 2], S.ul[r + 2], c + 4);
     const size_t idx = (size_t)gj * nx + gi;
-    if constexpr (EXPL) {
+    if constexpr (KIND == kRhsExplicit) {
       const df2 b = d2_norm(d2_sub_u(uc, d2_mul_u(gscale, dp)));
       bn[idx] = df_make(b.hi.x, b.lo.x);
       if (two) bn[idx + 1] = df_make(b.hi.y, b.lo.y);
     } else {
-      const df64 b0 = bnr[e][0], b1 = bnr[e][1];
-      const df2 Gv = d2_norm(d2_add_u(d2_sub_u(uc, d2(make_float2(b0.hi, b1.hi), make_float2(b0.lo, b1.lo))),
-                                      d2_mul_u(gscale, dp)));
+      df2 bv;
+      if constexpr (KIND == kRhsBoth) {
+        bv = d2_norm(d2_sub_u(uc, d2_mul_u(gscale, dp)));
+        bn[idx] = df_make(bv.hi.x, bv.lo.x);
+        if (two) bn[idx + 1] = df_make(bv.hi.y, bv.lo.y);
+        if (!two) bv = d2(make_float2(bv.hi.x, 1.0f), make_float2(bv.lo.x, 0.0f));  // as the loaded pair
+      } else {
+        const df64 b0 = bnr[e][0], b1 = bnr[e][1];
+        bv = d2(make_float2(b0.hi, b1.hi), make_float2(b0.lo, b1.lo));
+      }
+      const df2 gs = KIND == kRhsBoth ? d2_splat(RK.gscale2) : gscale;
+      const df2 Gv = d2_norm(d2_add_u(d2_sub_u(uc, bv), d2_mul_u(gs, dp)));
       const float2 gl = p_add(Gv.hi, Gv.lo);
       // FP32 film for the sweeps: the leading float of the double-float height
       if (two && ((nx | gi) & 1) == 0) {
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per 
       if (!(ag <= g)) g = ag;
     }
   }
-  if constexpr (EXPL) return;
+  if constexpr (KIND == kRhsExplicit) return;
   for (int o = 16; o > 0; o >>= 1) {
     const float g2 = __shfl_xor_sync(0xffffffffu, g, o);
     if (!(g2 <= g)) g = g2;

@@ -288,3 +288,17 @@ def test_kappa_from_contact_angle(torch):
     ctx = tf.Context(p)
     assert ctx.kappa == pytest.approx(O.kappa_from_contact_angle(math.radians(20.0), 0.1, 3, 2),
                                       rel=1e-15)
+
+
+@pytest.mark.parametrize("mode", [tf.TF_FP64, tf.TF_FP32_BULK])
+def test_fused_first_iteration_is_bit_identical(torch, mode):
+    # a step's first iteration forms b^n and its right side in one kernel
+    # (FP32-bulk); tf_newton_iteration forms them in two: the same bits
+    nx, ny = 300, 200
+    p = tf.tf_params_default(nx=nx, ny=ny, ds=2.0, precision=mode, newton_fixed_iter=1)
+    h = torch.from_numpy(S.spinodal_film(nx, ny, 1.0, 0.01, seed=31)).cuda()
+    a, b = torch.empty_like(h), torch.empty_like(h)
+    ctx = tf.Context(p)
+    tf.tf_newton_adi_step(ctx, h, a, 0.5)
+    tf.tf_newton_iteration(ctx, h, h, 0.5, b)
+    assert torch.equal(a, b)
