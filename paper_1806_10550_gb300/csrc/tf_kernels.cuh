@@ -190,6 +190,11 @@ template <class T> inline LineK<T> line_consts(const ModelK& M, const StepK& K) 
   L.pD1 = (T)(k1 * M.B1);
   return L;
 }
+// What a residual-stencil kernel forms: the residual of an iteration, the
+// explicit part of a step, or both from one D(u^n) (a step's first
+// iteration starts from u_0 = u^n).
+enum { kRhsResidual = 0, kRhsExplicit = 1, kRhsBoth = 2 };
+
 template <class T> struct RhsK {
   MobC<T> mc;
   T inv_ds2, four;

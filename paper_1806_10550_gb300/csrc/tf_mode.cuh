@@ -30,15 +30,17 @@ template <class Mode> struct Launch {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     if ((e = cudaFuncSetAttribute(k_stencil<Mode, 0>, A, (int)smem_stencil))) return e;
     if ((e = cudaFuncSetAttribute(k_stencil<Mode, 1>, A, (int)smem_stencil))) return e;
-    if ((e = cudaFuncSetAttribute(k_rhs<Mode, false>, A, (int)smem_rhs))) return e;
-    if ((e = cudaFuncSetAttribute(k_rhs<Mode, true>, A, (int)smem_rhs))) return e;
+    if ((e = cudaFuncSetAttribute(k_rhs<Mode, kRhsResidual>, A, (int)smem_rhs))) return e;
+    if ((e = cudaFuncSetAttribute(k_rhs<Mode, kRhsExplicit>, A, (int)smem_rhs))) return e;
+    if ((e = cudaFuncSetAttribute(k_rhs<Mode, kRhsBoth>, A, (int)smem_rhs))) return e;
     if ((e = cudaFuncSetAttribute(k_xsweep<Mode>, A, (int)smem_x))) return e;
     if ((e = cudaFuncSetAttribute(k_ysweep<Mode>, A, (int)smem_y))) return e;
     // the sweeps run two blocks per SM only with the largest shared carveout
     const cudaFuncAttribute C = cudaFuncAttributePreferredSharedMemoryCarveout;
     if ((e = cudaFuncSetAttribute(k_xsweep<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if ((e = cudaFuncSetAttribute(k_ysweep<Mode>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
-    if ((e = cudaFuncSetAttribute(k_rhs<Mode, true>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+    if ((e = cudaFuncSetAttribute(k_rhs<Mode, kRhsExplicit>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+    if ((e = cudaFuncSetAttribute(k_rhs<Mode, kRhsBoth>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if constexpr (kF32B) {
       const int sp = (int)sizeof(RhsPackedSmem);
       const int maxc = (int)cudaSharedmemCarveoutMaxShared;
@@ -49,7 +51,7 @@ template <class Mode> struct Launch {
       if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsExplicit>, C, maxc))) return e;
       if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsBoth>, C, maxc))) return e;
     }
-    return cudaFuncSetAttribute(k_rhs<Mode, false>, C, (int)cudaSharedmemCarveoutMaxShared);
+    return cudaFuncSetAttribute(k_rhs<Mode, kRhsResidual>, C, (int)cudaSharedmemCarveoutMaxShared);
   }
 
   static cudaError_t explicit_part_c(tf_ctx& c, const double* u_old, double dt) {
@@ -62,7 +64,7 @@ template <class Mode> struct Launch {
       }
     }
     dim3 grid(c.grid_rx, c.grid_ry);
-    k_rhs<Mode, true><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old,
+    k_rhs<Mode, kRhsExplicit><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old,
                                                          (HP*)c.bn, nullptr, nullptr, nullptr);
     return cudaGetLastError();
   }
@@ -81,28 +83,27 @@ template <class Mode> struct Launch {
       }
     }
     dim3 grid(c.grid_rx, c.grid_ry);
-    k_rhs<Mode, false><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k,
+    k_rhs<Mode, kRhsResidual><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k,
                                                    (HP*)c.bn, (LP*)c.w,
                                                    (LP*)c.ulp, c.px);
     return cudaGetLastError();
   }
-  // b^n of a step and the right side of its first iteration (u_0 = u^n):
-  // one packed kernel in FP32-bulk (D(u^n) formed once), else the two
-  // kernels in turn.  Results equal explicit_part_c then rhs_c.
+  // b^n of a step and the right side of its first iteration (u_0 = u^n)
+  // from one D(u^n); results equal explicit_part_c then rhs_c.
   static cudaError_t explicit_rhs0_c(tf_ctx& c, const double* u_old, double dt) {
-    c.expl_kernels = 2;
+    c.expl_kernels = 1;
     if constexpr (kF32B) {
       if (c.packed_rhs) {
-        c.expl_kernels = 1;
         k_rhs_packed<kRhsBoth><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
             c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px);
         return cudaGetLastError();
       }
     }
-    cudaError_t e = explicit_part_c(c, u_old, dt);
-    if (e != cudaSuccess) return e;
-    c.expl_kernels = 2;
-    return rhs_c(c, u_old, dt);
+    c.expl_kernels = 1;
+    dim3 grid(c.grid_rx, c.grid_ry);
+    k_rhs<Mode, kRhsBoth><<<grid, 256, smem_rhs, c.stream>>>(c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old,
+                                                             (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px);
+    return cudaGetLastError();
   }
   // film the sweeps stage: u_k itself in FP64, its FP32 copy (written by
   // k_rhs of the same iteration) in FP32-bulk

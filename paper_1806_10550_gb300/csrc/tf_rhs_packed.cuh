@@ -126,8 +126,6 @@ __device__ __forceinline__ df2 mid2(df2 A, df2 B) {
 // KIND: kRhsResidual (G from u_k and the stored b^n), kRhsExplicit (b^n from
 // u^n) or kRhsBoth (b^n from u^n, stored, and G of the first iteration,
 // u_0 = u^n, from the same stored b^n -- what kRhsResidual would compute).
-enum { kRhsResidual = 0, kRhsExplicit = 1, kRhsBoth = 2 };
-
 template <int KIND>
 __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per SM: up to 64 registers
     k_rhs_packed(ModelK M, RhsK<df64> RK, const double* __restrict__ u, df64* __restrict__ bn,

@@ -53,10 +53,13 @@ template <class HP, int T> struct RhsSmem {
   HP fx[T][T + 1], fy[T + 1][T];
 };
 
-// EXPL = false: the residual pass of one Newton iteration.  EXPL = true: the
-// explicit part b^n = u^n - (1 - theta) dt D(u^n) of a step (eq.
+// KIND kRhsResidual: the residual pass of one Newton iteration.  kRhsExplicit:
+// the explicit part b^n = u^n - (1 - theta) dt D(u^n) of a step (eq.
 // CrankNicolson), written to bn in HP; rhs, ul and part are unused.
-template <class Mode, bool EXPL>
+// kRhsBoth: both from one D(u^n) -- b^n, and the residual of the step's
+// first iteration (u_0 = u^n) from the stored b^n, as kRhsResidual would
+// form it (gscale the explicit part's, gscale2 the residual's).
+template <class Mode, int KIND>
 __global__ void __launch_bounds__(256, 4)  // shared memory allows 4 blocks per SM: up to 64 registers
     k_rhs(ModelK M, RhsK<typename Mode::HP> RK, const double* __restrict__ u,
           typename Mode::HP* __restrict__ bn,
@@ -124,11 +127,18 @@ __global__ void __launch_bounds__(256, 4)  // shared memory allows 4 blocks per 
     if (gj < M.ny && gi < M.nx) {
       const size_t idx = (size_t)gj * M.nx + gi;
       HP dp = hp_add(hp_sub(S.fx[r][c + 1], S.fx[r][c]), hp_sub(S.fy[r + 1][c], S.fy[r][c]));
-      if constexpr (EXPL) {  // gscale holds (1 - theta) dt / (2 ds^2)
+      if constexpr (KIND == kRhsExplicit) {  // gscale holds (1 - theta) dt / (2 ds^2)
         bn[idx] = hp_norm(hp_sub(S.u[r + 2][c + 2], hp_mul(gscale, dp)));
         continue;
       }
-      HP Gv = hp_norm(hp_add(hp_sub(S.u[r + 2][c + 2], bn[idx]), hp_mul(gscale, dp)));
+      HP Gv;
+      if constexpr (KIND == kRhsBoth) {
+        const HP b = hp_norm(hp_sub(S.u[r + 2][c + 2], hp_mul(gscale, dp)));
+        bn[idx] = b;
+        Gv = hp_norm(hp_add(hp_sub(S.u[r + 2][c + 2], b), hp_mul(RK.gscale2, dp)));
+      } else {
+        Gv = hp_norm(hp_add(hp_sub(S.u[r + 2][c + 2], bn[idx]), hp_mul(gscale, dp)));
+      }
       LP gl = to_lp<LP, HP>(Gv);
       rhs[idx] = -gl;
       // FP32 film for the sweeps: the leading float of the double-float
@@ -138,7 +148,7 @@ __global__ void __launch_bounds__(256, 4)  // shared memory allows 4 blocks per 
       if (!(ag <= g)) g = ag;
     }
   }
-  if constexpr (EXPL) return;
+  if constexpr (KIND == kRhsExplicit) return;
   for (int o = 16; o > 0; o >>= 1) {
     LP g2 = __shfl_xor_sync(0xffffffffu, g, o);
     if (!(g2 <= g)) g = g2;
