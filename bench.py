@@ -298,9 +298,26 @@ def cpu_baseline_sample(w, h0):
     t = time.perf_counter()
     _, info = O.step(M, ctl, h0, w["dt0"])
     el = time.perf_counter() - t
-    return dict(value=N * N / el, unit="cell-updates/s", cores=O.num_threads(), kind="oracle",
-                sample=f"one time step (dt={w['dt0']}, {info['iterations']} Newton iterations) "
-                       f"of the {N}x{N} film on the host cores, {el:.1f} s")
+    out = dict(value=N * N / el, unit="cell-updates/s", cores=O.num_threads(), kind="oracle",
+               sample=f"one time step (dt={w['dt0']}, {info['iterations']} Newton iterations) "
+                      f"of the {N}x{N} film on the host cores, {el:.1f} s")
+    # The same oracle on one thread (identical results), one step of a 2048^2
+    # film with the workload's parameters and dt.
+    n1 = min(N, 2048)
+    from paper_1806_10550_gb300 import synthetic as S
+    h1 = S.spinodal_film(n1, n1, w["h0"], w["eps"], w["seed"])
+    cores = O.num_threads()
+    try:
+        O.set_num_threads(1)
+        t = time.perf_counter()
+        _, info1 = O.step(oracle_model(O, w, n1), ctl, h1, w["dt0"])
+        el1 = time.perf_counter() - t
+    finally:
+        O.set_num_threads(cores)
+    out["single_thread"] = dict(value=n1 * n1 / el1, unit="cell-updates/s", cores=1,
+                                sample=f"one time step ({info1['iterations']} Newton iterations) "
+                                       f"of a {n1}x{n1} film, one thread, {el1:.1f} s")
+    return out
 
 
 METRIC = "grid cell-updates/s per Newton-ADI step at 8192^2"

@@ -136,6 +136,8 @@ def lib():
                                  C.POINTER(C.c_int), C.POINTER(_Record), dp, dp,
                                  C.POINTER(C.c_int)]
         L.or_num_threads.restype = C.c_int
+        L.or_set_num_threads.restype = None
+        L.or_set_num_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -354,3 +356,9 @@ def advance(M: Model, ctl: Control, h0, t0: float, t_end: float, dt0: float,
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the following oracle calls; the results do not depend on
+    it (each line is one thread's work, with the same arithmetic)."""
+    lib().or_set_num_threads(int(n))

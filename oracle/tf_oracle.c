@@ -46,6 +46,14 @@ int or_num_threads(void) {
 #endif
 }
 
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* kappa = (1 - cos theta_c) / (b M), M = (n-m)/((m-1)(n-1)): the strength of
  * the power-law disjoining pressure that gives contact angle theta_c. */
 double or_kappa_from_contact_angle(double th, double b, int n, int m) {

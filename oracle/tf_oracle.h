@@ -137,6 +137,9 @@ int or_advance(const or_model* M, const or_control* C, double* h, double t0,
 
 /* Number of OpenMP threads the oracle uses (1 if built without OpenMP).    */
 int or_num_threads(void);
+/* Threads of the following calls (n > 0); every line is still computed by
+ * one thread with the same arithmetic, so results do not depend on n. */
+void or_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

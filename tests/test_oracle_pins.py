@@ -433,3 +433,23 @@ def test_newton_error_is_max_relative_update():
     v = r["unew"] - uk
     assert r["err"] == pytest.approx(np.max(np.abs(v) / uk), rel=1e-12)
     assert r["err"] > 3.0 * np.max(np.abs(v))
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """Every line is one thread's work with the same arithmetic, so one
+    thread and all cores give bit-identical steps (the single-thread and
+    all-core oracle timings compute the same thing)."""
+    M = pl_model(96, 80, 0.05)
+    h0 = S.spinodal_film(96, 80, 1.0, 0.01, 7)
+    ctl = O.Control(tol=1e-10, max_iter=10)
+    n0 = O.num_threads()
+    try:
+        O.set_num_threads(1)
+        assert O.num_threads() == 1
+        h1, i1 = O.step(M, ctl, h0, 1e-3)
+    finally:
+        O.set_num_threads(n0)
+    assert O.num_threads() == n0
+    hn, i_n = O.step(M, ctl, h0, 1e-3)
+    assert i1["iterations"] == i_n["iterations"]
+    assert np.array_equal(h1, hn)
