@@ -651,7 +651,8 @@ def reference_spectrum(args, w):
     print(json.dumps(line))
 
 
-ADJOINT_METRIC = "adjoint film cell-steps/s (forward + reverse of the 3-iteration step) at 1024^2"
+ADJOINT_METRIC = ("adjoint film cell-steps/s: gradient of |h(T) - h_target|^2 over 400 fixed steps "
+                  "(3 Newton iterations each, forward + checkpointed reverse) at 1024^2")
 
 # Algorithmic bytes per cell of one launch of each adjoint kernel group:
 # the transposed solve reads the five band diagonals and the right side and
@@ -665,14 +666,18 @@ ADJ_BYTES_PER_CELL = {"solve_t": 56.0, "line_x": 40.0, "line_y": 40.0, "D": 32.0
 def adjoint_config(w, world):
     N = w["N"]
     return dict(workload=(f"{N}x{N} spinodal film, power-law model, {w['P']} lambda_m square, "
-                          f"seed {w['seed']}, dt {w['dt_fixed']}, {w['fixed_iter']} Newton iterations unrolled"),
-                mode="FP64", global_batch=world, l2="working set larger than L2 (about 20 grids of 8 MiB)",
+                          f"seed {w['seed']}, {w['steps']} steps of dt {w['dt_fixed']} with "
+                          f"{w['fixed_iter']} Newton iterations unrolled; loss |h(T) - h_target|^2, "
+                          f"h_target from seed {w['target_seed']}; gradient in h(0) and theta_c; "
+                          f"checkpoints every ceil(sqrt({w['steps']})) steps"),
+                mode="FP64", global_batch=world,
+                l2="working set larger than L2 (about 60 grids of 8 MiB)",
                 parallelism=f"replicas x{world}")
 
 
 def oracle_adjoint_sample(w, n=12):
-    """The oracle's adjoint (complex-step Jacobian, transposed) on an n x n
-    sample of the workload (same spacing, dt and noise)."""
+    """The oracle's adjoint (complex-step Jacobian, transposed) of one step
+    on an n x n sample of the workload (same spacing, dt and noise)."""
     import oracle as O
     import oracle.adjoint as AD
     from paper_1806_10550_gb300 import synthetic as S
@@ -686,71 +691,94 @@ def oracle_adjoint_sample(w, n=12):
 
 
 def run_adjoint(args, w):
-    """Forward and reverse of the fixed-iteration step per timed step
-    (tf_adjoint_step), grids resident in HBM; e2e adds the copies of the film
-    and the cotangent from pinned host memory and of the result back."""
+    """The adjoint workload, one timed step = one loss gradient: the tape's
+    forward over the trajectory (checkpoints kept), the loss cotangent
+    2 (h(T) - h_target), and the checkpointed reverse; grids resident in
+    HBM.  e2e adds the H2D copy of the initial film from pinned memory and
+    the D2H copy of the gradient."""
     import torch
     import paper_1806_10550_gb300 as tf
     from paper_1806_10550_gb300 import synthetic as S
     rank, world, local, dist = dist_setup()
     tf.library(build_if_missing=True)
-    N, K, dt = w["N"], w["fixed_iter"], w["dt_fixed"]
-    ctx = tf.Context(tf.params_for_workload(w, tf.TF_FP64))
+    N, K, dt, ns = w["N"], w["fixed_iter"], w["dt_fixed"], w["steps"]
+    p = tf.params_for_workload(w, tf.TF_FP64)
+    p.kappa, p.contact_angle = 0.0, w["theta_c"]  # kappa from the contact angle
+    ctx = tf.Context(p)
+    tape = tf.tf_tape_create(ctx, ns, K, dt)
+    tinfo = tf.tf_tape_info(tape)
     h_host = torch.from_numpy(S.spinodal_film(N, N, w["h0"], w["eps"], w["seed"])).pin_memory()
-    g_host = torch.from_numpy(np.random.default_rng(5).standard_normal((N, N))).pin_memory()
-    h, g = h_host.cuda(), g_host.cuda()
-    gh = torch.empty_like(h)
+    h = h_host.cuda()
+    target = tf.tf_tape_forward(tape, torch.from_numpy(
+        S.spinodal_film(N, N, w["h0"], w["eps"], w["target_seed"])).cuda()).clone()
+    hT, gh = torch.empty_like(h), torch.empty_like(h)
+
+    def gradient(h0):
+        tf.tf_tape_forward(tape, h0, hT)
+        return tf.tf_tape_backward(tape, 2.0 * (hT - target), g_h0=gh)
+
     for _ in range(args.warmup):
-        tf.tf_adjoint_step(ctx, h, dt, K, g, g_h=gh)
-    S_ = args.steps if args.steps != 200 else 10
-    groups = {k: 0.0 for k in tf.ADJOINT_GROUPS}
+        gradient(h)
+    S_ = args.steps if args.steps != 200 else 1
+    groups = {k: 0.0 for k in tf.TAPE_GROUPS}
+    tf.tf_timing_enable(ctx, True)
     barrier(dist)
     clocks = ClockSampler(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with clocks:
         e0.record()
         for _ in range(S_):
-            r = tf.tf_adjoint_step(ctx, h, dt, K, g, g_h=gh)
-            for k, v in tf.tf_adjoint_timing().items():
+            r = gradient(h)
+            for k, v in tf.tf_tape_timing(tape).items():
                 groups[k] += v
         e1.record()
         torch.cuda.synchronize()
     barrier(dist)
     ms = e0.elapsed_time(e1)
-    value = job_rate(dist, N * N * S_, ms)
-    # end to end from pinned host buffers
-    hd, gd, out = torch.empty_like(h), torch.empty_like(g), torch.empty_like(h_host).pin_memory()
+    tim = tf.tf_timing_get(ctx)
+    tf.tf_timing_enable(ctx, False)
+    value = job_rate(dist, N * N * ns * S_, ms)
+    # end to end from pinned host memory
+    hd, out = torch.empty_like(h), torch.empty_like(h_host).pin_memory()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record()
     for _ in range(S_):
         hd.copy_(h_host, non_blocking=True)
-        gd.copy_(g_host, non_blocking=True)
-        tf.tf_adjoint_step(ctx, hd, dt, K, gd, g_h=gh)
+        gradient(hd)
         out.copy_(gh, non_blocking=True)
     e3.record()
     torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3)
+    # the dominant kernel over both halves: the forward's FP64 kernels (every
+    # forward, recomputed and re-run step; the context's timing) and the
+    # reverse's groups (the tape's timing)
     per = {k: v / S_ for k, v in groups.items()}
-    launches = {"solve_t": 2 * K, "line_x": K, "line_y": K, "D": K + 1}
-    dom = max(launches, key=lambda k: per[k])
-    ms_launch = per[dom] / launches[dom]
+    fwd = kernel_table(dict(timing=tim), N, 8)
+    rev_launches = {"solve_t": 2 * K * ns, "line_x": K * ns, "line_y": K * ns, "D": (K + 1) * ns}
+    cand = {k: (n_ / S_, ms_ / S_, b) for k, (n_, ms_, b) in fwd.items()}
+    cand.update({k: (rev_launches[k], per[k], ADJ_BYTES_PER_CELL[k] * N * N) for k in rev_launches})
+    dom = max(cand, key=lambda k: cand[k][1])
+    n_l, ms_k, bytes_l = cand[dom]
+    ms_launch = ms_k / max(1, n_l)
     pk = peaks()
-    ach = ADJ_BYTES_PER_CELL[dom] * N * N / (ms_launch * 1e-3) / 1e9
+    ach = bytes_l / (ms_launch * 1e-3) / 1e9
     roof = dict(bound="hbm", kernel=dom, unit="GB/s", peak=pk["hbm_gbs"], peak_source=pk["source"],
                 ms_per_launch=round(ms_launch, 4), achieved=round(ach, 1), frac=round(ach / pk["hbm_gbs"], 4),
-                algorithmic_bytes_per_launch=int(ADJ_BYTES_PER_CELL[dom] * N * N), traffic=None)
+                algorithmic_bytes_per_launch=int(bytes_l), traffic=None,
+                kernel_ms_per_step={k: round(v[1], 1) for k, v in cand.items()})
     line = dict(
         metric=ADJOINT_METRIC, value=value, unit="cell-steps/s", n_gpus=world, steps=S_, warmup=args.warmup,
         ms_per_step=ms / S_, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-        data="synthetic", config=adjoint_config(w, world), g_kappa=r["g_kappa"],
-        group_ms_per_step={k: round(v, 3) for k, v in per.items()}, roofline=roof,
-        # per step: forward 6 per iteration (explicit part, residual, x and y
-        # sweeps, finalize, film statistics); reverse per iteration 1 tables,
-        # 2 band, 2 solve, 2 line and 1 D derivative, 3 Laplacian-transpose
-        # and 2 axpy kernels, then 1 axpy, 1 D derivative, 1 Laplacian-transpose
-        gpu_launches=S_ * (19 * K + 3),
-        e2e=dict(value=job_rate(dist, N * N * S_, ms_e2e), unit="cell-steps/s",
-                 h2d_bytes_per_step=2 * N * N * 8, d2h_bytes_per_step=N * N * 8),
+        data="synthetic", config=adjoint_config(w, world), g_theta=r["g_theta"], g_kappa=r["g_kappa"],
+        checkpoints=dict(every=tinfo["every"], count=tinfo["checkpoints"], tape_bytes=tinfo["bytes"]),
+        group_ms_per_step={k: round(v, 1) for k, v in per.items()}, roofline=roof,
+        # the forward kernels counted by the context; the reverse per step
+        # and iteration 1 tables, 2 band, 2 solve, 2 line and 1 D derivative,
+        # 3 Laplacian-transpose and 2 axpy kernels, then 1 axpy, 1 D
+        # derivative and 1 Laplacian-transpose; plus the loss cotangent
+        gpu_launches=tim["launches"] + S_ * ns * (13 * K + 3),
+        e2e=dict(value=job_rate(dist, N * N * ns * S_, ms_e2e), unit="cell-steps/s",
+                 h2d_bytes_per_step=N * N * 8, d2h_bytes_per_step=N * N * 8),
     )
     cs = clocks.summary()
     line["clocks"] = dict(sm_mhz=cs["sm_mhz"], sm_max_mhz=cs["sm_max_mhz"], reasons=cs["reasons"])
@@ -758,8 +786,8 @@ def run_adjoint(args, w):
         import oracle as O
         el, n = oracle_adjoint_sample(w)
         line["cpu_baseline"] = dict(value=n * n / el, unit="cell-steps/s", cores=O.num_threads(), kind="oracle",
-                                    sample=(f"the oracle's adjoint of a {n}x{n} sample (complex-step Jacobian: "
-                                            f"{n * n} forward steps), {el:.1f} s"))
+                                    sample=(f"the oracle's adjoint of one step of a {n}x{n} sample "
+                                            f"(complex-step Jacobian: {n * n} forward steps), {el:.1f} s"))
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -768,7 +796,7 @@ def run_adjoint(args, w):
 
 def reference_adjoint(args, w):
     """The oracle's adjoint as the reference arm: each step one oracle adjoint
-    of a 12 x 12 sample of the workload."""
+    of one time step of a 12 x 12 sample of the workload (cell-steps/s)."""
     if int(os.environ.get("RANK", "0")) != 0:
         return
     import oracle as O

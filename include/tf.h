@@ -282,7 +282,7 @@ int tf_residual_noalloc(const tf_params* p, void* stream, const double* h_k,
  * g_h: device output grid (not aliasing h_old, g or h_new); g_kappa,
  * g_theta: host outputs or NULL (g_theta = g_kappa dkappa/dtheta_c when
  * kappa was derived from the contact angle, else 0).  K: 1..64.
- * Workspace (3K + 12 grids) is allocated on first use and kept by the
+ * Workspace (3K + 19 grids) is allocated on first use and kept by the
  * context.  Synchronises the context's stream.  Returns TF_OK, TF_ERR_ARG,
  * TF_ERR_NOMEM or TF_ERR_CUDA (or a forward iteration's error).         */
 int tf_adjoint_step(tf_ctx* ctx, const double* h_old, double dt, int K, const double* g,
@@ -294,6 +294,55 @@ int tf_adjoint_step(tf_ctx* ctx, const double* h_old, double dt, int K, const do
  * coefficient derivatives, D derivatives, the copy of the kappa partial
  * sums.  n: entries wanted (up to 7).                                     */
 int tf_adjoint_timing(double* ms, int n);
+
+/* ---- adjoint of a trajectory of fixed steps, with checkpoints ----------
+ * The map u^0 -> u^N of N time steps, each the fixed-iteration step above
+ * (K Newton iterations at step size dt), and its reverse for a cotangent g
+ * of u^N: g_h0 = (du^N/du^0)^T g and g_kappa = (du^N/dkappa)^T g, the
+ * chain rule over the steps (Sec. Numerical Method; the adjoint of each step
+ * is tf_adjoint_step's).  Uniform checkpoints: the forward keeps u^n at
+ * n = 0, e, 2e, ... (ceil(N/e) grids); the reverse runs one segment of e
+ * steps again from its checkpoint, keeping each step's iterates (u_k, w_k,
+ * v_k: 3K grids), and reverses them, so memory is ceil(N/e) + 3Ke + 2 grids
+ * (O(sqrt N) at e = ceil(sqrt(N))) for two forward passes and one reverse.
+ * Every segment recomputes exactly the forward's bits (the same kernels and
+ * order), so the result does not depend on e.  The context must satisfy
+ * tf_adjoint_step's conditions.                                          */
+typedef struct tf_tape tf_tape;
+
+/* A tape for nsteps >= 1 steps of K (1..64) iterations at dt > 0 on the
+ * context's grid, checkpoint interval every (0: ceil(sqrt(nsteps)); else
+ * 1..nsteps).  Allocates ceil(nsteps/every) + 3 K every + 2 device grids
+ * (the reverse also uses the context's adjoint workspace).  The
+ * context must outlive the tape.  Returns TF_OK, TF_ERR_ARG or
+ * TF_ERR_NOMEM.                                                           */
+int tf_tape_create(tf_ctx* ctx, int nsteps, int K, double dt, int every, tf_tape** out);
+void tf_tape_destroy(tf_tape* tape);
+
+/* every: the interval in use; checkpoints: ceil(nsteps/every); bytes: the
+ * tape's device memory; forward_done: 1 once tf_tape_forward succeeded.    */
+int tf_tape_info(const tf_tape* tape, int* every, int* checkpoints, size_t* bytes, int* forward_done);
+
+/* Runs the N steps from h0 (device grid), keeping the checkpoints, and
+ * writes u^N to hT (device grid, may equal h0; not inside the tape).
+ * Returns TF_OK, a step failure TF_STEP_NONPOSITIVE / TF_STEP_ZERO_PIVOT of
+ * the first step that had one (the trajectory left the model's domain; the
+ * tape is then unusable), or a negative error.  Synchronises the stream.   */
+int tf_tape_forward(tf_tape* tape, const double* h0, double* hT);
+
+/* The reverse of the last forward: g (device grid, the cotangent of u^N),
+ * g_h0 (device output grid, may equal g), g_kappa, g_theta (host outputs or
+ * NULL; g_theta as in tf_adjoint_step).  Sums over the steps are taken in a
+ * fixed order, so repeated calls give the same bits.  Returns TF_OK,
+ * TF_ERR_ARG (no forward yet) or a negative error.                         */
+int tf_tape_backward(tf_tape* tape, const double* g, double* g_h0, double* g_kappa, double* g_theta);
+
+/* Kernel time (ms, CUDA events) of the tape's last forward and backward:
+ * [0] forward steps, [1] the segments' steps run again with their
+ * iterates, then the seven tf_adjoint_timing groups summed over the reverse
+ * steps (the "forward" group stays 0: the iterates come from [1]).  n: up
+ * to 9.                                                                  */
+int tf_tape_timing(const tf_tape* tape, double* ms, int n);
 
 /* ---- radial Fourier analysis of a film (App. Radial Fourier Transform) ---
  * The dominant wavenumber of a film pattern, all steps on the GPU, in the

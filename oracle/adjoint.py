@@ -20,7 +20,9 @@ no-flux walls, the line bands of the direction split, dense solves), and
 complex-step differentiation of it: for a real-analytic map F,
 Im F(x + i eps e_j) / eps is the j-th column of its Jacobian to rounding
 (no subtraction, eps = 1e-30).  The full Jacobian is formed column by column
-and transposed, so the oracle shares nothing with a reverse sweep.  Only
+and transposed, so the oracle shares nothing with a reverse sweep.  A
+trajectory of N such steps chains the steps' transposed Jacobians in
+reverse order (its pin: the complex-step Jacobian of the whole trajectory).  Only
 the power-law and linear models are covered (the maps whose complex
 extension is a plain rational function).  Every forward function is pinned
 against the C oracle on real inputs; the derivatives against central finite
@@ -157,6 +159,41 @@ def vjp(M: Model, un, dt, K, g):
     J, Jk = jacobian(M, un, dt, K)
     g = np.asarray(g, dtype=np.float64).ravel()
     return (J.T @ g).reshape(np.shape(un)), float(Jk @ g)
+
+
+def trajectory(M: Model, h0, dt, K, nsteps, kappa=None):
+    """States u^0 .. u^N of N fixed steps (list of N + 1 grids)."""
+    hs = [np.asarray(h0)]
+    for _ in range(nsteps):
+        hs.append(step_fixed(M, hs[-1], dt, K, kappa))
+    return hs
+
+
+def trajectory_vjp(M: Model, h0, dt, K, nsteps, g):
+    """(g^T d u^N/d u^0, g^T d u^N/d kappa) by the chain rule over the steps:
+    the cotangent passes through each step's transposed Jacobian in reverse
+    order, and the kappa parts of the steps add."""
+    hs = trajectory(M, np.asarray(h0, dtype=np.float64), dt, K, nsteps)
+    gc = np.asarray(g, dtype=np.float64)
+    gk = 0.0
+    for n in range(nsteps - 1, -1, -1):
+        gc, k = vjp(M, hs[n], dt, K, gc)
+        gk += k
+    return gc, gk
+
+
+def trajectory_jacobian(M: Model, h0, dt, K, nsteps):
+    """Full Jacobian of u^N with respect to u^0 and the kappa column, by
+    complex steps through the whole trajectory (no chain rule)."""
+    h0 = np.asarray(h0, dtype=np.float64)
+    N = h0.size
+    J = np.empty((N, N))
+    for j in range(N):
+        e = np.zeros(N, dtype=np.complex128)
+        e[j] = 1j * EPS_CS
+        J[:, j] = trajectory(M, h0 + e.reshape(h0.shape), dt, K, nsteps)[-1].imag.ravel() / EPS_CS
+    hk = trajectory(M, h0.astype(np.complex128), dt, K, nsteps, kappa=M.kappa + 1j * EPS_CS)[-1]
+    return J, hk.imag.ravel() / EPS_CS
 
 
 def dkappa_dtheta(theta_c: float, b: float, n: int, m: int) -> float:

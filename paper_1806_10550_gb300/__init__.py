@@ -9,7 +9,10 @@ CPU fallback: without the built library or a CUDA device every call raises.
 Functions carry the names of the C ABI: ``tf_params_default``, ``tf_init``,
 ``tf_destroy``, ``tf_residual``, ``tf_newton_iteration``,
 ``tf_newton_adi_step``, ``tf_advance``, ``tf_ensemble_advance``, ``tf_strerror``,
-``tf_adjoint_step`` (the reverse of the fixed-iteration step), and for the
+``tf_adjoint_step`` (the reverse of the fixed-iteration step), the tape of a
+checkpointed trajectory ``tf_tape_create``, ``tf_tape_forward``,
+``tf_tape_backward``, ``tf_tape_info``, ``tf_tape_timing``,
+``tf_tape_destroy``, and for the
 radial Fourier analysis ``tf_spectrum_params_default``,
 ``tf_spectrum_plan_create``, ``tf_spectrum_run``, ``tf_spectrum_plan_info``,
 ``tf_spectrum_timing``, ``tf_spectrum_plan_destroy``.
@@ -138,6 +141,14 @@ def library(build_if_missing: bool = True):
     L.tf_timing_get.argtypes = [vp, C.POINTER(TfTiming)]
     L.tf_adjoint_step.argtypes = [vp, vp, dp, C.c_int, vp, vp, vp, C.POINTER(dp), C.POINTER(dp)]
     L.tf_adjoint_timing.argtypes = [C.POINTER(dp), C.c_int]
+    L.tf_tape_create.argtypes = [vp, C.c_int, C.c_int, dp, C.c_int, C.POINTER(vp)]
+    L.tf_tape_destroy.argtypes = [vp]
+    L.tf_tape_destroy.restype = None
+    L.tf_tape_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t),
+                               C.POINTER(C.c_int)]
+    L.tf_tape_forward.argtypes = [vp, vp, vp]
+    L.tf_tape_backward.argtypes = [vp, vp, vp, C.POINTER(dp), C.POINTER(dp)]
+    L.tf_tape_timing.argtypes = [vp, C.POINTER(dp), C.c_int]
     L.tf_spectrum_params_default.argtypes = [C.POINTER(TfSpectrumParams)]
     L.tf_spectrum_params_default.restype = None
     L.tf_spectrum_plan_create.argtypes = [C.c_int, C.c_int, dp, C.POINTER(TfSpectrumParams), vp,
@@ -149,7 +160,8 @@ def library(build_if_missing: bool = True):
     L.tf_spectrum_timing.argtypes = [vp, C.POINTER(dp), C.c_int]
     for f in ("tf_init", "tf_residual", "tf_newton_iteration", "tf_newton_adi_step", "tf_advance",
               "tf_ensemble_advance", "tf_timing_enable", "tf_timing_get", "tf_adjoint_step",
-              "tf_adjoint_timing",
+              "tf_adjoint_timing", "tf_tape_create", "tf_tape_info", "tf_tape_forward",
+              "tf_tape_backward", "tf_tape_timing",
               "tf_spectrum_plan_create",
               "tf_spectrum_plan_info", "tf_spectrum_run", "tf_spectrum_timing"):
         getattr(L, f).restype = C.c_int
@@ -367,6 +379,111 @@ def tf_adjoint_timing() -> dict:
     ms = (C.c_double * len(ADJOINT_GROUPS))()
     _check(library().tf_adjoint_timing(ms, len(ADJOINT_GROUPS)), "tf_adjoint_timing")
     return dict(zip(ADJOINT_GROUPS, list(ms)))
+
+
+TAPE_GROUPS = ("tape_forward", "recompute") + ADJOINT_GROUPS
+
+
+class Tape:
+    """Owns one ``tf_tape``: ``nsteps`` fixed steps of ``K`` iterations at
+    ``dt`` with a checkpoint every ``every`` steps (0: ceil(sqrt(nsteps))).
+    Keeps its context alive."""
+
+    def __init__(self, ctx: Context, nsteps: int, K: int, dt: float, every: int = 0):
+        h = C.c_void_p()
+        _check(library().tf_tape_create(ctx.handle, int(nsteps), int(K), float(dt), int(every),
+                                        C.byref(h)), "tf_tape_create")
+        self.handle, self.ctx = h, ctx
+        self.nsteps, self.K, self.dt = int(nsteps), int(K), float(dt)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            library().tf_tape_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tf_tape_create(ctx: Context, nsteps: int, K: int, dt: float, every: int = 0) -> Tape:
+    return Tape(ctx, nsteps, K, dt, every)
+
+
+def tf_tape_destroy(tape: Tape):
+    tape.close()
+
+
+def tf_tape_info(tape: Tape) -> dict:
+    e, n, f = C.c_int(), C.c_int(), C.c_int()
+    b = C.c_size_t()
+    _check(library().tf_tape_info(tape.handle, C.byref(e), C.byref(n), C.byref(b), C.byref(f)),
+           "tf_tape_info")
+    return dict(every=e.value, checkpoints=n.value, bytes=b.value, forward_done=bool(f.value))
+
+
+def tf_tape_forward(tape: Tape, h0, hT=None):
+    """u^N of the tape's trajectory from ``h0`` (returns ``hT``)."""
+    torch = _torch()
+    if hT is None:
+        hT = torch.empty_like(h0)
+    r = library().tf_tape_forward(tape.handle, tape.ctx.ptr(h0, "h0"), tape.ctx.ptr(hT, "hT"))
+    if r > 0:
+        raise RuntimeError(f"tf_tape_forward: step failure {r} (the trajectory left the model's domain)")
+    _check(r, "tf_tape_forward")
+    return hT
+
+
+def tf_tape_backward(tape: Tape, g, g_h0=None) -> dict:
+    """Reverse of the last forward for the cotangent ``g`` of u^N: dict with
+    ``g_h0`` (CUDA tensor), ``g_kappa`` and ``g_theta``."""
+    torch = _torch()
+    if g_h0 is None:
+        g_h0 = torch.empty_like(g)
+    gk, gt = C.c_double(), C.c_double()
+    _check(library().tf_tape_backward(tape.handle, tape.ctx.ptr(g, "g"), tape.ctx.ptr(g_h0, "g_h0"),
+                                      C.byref(gk), C.byref(gt)), "tf_tape_backward")
+    return dict(g_h0=g_h0, g_kappa=gk.value, g_theta=gt.value)
+
+
+def tf_tape_timing(tape: Tape) -> dict:
+    """Kernel time (ms) of the tape's last forward and backward by group."""
+    ms = (C.c_double * len(TAPE_GROUPS))()
+    _check(library().tf_tape_timing(tape.handle, ms, len(TAPE_GROUPS)), "tf_tape_timing")
+    return dict(zip(TAPE_GROUPS, list(ms)))
+
+
+def trajectory(h0, theta, params: TfParams, dt: float, K: int, nsteps: int, every: int = 0):
+    """u^N after ``nsteps`` fixed steps of ``K`` iterations from ``h0``, as a
+    differentiable function of the film ``h0`` and of the contact angle
+    ``theta`` (radians, a float64 tensor; kappa = (1 - cos theta)/(b M) of the
+    power law).  ``params``: an FP64 power-law parameter set (its kappa and
+    contact angle are replaced).  The forward keeps ceil(N/every)
+    checkpoints; the backward recomputes one segment at a time and chains the
+    steps' adjoints (tf_tape_backward)."""
+    torch = _torch()
+
+    class _Trajectory(torch.autograd.Function):
+        @staticmethod
+        def forward(actx, x, th):
+            p = TfParams.from_buffer_copy(params)
+            p.kappa = 0.0
+            p.contact_angle = float(th)
+            ctx = Context(p)
+            tape = Tape(ctx, nsteps, K, dt, every)
+            actx.tape = tape
+            actx.theta_like = th
+            return tf_tape_forward(tape, x.detach().contiguous())
+
+        @staticmethod
+        def backward(actx, g):
+            r = tf_tape_backward(actx.tape, g.contiguous())
+            th = actx.theta_like
+            return r["g_h0"], torch.tensor(r["g_theta"], dtype=th.dtype, device=th.device)
+
+    return _Trajectory.apply(h0, theta)
 
 
 def tf_timing_enable(ctx: Context, on: bool = True):

@@ -453,6 +453,15 @@ struct GroupTimer {
   }
 };
 
+// dkappa/dtheta_c when kappa = (1 - cos theta_c)/(b M) was derived from the
+// contact angle (power law), M = (n - m)/((m - 1)(n - 1)): sin theta_c/(b M);
+// 0 when kappa was given.
+double dkappa_dtheta(const tf_ctx& c) {
+  if (c.p.kappa > 0.0 || c.p.model != TF_MODEL_POWERLAW) return 0.0;
+  const double Mf = (double)(c.p.n - c.p.m) / ((double)(c.p.m - 1) * (double)(c.p.n - 1));
+  return sin(c.p.contact_angle) / (c.p.b * Mf);
+}
+
 double g_adj_ms[kGroups];  // last call's group times (the library's callers
                            // serialise adjoint calls per process for timing)
 
@@ -464,70 +473,80 @@ extern "C" int tf_adjoint_timing(double* ms, int n) {
   return TF_OK;
 }
 
-extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K, const double* g,
-                               double* h_new, double* g_h, double* g_kappa, double* g_theta) {
-  if (!c || !h_old || !g || !g_h || K < 1 || K > 64 || !(dt > 0.0) || !isfinite(dt)) return TF_ERR_ARG;
-  if (c->p.precision != TF_FP64) return TF_ERR_ARG;
-  if (c->p.model != TF_MODEL_POWERLAW && c->p.model != TF_MODEL_LINEAR) return TF_ERR_ARG;
-  if (g_h == h_old || g_h == g || (h_new && (h_new == h_old || h_new == g_h))) return TF_ERR_ARG;
-  const int nx = c->p.nx, ny = c->p.ny;
+namespace {
+
+// Reverse workspace, kept by the context: band (5), lam_y, lam_x, bbar,
+// scratch (4; its first grid is also Lbar), tables (7), the kappa partial
+// sums (one per 128-cell block of a row, per derivative launch) and, when
+// asked for, room for one step's iterates (u_1..u_K, w_0..w_{K-1},
+// v_0..v_{K-1}).
+struct RevWork {
+  double *band, *lam_y, *lam_x, *bbar, *scratch, *part, *iter;
+  Tables Tb;
+  int npart, nkl;
+};
+
+int rev_workspace(tf_ctx* c, int K, bool iterates, RevWork* w) {
   const size_t N = c->N;
-  cudaStream_t st = c->stream;
-  // kappa partial sums: one per 128-cell block of a row, per derivative launch
-  const int npart = ((nx + kVjpThreads - 1) / kVjpThreads) * ny, nkl = 3 * K + 1;
-  // workspace: u_1..u_K, w_0..w_{K-1}, v_0..v_{K-1}, band (5), lam_y, lam_x,
-  // bbar, scratch (4; its first grid is also Lbar), tables (7), kappa partials
-  const size_t grids = (size_t)3 * K + 5 + 3 + 4 + 7;
-  const size_t bytes = grids * N * sizeof(double) + (size_t)npart * nkl * sizeof(double);
+  w->npart = ((c->p.nx + kVjpThreads - 1) / kVjpThreads) * c->p.ny;
+  w->nkl = 3 * K + 1;
+  const size_t rev = 19 * N + (size_t)w->npart * w->nkl;
+  const size_t bytes = (rev + (iterates ? (size_t)3 * K * N : 0)) * sizeof(double);
   if (c->adj_bytes < bytes) {
     if (c->adj_ws) cudaFree(c->adj_ws);
     c->adj_ws = nullptr;
     c->adj_bytes = 0;
-    if (cudaMalloc(&c->adj_ws, bytes) != cudaSuccess) return TF_ERR_NOMEM;
+    if (cudaMalloc(&c->adj_ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return TF_ERR_NOMEM;
+    }
     c->adj_bytes = bytes;
   }
   double* base = (double*)c->adj_ws;
-  std::vector<double*> U(K + 1), W(K), V(K);
-  U[0] = const_cast<double*>(h_old);
-  size_t off = 0;
-  for (int k = 1; k <= K; ++k, off += N) U[k] = base + off;
-  for (int k = 0; k < K; ++k, off += N) W[k] = base + off;
-  for (int k = 0; k < K; ++k, off += N) V[k] = base + off;
-  double* band = base + off;
-  off += 5 * N;
-  double* lam_y = base + off;
-  off += N;
-  double* lam_x = base + off;
-  off += N;
-  double* bbar = base + off;
-  off += N;
-  double* scratch = base + off;
-  off += 4 * N;
-  Tables Tb;
-  Tb.f0 = base + off;
-  Tb.f1 = Tb.f0 + N;
-  Tb.d0 = Tb.f1 + N;
-  Tb.d1 = Tb.d0 + N;
-  Tb.e0 = Tb.d1 + N;
-  Tb.e1 = Tb.e0 + N;
-  Tb.lap = Tb.e1 + N;
-  off += 7 * N;
-  double* part = base + off;  // nkl x npart kappa partials
-  double* Lbar = scratch;      // free once a transposed solve has finished
+  w->band = base;
+  w->lam_y = base + 5 * N;
+  w->lam_x = base + 6 * N;
+  w->bbar = base + 7 * N;
+  w->scratch = base + 8 * N;
+  w->Tb.f0 = base + 12 * N;
+  w->Tb.f1 = w->Tb.f0 + N;
+  w->Tb.d0 = w->Tb.f1 + N;
+  w->Tb.d1 = w->Tb.d0 + N;
+  w->Tb.e0 = w->Tb.d1 + N;
+  w->Tb.e1 = w->Tb.e0 + N;
+  w->Tb.lap = w->Tb.e1 + N;
+  w->part = base + 19 * N;
+  w->iter = iterates ? base + rev : nullptr;
+  return TF_OK;
+}
 
-  GroupTimer T;
-  T.st = st;
-  // forward: K iterations of the FP64 path, keeping u_k, w_k, v_k
-  const int tf0 = T.begin(kGForward);
+// K iterations of the FP64 path from u^n = U[0], keeping u_1..u_K in
+// U[1..K] and w_k, v_k (tf_newton_iteration: bit-identical to the forward
+// step, whose first iteration is fused with the explicit part).
+int adj_forward(tf_ctx* c, double dt, int K, double* const* U, double* const* W, double* const* V) {
   for (int k = 0; k < K; ++k) {
     tf_step_info info;
-    const int r = tf_newton_iteration(c, U[k], h_old, dt, W[k], V[k], U[k + 1], &info);
+    const int r = tf_newton_iteration(c, U[k], U[0], dt, W[k], V[k], U[k + 1], &info);
     if (r < 0) return r;
   }
-  T.end(tf0);
-  if (h_new && cudaMemcpyAsync(h_new, U[K], N * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-    return TF_ERR_CUDA;
+  return TF_OK;
+}
 
+// The reverse of one step from its iterates (U[0] = u^n, U[1..K-1], W, V):
+// g_h = (du^K/du^n)^T g; *kbar receives the step's kappa cotangent (partial
+// sums added on the host in a fixed order).  Synchronises the stream.
+int adj_reverse(tf_ctx* c, const RevWork& R, const double* const* U, const double* const* W,
+                const double* const* V, double dt, int K, const double* g, double* g_h, double* kbar,
+                GroupTimer& T) {
+  const int nx = c->p.nx, ny = c->p.ny;
+  const size_t N = c->N;
+  cudaStream_t st = c->stream;
+  const double* h_old = U[0];
+  double *band = R.band, *lam_y = R.lam_y, *lam_x = R.lam_x, *bbar = R.bbar, *scratch = R.scratch;
+  double* part = R.part;
+  double* Lbar = scratch;  // free once a transposed solve has finished
+  const Tables& Tb = R.Tb;
+  const int npart = R.npart, nkl = R.nkl;
   AdjK M;
   M.nx = nx;
   M.ny = ny;
@@ -608,18 +627,241 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
   }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return TF_ERR_CUDA;
   if (T.err != cudaSuccess) return TF_ERR_CUDA;
-  T.collect(g_adj_ms);
-  double kbar = 0.0;
-  for (double v : hp) kbar += v;
-  if (g_kappa) *g_kappa = kbar;
-  if (g_theta) {
-    // kappa = (1 - cos theta_c)/(b M) when derived from the contact angle
-    double dk = 0.0;
-    if (c->p.kappa <= 0.0 && M.model == TF_MODEL_POWERLAW) {
-      const double Mf = (double)(c->p.n - c->p.m) / ((double)(c->p.m - 1) * (double)(c->p.n - 1));
-      dk = sin(c->p.contact_angle) / (c->p.b * Mf);
-    }
-    *g_theta = kbar * dk;
+  double ks = 0.0;
+  for (double v : hp) ks += v;
+  *kbar = ks;
+  return TF_OK;
+}
+
+}  // namespace
+
+extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K, const double* g,
+                               double* h_new, double* g_h, double* g_kappa, double* g_theta) {
+  if (!c || !h_old || !g || !g_h || K < 1 || K > 64 || !(dt > 0.0) || !isfinite(dt)) return TF_ERR_ARG;
+  if (c->p.precision != TF_FP64) return TF_ERR_ARG;
+  if (c->p.model != TF_MODEL_POWERLAW && c->p.model != TF_MODEL_LINEAR) return TF_ERR_ARG;
+  if (g_h == h_old || g_h == g || (h_new && (h_new == h_old || h_new == g_h))) return TF_ERR_ARG;
+  const size_t N = c->N;
+  RevWork R;
+  int r = rev_workspace(c, K, true, &R);
+  if (r) return r;
+  std::vector<double*> U(K + 1), W(K), V(K);
+  U[0] = const_cast<double*>(h_old);
+  for (int k = 0; k < K; ++k) {
+    U[k + 1] = R.iter + (size_t)k * N;
+    W[k] = R.iter + (size_t)(K + k) * N;
+    V[k] = R.iter + (size_t)(2 * K + k) * N;
   }
+  GroupTimer T;
+  T.st = c->stream;
+  const int tf0 = T.begin(kGForward);
+  r = adj_forward(c, dt, K, U.data(), W.data(), V.data());
+  if (r) return r;
+  T.end(tf0);
+  if (h_new && cudaMemcpyAsync(h_new, U[K], N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+    return TF_ERR_CUDA;
+  double kbar = 0.0;
+  r = adj_reverse(c, R, U.data(), W.data(), V.data(), dt, K, g, g_h, &kbar, T);
+  if (r) return r;
+  T.collect(g_adj_ms);
+  if (g_kappa) *g_kappa = kbar;
+  if (g_theta) *g_theta = kbar * dkappa_dtheta(*c);
+  return TF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Trajectories: N fixed steps with uniform checkpoints.  The forward keeps
+// u^n at n = 0, e, 2e, ...; the reverse takes the segments last to first,
+// runs a segment's e steps again from its checkpoint keeping every step's
+// iterates (the same bits as the forward: tf_newton_iteration equals the
+// fused step), and reverses them, the cotangent ping-ponging between two
+// grids.
+
+struct tf_tape {
+  tf_ctx* c;
+  int nsteps, K, every, nckpt;
+  double dt;
+  double* mem;  // nckpt checkpoints, every x 3K iterate grids, 2 cotangents
+  size_t bytes;
+  bool forward_done;
+  double ms[2 + kGroups];
+};
+
+namespace {
+
+double* tape_ckpt(tf_tape* t, int s) { return t->mem + (size_t)s * t->c->N; }
+// grid q (0 .. 3K-1) of segment step i: u_1..u_K, w_0..w_{K-1}, v_0..v_{K-1}
+double* tape_iter(tf_tape* t, int i, int q) {
+  return t->mem + ((size_t)t->nckpt + (size_t)i * 3 * t->K + q) * t->c->N;
+}
+double* tape_cot(tf_tape* t, int i) {
+  return t->mem + ((size_t)t->nckpt + (size_t)t->every * 3 * t->K + i) * t->c->N;
+}
+
+// Event-timed region on the context's stream, added to *acc.
+struct RegionTimer {
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  explicit RegionTimer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  void stop(double* acc) {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) *acc += ms;
+  }
+  ~RegionTimer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+}  // namespace
+
+extern "C" int tf_tape_create(tf_ctx* c, int nsteps, int K, double dt, int every, tf_tape** out) {
+  if (!out) return TF_ERR_ARG;
+  *out = nullptr;
+  if (!c || nsteps < 1 || K < 1 || K > 64 || !(dt > 0.0) || !isfinite(dt) || every < 0 || every > nsteps)
+    return TF_ERR_ARG;
+  if (c->p.precision != TF_FP64) return TF_ERR_ARG;
+  if (c->p.model != TF_MODEL_POWERLAW && c->p.model != TF_MODEL_LINEAR) return TF_ERR_ARG;
+  if (every == 0) {
+    every = (int)ceil(sqrt((double)nsteps));
+    while ((long long)(every - 1) * (every - 1) >= nsteps) --every;  // sqrt rounding
+    while ((long long)every * every < nsteps) ++every;
+  }
+  tf_tape* t = (tf_tape*)calloc(1, sizeof(tf_tape));
+  if (!t) return TF_ERR_NOMEM;
+  t->c = c;
+  t->nsteps = nsteps;
+  t->K = K;
+  t->dt = dt;
+  t->every = every;
+  t->nckpt = (nsteps + every - 1) / every;
+  const size_t grids = (size_t)t->nckpt + (size_t)every * 3 * K + 2;
+  t->bytes = grids * c->N * sizeof(double);
+  if (cudaMalloc(&t->mem, t->bytes) != cudaSuccess) {
+    cudaGetLastError();
+    free(t);
+    return TF_ERR_NOMEM;
+  }
+  *out = t;
+  return TF_OK;
+}
+
+extern "C" void tf_tape_destroy(tf_tape* t) {
+  if (!t) return;
+  cudaFree(t->mem);
+  free(t);
+}
+
+extern "C" int tf_tape_info(const tf_tape* t, int* every, int* checkpoints, size_t* bytes, int* forward_done) {
+  if (!t) return TF_ERR_ARG;
+  if (every) *every = t->every;
+  if (checkpoints) *checkpoints = t->nckpt;
+  if (bytes) *bytes = t->bytes;
+  if (forward_done) *forward_done = t->forward_done ? 1 : 0;
+  return TF_OK;
+}
+
+extern "C" int tf_tape_timing(const tf_tape* t, double* ms, int n) {
+  if (!t || !ms || n < 1) return TF_ERR_ARG;
+  for (int g = 0; g < n && g < 2 + kGroups; ++g) ms[g] = t->ms[g];
+  return TF_OK;
+}
+
+extern "C" int tf_tape_forward(tf_tape* t, const double* h0, double* hT) {
+  if (!t || !h0 || !hT) return TF_ERR_ARG;
+  tf_ctx& c = *t->c;
+  const size_t gb = c.N * sizeof(double);
+  const char* lo = (const char*)t->mem;
+  const char* hi = lo + t->bytes;
+  if (((const char*)hT >= lo && (const char*)hT < hi) || ((const char*)h0 >= lo && (const char*)h0 < hi))
+    return TF_ERR_ARG;
+  t->forward_done = false;
+  t->ms[0] = 0.0;
+  cudaStream_t st = c.stream;
+  RegionTimer R(st);
+  // u^n is written straight into its checkpoint when n % e == 0 (u^0 is
+  // copied there), else into one of two scratch grids (the cotangent grids,
+  // free until the reverse); the last step writes hT.
+  double* scr[2] = {tape_cot(t, 0), tape_cot(t, 1)};
+  if (cudaMemcpyAsync(tape_ckpt(t, 0), h0, gb, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return TF_ERR_CUDA;
+  const double* cur = tape_ckpt(t, 0);
+  for (int n = 0; n < t->nsteps; ++n) {
+    double* nxt;
+    if (n + 1 == t->nsteps)
+      nxt = hT;
+    else if ((n + 1) % t->every == 0)
+      nxt = tape_ckpt(t, (n + 1) / t->every);
+    else
+      nxt = cur == scr[0] ? scr[1] : scr[0];
+    const int r = tf::fixed_step(c, cur, nxt, t->dt, t->K);
+    if (r != TF_OK) return r;
+    cur = nxt;
+  }
+  R.stop(&t->ms[0]);
+  t->forward_done = true;
+  return TF_OK;
+}
+
+extern "C" int tf_tape_backward(tf_tape* t, const double* g, double* g_h0, double* g_kappa, double* g_theta) {
+  if (!t || !g || !g_h0 || !t->forward_done) return TF_ERR_ARG;
+  tf_ctx& c = *t->c;
+  const int K = t->K;
+  const size_t gb = c.N * sizeof(double);
+  cudaStream_t st = c.stream;
+  for (int k = 1; k < 2 + kGroups; ++k) t->ms[k] = 0.0;
+  RevWork Rw;
+  int r = rev_workspace(&c, K, false, &Rw);
+  if (r) return r;
+  double* cot[2] = {tape_cot(t, 0), tape_cot(t, 1)};
+  if (cudaMemcpyAsync(cot[0], g, gb, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return TF_ERR_CUDA;
+  int cc = 0;
+  double kbar = 0.0;
+  std::vector<double*> U((size_t)t->every * (K + 1)), W((size_t)t->every * K), V((size_t)t->every * K);
+  for (int s = t->nckpt - 1; s >= 0; --s) {
+    const int n0 = s * t->every, len = (n0 + t->every < t->nsteps ? n0 + t->every : t->nsteps) - n0;
+    // the segment's iterates: step i starts from u^{n0+i} (the checkpoint,
+    // then the previous step's u_K)
+    for (int i = 0; i < len; ++i) {
+      double** Ui = &U[(size_t)i * (K + 1)];
+      Ui[0] = i == 0 ? tape_ckpt(t, s) : U[(size_t)(i - 1) * (K + 1) + K];
+      for (int k = 0; k < K; ++k) {
+        Ui[k + 1] = tape_iter(t, i, k);
+        W[(size_t)i * K + k] = tape_iter(t, i, K + k);
+        V[(size_t)i * K + k] = tape_iter(t, i, 2 * K + k);
+      }
+    }
+    {
+      RegionTimer R(st);
+      for (int i = 0; i < len; ++i) {
+        r = adj_forward(&c, t->dt, K, &U[(size_t)i * (K + 1)], &W[(size_t)i * K], &V[(size_t)i * K]);
+        if (r) return r;
+      }
+      R.stop(&t->ms[1]);
+    }
+    for (int i = len - 1; i >= 0; --i) {
+      GroupTimer T;
+      T.st = st;
+      double gk = 0.0;
+      r = adj_reverse(&c, Rw, &U[(size_t)i * (K + 1)], &W[(size_t)i * K], &V[(size_t)i * K], t->dt, K, cot[cc],
+                      cot[cc ^ 1], &gk, T);
+      if (r) return r;
+      double ms[kGroups];
+      T.collect(ms);
+      for (int k = 0; k < kGroups; ++k) t->ms[2 + k] += ms[k];
+      cc ^= 1;
+      kbar += gk;
+    }
+  }
+  if (cudaMemcpyAsync(g_h0, cot[cc], gb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return TF_ERR_CUDA;
+  if (g_kappa) *g_kappa = kbar;
+  if (g_theta) *g_theta = kbar * dkappa_dtheta(c);
   return TF_OK;
 }

@@ -316,6 +316,15 @@ template <class T> int dalloc(T** p, size_t bytes) {
 
 }  // namespace
 
+namespace tf {
+int fixed_step(tf_ctx& c, const double* h_old, double* h_new, double dt, int K) {
+  tf_step_info info;
+  const int s = step(c, h_old, h_new, dt, K, &info);
+  if (s < 0) return s;
+  return s == TF_STEP_CONVERGED ? TF_OK : s;
+}
+}  // namespace tf
+
 extern "C" {
 
 void tf_params_default(tf_params* p) {

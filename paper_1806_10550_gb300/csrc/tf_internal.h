@@ -35,6 +35,15 @@ extern const Ops ops_f32b;
 
 }  // namespace tf
 
+namespace tf {
+
+// One time step of exactly K Newton iterations at dt (the step of
+// tf_newton_adi_step with its fixed-iteration override): TF_OK, a step
+// failure (TF_STEP_NONPOSITIVE, TF_STEP_ZERO_PIVOT) or a negative error.
+int fixed_step(tf_ctx& c, const double* h_old, double* h_new, double dt, int K);
+
+}  // namespace tf
+
 struct tf_ctx {
   tf_params p;
   tf::ModelK mk;

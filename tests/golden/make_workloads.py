@@ -17,7 +17,9 @@ theta_c = 20 deg, M = 1/2, C = 1, h0 = 1):
             exactly 3 Newton iterations at dt = 0.01, where 3 iterations
             bring max|v/u| to 8e-5 (10 iterations: 7e-11).  At dt =
             (2/sigma_max)/400 = 47.6 the 3-iteration map from this film
-            diverges (max|v/u| = 569, a non-positive iterate).
+            diverges (max|v/u| = 569, a non-positive iterate).  The
+            trajectory: 400 such steps (T = 4); its loss |h(T) - h_target|^2
+            takes h_target from the same 400 steps of the film of seed 1242.
 Step control: dt_max = 0.01/sigma_max, dt_min = 1e-9, shrink 1/2, grow 5/4
 after 5 accepted steps, K = 10 Newton iterations, tol 1e-10.
 
@@ -68,7 +70,7 @@ def main():
         "nucl8k": dict(common, N=8192, P=256, eps=1e-4, seed=1236, dt0=1e-3, T=1e30,
                        holes=64, depth=0.3, width=lam / 4.0),
         "adjoint1k": dict(common, N=1024, P=16, eps=0.01, seed=1238, dt0=1e-3,
-                          T=1e30, dt_fixed=0.01, fixed_iter=3),
+                          T=1e30, dt_fixed=0.01, fixed_iter=3, steps=400, target_seed=1242),
     }
     for w in W.values():
         w["ds"] = w["P"] * lam / w["N"]

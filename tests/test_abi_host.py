@@ -111,6 +111,15 @@ def test_null_arguments_rejected():
     assert L.tf_advance(None, None, 0.0, 1.0, 1.0, 1, None, None, None, None) == tf.TF_ERR_ARG
     assert tf.tf_strerror(tf.TF_ERR_ARG) == "invalid argument"
     L.tf_destroy(None)
+    out = C.c_void_p(123)
+    assert L.tf_tape_create(None, 10, 3, 0.01, 0, C.byref(out)) == tf.TF_ERR_ARG
+    assert out.value is None
+    assert L.tf_tape_create(None, 10, 3, 0.01, 0, None) == tf.TF_ERR_ARG
+    assert L.tf_tape_info(None, None, None, None, None) == tf.TF_ERR_ARG
+    assert L.tf_tape_forward(None, None, None) == tf.TF_ERR_ARG
+    assert L.tf_tape_backward(None, None, None, None, None) == tf.TF_ERR_ARG
+    assert L.tf_tape_timing(None, None, 0) == tf.TF_ERR_ARG
+    L.tf_tape_destroy(None)
 
 
 def test_no_cpu_fallback_without_gpu():

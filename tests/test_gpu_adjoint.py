@@ -130,3 +130,146 @@ def test_unrolled_step_is_differentiable_in_torch(torch):
                                      rtol=1e-6)
     out = tf.unrolled_step(h, ctx, dt, 3)
     assert np.max(np.abs(out.detach().cpu().numpy() - AD.step_fixed(M, h.detach().cpu().numpy(), dt, 3))) <= 1e-13
+
+
+# --------------------------------------------------------------------------
+# Trajectories of fixed steps with checkpoints (tf_tape_*)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nx,ny,K,nsteps,every", [(7, 5, 3, 5, 0), (7, 5, 3, 5, 2), (10, 9, 2, 4, 1),
+                                                   (6, 11, 1, 3, 3), (8, 1, 3, 6, 4)])
+def test_tape_matches_oracle_trajectory(torch, nx, ny, K, nsteps, every):
+    M, p, dt = setup(nx, ny)
+    u = S.spinodal_film(nx, ny, 1.0, 0.05, seed=3 * nx + ny)
+    g = np.random.default_rng(nx * ny).standard_normal((ny, nx))
+    hs = AD.trajectory(M, u, dt, K, nsteps)
+    ref_g, ref_k = AD.trajectory_vjp(M, u, dt, K, nsteps, g)
+    ctx = tf.Context(p)
+    tape = tf.tf_tape_create(ctx, nsteps, K, dt, every)
+    info = tf.tf_tape_info(tape)
+    e = every or math.ceil(math.sqrt(nsteps))
+    assert info["every"] == e and info["checkpoints"] == math.ceil(nsteps / e)
+    assert not info["forward_done"]
+    hT = tf.tf_tape_forward(tape, dev(torch, u))
+    assert tf.tf_tape_info(tape)["forward_done"]
+    assert np.max(np.abs(hT.cpu().numpy() - hs[-1])) <= 1e-13
+    r = tf.tf_tape_backward(tape, dev(torch, g))
+    assert np.max(np.abs(r["g_h0"].cpu().numpy() - ref_g)) <= 1e-10 * np.max(np.abs(ref_g))
+    assert abs(r["g_kappa"] - ref_k) <= 1e-9 * abs(ref_k)
+
+
+def test_tape_result_does_not_depend_on_the_interval(torch):
+    # every segment recomputes the forward's own bits, so any checkpoint
+    # interval gives the same result bit for bit; the forward is the same as
+    # repeated fixed-iteration steps
+    nx, ny, K, nsteps, dt = 96, 64, 3, 10, 0.02
+    p = tf.tf_params_default(nx=nx, ny=ny, ds=1.5, precision=tf.TF_FP64)
+    ctx = tf.Context(p)
+    u = dev(torch, S.spinodal_film(nx, ny, 1.0, 0.02, seed=77))
+    g = dev(torch, np.random.default_rng(78).standard_normal((ny, nx)))
+    fw = tf.Context(tf.tf_params_default(nx=nx, ny=ny, ds=1.5, precision=tf.TF_FP64, newton_fixed_iter=K))
+    cur = u.clone()
+    for _ in range(nsteps):
+        nxt = torch.empty_like(cur)
+        tf.tf_newton_adi_step(fw, cur, nxt, dt)
+        cur = nxt
+    res = []
+    for every in (1, 2, 3, 4, 10, 0):
+        tape = tf.tf_tape_create(ctx, nsteps, K, dt, every)
+        hT = tf.tf_tape_forward(tape, u)
+        assert torch.equal(hT, cur)
+        r = tf.tf_tape_backward(tape, g)
+        r2 = tf.tf_tape_backward(tape, g)  # repeatable
+        assert torch.equal(r["g_h0"], r2["g_h0"]) and r["g_kappa"] == r2["g_kappa"]
+        res.append(r)
+        t = tf.tf_tape_timing(tape)
+        assert t["tape_forward"] > 0 and t["recompute"] > 0 and t["solve_t"] > 0
+        assert t["forward"] == 0.0  # the reverse takes the iterates of the recomputed segments
+    for r in res[1:]:
+        assert torch.equal(r["g_h0"], res[0]["g_h0"])
+        assert r["g_kappa"] == res[0]["g_kappa"]
+
+
+def test_tape_arguments(torch):
+    p = tf.tf_params_default(nx=16, ny=8, ds=1.0, precision=tf.TF_FP64)
+    ctx = tf.Context(p)
+    for bad in (dict(nsteps=0), dict(K=0), dict(K=65), dict(dt=0.0), dict(every=-1), dict(every=6)):
+        kw = dict(nsteps=5, K=3, dt=0.01, every=0)
+        kw.update(bad)
+        with pytest.raises(RuntimeError):
+            tf.tf_tape_create(ctx, **kw)
+    with pytest.raises(RuntimeError):
+        tf.tf_tape_create(tf.Context(tf.tf_params_default(nx=16, ny=8, ds=1.0, precision=tf.TF_FP32_BULK)),
+                          5, 3, 0.01)
+    tape = tf.tf_tape_create(ctx, 5, 3, 0.01)
+    z = torch.ones((8, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError):  # no forward yet
+        tf.tf_tape_backward(tape, z)
+    # a film that leaves the model's domain: reported, and the tape stays unusable
+    neg = -z
+    with pytest.raises(RuntimeError):
+        tf.tf_tape_forward(tape, neg)
+    assert not tf.tf_tape_info(tape)["forward_done"]
+    with pytest.raises(RuntimeError):
+        tf.tf_tape_backward(tape, z)
+
+
+def test_trajectory_is_differentiable_in_torch(torch):
+    # torch.autograd.gradcheck over the film and the contact angle
+    nx, ny = 6, 5
+    M, p, dt = setup(nx, ny)
+    h = dev(torch, S.spinodal_film(nx, ny, 1.0, 0.05, seed=21)).requires_grad_(True)
+    th = torch.tensor(math.radians(20.0), dtype=torch.float64, device="cuda", requires_grad=True)
+    f = lambda x, t: tf.trajectory(x, t, p, dt, 2, 4, every=2)  # noqa: E731
+    assert torch.autograd.gradcheck(f, (h, th), eps=1e-6, atol=1e-8, rtol=1e-6)
+    out = f(h, th)
+    assert np.max(np.abs(out.detach().cpu().numpy() - AD.trajectory(M, h.detach().cpu().numpy(), dt, 2, 4)[-1])) \
+        <= 1e-13
+
+
+def _loss_difference(a_p, a_m, t):
+    # |a+ - t|^2 - |a- - t|^2 written as sum (a+ - a-)(a+ + a- - 2t): no
+    # cancellation between two large sums
+    return float(((a_p - a_m) * (a_p + a_m - 2.0 * t)).sum())
+
+
+def test_adjoint_trajectory_workload_against_central_differences(torch):
+    """The adjoint workload: 1024^2 on 16 lambda_m, 400 steps of 3 Newton
+    iterations at dt = 0.01, loss |h(T) - h_target|^2 with h_target the same
+    trajectory from another seed's film; gradients of the loss with respect
+    to the initial film (32 random directions) and the contact angle against
+    central differences of the GPU forward, to 1e-6 relative."""
+    W = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "workloads.json")))
+    w = W["adjoint1k"]
+    N, K, dt, ns = w["N"], w["fixed_iter"], w["dt_fixed"], w["steps"]
+    p = tf.params_for_workload(w, tf.TF_FP64)
+    th0 = w["theta_c"]
+
+    def run(h0, th):
+        q = tf.TfParams.from_buffer_copy(p)
+        q.kappa, q.contact_angle = 0.0, th
+        tape = tf.tf_tape_create(tf.Context(q), ns, K, dt)
+        return tape, tf.tf_tape_forward(tape, h0)
+
+    u = dev(torch, S.spinodal_film(N, N, w["h0"], w["eps"], w["seed"]))
+    _, target = run(dev(torch, S.spinodal_film(N, N, w["h0"], w["eps"], w["target_seed"])), th0)
+    tape, hT = run(u, th0)
+    assert tf.tf_tape_info(tape)["every"] == 20
+    r = tf.tf_tape_backward(tape, 2.0 * (hT - target))
+    gh = r["g_h0"]
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for _ in range(32):
+        d = dev(torch, rng.standard_normal((N, N)))
+        h = 1e-6
+        _, ap = run(u + h * d, th0)
+        _, am = run(u - h * d, th0)
+        fd = _loss_difference(ap, am, target) / (2 * h)
+        ad = float(torch.sum(gh * d))
+        worst = max(worst, abs(fd - ad) / abs(ad))
+    assert worst <= 1e-6, worst
+    ht = 1e-4
+    _, ap = run(u, th0 + ht)
+    _, am = run(u, th0 - ht)
+    fdt = _loss_difference(ap, am, target) / (2 * ht)
+    assert abs(fdt - r["g_theta"]) <= 1e-6 * abs(r["g_theta"]), (fdt, r["g_theta"])

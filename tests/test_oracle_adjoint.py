@@ -101,3 +101,22 @@ def test_dkappa_dtheta():
     th, h = math.radians(23.0), 1e-6
     fd = (O.kappa_from_contact_angle(th + h, 0.1, 3, 2) - O.kappa_from_contact_angle(th - h, 0.1, 3, 2)) / (2 * h)
     assert abs(AD.dkappa_dtheta(th, 0.1, 3, 2) - fd) < 1e-8 * abs(fd)
+
+
+def test_trajectory_vjp_is_the_chain_rule():
+    """The chained steps' adjoints equal the transposed complex-step Jacobian
+    of the whole trajectory (one complex step through all N steps), and the
+    trajectory's last state equals the C oracle run step by step."""
+    M, sm = model(5, 4)
+    dt, K, N = (2.0 / sm) / 400, 2, 4
+    u = S.spinodal_film(5, 4, 1.0, 0.05, seed=12)
+    g = np.random.default_rng(13).standard_normal(u.shape)
+    hs = AD.trajectory(M, u, dt, K, N)
+    c = u
+    for _ in range(N):
+        c = c_step(M, c, dt, K)
+    assert np.max(np.abs(hs[-1] - c)) < 1e-13
+    J, Jk = AD.trajectory_jacobian(M, u, dt, K, N)
+    gu, gk = AD.trajectory_vjp(M, u, dt, K, N, g)
+    assert np.max(np.abs(gu.ravel() - J.T @ g.ravel())) < 1e-11 * np.max(np.abs(gu))
+    assert abs(gk - Jk @ g.ravel()) < 1e-11 * abs(gk)
