@@ -303,8 +303,11 @@ int tf_adjoint_timing(double* ms, int n);
  * is tf_adjoint_step's).  Uniform checkpoints: the forward keeps u^n at
  * n = 0, e, 2e, ... (ceil(N/e) grids); the reverse runs one segment of e
  * steps again from its checkpoint, keeping each step's iterates (u_k, w_k,
- * v_k: 3K grids), and reverses them, so memory is ceil(N/e) + 3Ke + 2 grids
+ * v_k: 3K grids), and reverses them, so memory is ceil(N/e) + 6Ke + 2 grids
  * (O(sqrt N) at e = ceil(sqrt(N))) for two forward passes and one reverse.
+ * A segment is run again (on the context's stream, from a host worker
+ * thread) while the next one is reversed (on the tape's own stream): two
+ * banks of iterates.
  * Every segment recomputes exactly the forward's bits (the same kernels and
  * order), so the result does not depend on e.  The context must satisfy
  * tf_adjoint_step's conditions.                                          */
@@ -312,7 +315,7 @@ typedef struct tf_tape tf_tape;
 
 /* A tape for nsteps >= 1 steps of K (1..64) iterations at dt > 0 on the
  * context's grid, checkpoint interval every (0: ceil(sqrt(nsteps)); else
- * 1..nsteps).  Allocates ceil(nsteps/every) + 3 K every + 2 device grids
+ * 1..nsteps).  Allocates ceil(nsteps/every) + 6 K every + 2 device grids
  * (the reverse also uses the context's adjoint workspace).  The
  * context must outlive the tape.  Returns TF_OK, TF_ERR_ARG or
  * TF_ERR_NOMEM.                                                           */
@@ -333,8 +336,9 @@ int tf_tape_forward(tf_tape* tape, const double* h0, double* hT);
 /* The reverse of the last forward: g (device grid, the cotangent of u^N),
  * g_h0 (device output grid, may equal g), g_kappa, g_theta (host outputs or
  * NULL; g_theta as in tf_adjoint_step).  Sums over the steps are taken in a
- * fixed order, so repeated calls give the same bits.  Returns TF_OK,
- * TF_ERR_ARG (no forward yet) or a negative error.                         */
+ * fixed order, so repeated calls give the same bits.  Waits for the
+ * context's stream first; synchronises both streams before it returns.
+ * Returns TF_OK, TF_ERR_ARG (no forward yet) or a negative error.          */
 int tf_tape_backward(tf_tape* tape, const double* g, double* g_h0, double* g_kappa, double* g_theta);
 
 /* Kernel time (ms, CUDA events) of the tape's last forward and backward:

@@ -27,6 +27,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <thread>
+#include <utility>
 #include <vector>
 
 #include "tf_internal.h"
@@ -521,26 +523,23 @@ int rev_workspace(tf_ctx* c, int K, bool iterates, RevWork* w) {
 }
 
 // K iterations of the FP64 path from u^n = U[0], keeping u_1..u_K in
-// U[1..K] and w_k, v_k (tf_newton_iteration: bit-identical to the forward
-// step, whose first iteration is fused with the explicit part).
+// U[1..K] and w_k, v_k: queued without waiting (the forward step's kernels
+// in its order, so its bits).
 int adj_forward(tf_ctx* c, double dt, int K, double* const* U, double* const* W, double* const* V) {
-  for (int k = 0; k < K; ++k) {
-    tf_step_info info;
-    const int r = tf_newton_iteration(c, U[k], U[0], dt, W[k], V[k], U[k + 1], &info);
-    if (r < 0) return r;
-  }
-  return TF_OK;
+  return tf::fixed_iterates(*c, dt, K, U, W, V);
 }
 
 // The reverse of one step from its iterates (U[0] = u^n, U[1..K-1], W, V):
 // g_h = (du^K/du^n)^T g; *kbar receives the step's kappa cotangent (partial
-// sums added on the host in a fixed order).  Synchronises the stream.
+// sums added on the host in a fixed order).  Runs on T.st and synchronises
+// it; reads only the context's parameters and its adjoint workspace, so a
+// forward may run on the context's own stream at the same time.
 int adj_reverse(tf_ctx* c, const RevWork& R, const double* const* U, const double* const* W,
                 const double* const* V, double dt, int K, const double* g, double* g_h, double* kbar,
                 GroupTimer& T) {
   const int nx = c->p.nx, ny = c->p.ny;
   const size_t N = c->N;
-  cudaStream_t st = c->stream;
+  cudaStream_t st = T.st;  // the stream the reverse runs on
   const double* h_old = U[0];
   double *band = R.band, *lam_y = R.lam_y, *lam_x = R.lam_x, *bbar = R.bbar, *scratch = R.scratch;
   double* part = R.part;
@@ -675,14 +674,18 @@ extern "C" int tf_adjoint_step(tf_ctx* c, const double* h_old, double dt, int K,
 // runs a segment's e steps again from its checkpoint keeping every step's
 // iterates (the same bits as the forward: tf_newton_iteration equals the
 // fused step), and reverses them, the cotangent ping-ponging between two
-// grids.
+// grids.  Both halves are chains of dependent FP64 operations that leave
+// most of the GPU idle, so segment s-1 is run again (a host worker thread,
+// the context's stream, one bank of iterates) while segment s is reversed
+// (this thread, the tape's own stream, the other bank).
 
 struct tf_tape {
   tf_ctx* c;
   int nsteps, K, every, nckpt;
   double dt;
-  double* mem;  // nckpt checkpoints, every x 3K iterate grids, 2 cotangents
+  double* mem;  // nckpt checkpoints, 2 banks of every x 3K iterate grids, 2 cotangents
   size_t bytes;
+  cudaStream_t rev;  // the reverse's stream
   bool forward_done;
   double ms[2 + kGroups];
 };
@@ -690,12 +693,13 @@ struct tf_tape {
 namespace {
 
 double* tape_ckpt(tf_tape* t, int s) { return t->mem + (size_t)s * t->c->N; }
-// grid q (0 .. 3K-1) of segment step i: u_1..u_K, w_0..w_{K-1}, v_0..v_{K-1}
-double* tape_iter(tf_tape* t, int i, int q) {
-  return t->mem + ((size_t)t->nckpt + (size_t)i * 3 * t->K + q) * t->c->N;
+// grid q (0 .. 3K-1) of segment step i in bank b: u_1..u_K, w_0..w_{K-1},
+// v_0..v_{K-1}
+double* tape_iter(tf_tape* t, int b, int i, int q) {
+  return t->mem + ((size_t)t->nckpt + ((size_t)b * t->every + i) * 3 * t->K + q) * t->c->N;
 }
 double* tape_cot(tf_tape* t, int i) {
-  return t->mem + ((size_t)t->nckpt + (size_t)t->every * 3 * t->K + i) * t->c->N;
+  return t->mem + ((size_t)t->nckpt + (size_t)2 * t->every * 3 * t->K + i) * t->c->N;
 }
 
 // Event-timed region on the context's stream, added to *acc.
@@ -741,12 +745,23 @@ extern "C" int tf_tape_create(tf_ctx* c, int nsteps, int K, double dt, int every
   t->dt = dt;
   t->every = every;
   t->nckpt = (nsteps + every - 1) / every;
-  const size_t grids = (size_t)t->nckpt + (size_t)every * 3 * K + 2;
+  const size_t grids = (size_t)t->nckpt + (size_t)2 * every * 3 * K + 2;
   t->bytes = grids * c->N * sizeof(double);
   if (cudaMalloc(&t->mem, t->bytes) != cudaSuccess) {
     cudaGetLastError();
     free(t);
     return TF_ERR_NOMEM;
+  }
+  // the reverse is the longer half of each segment's work: its stream gets
+  // the highest priority, and the forward of the next segment fills the
+  // SMs it leaves idle
+  int prio_lo = 0, prio_hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) prio_hi = 0;
+  if (cudaStreamCreateWithPriority(&t->rev, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(t->mem);
+    free(t);
+    return TF_ERR_CUDA;
   }
   *out = t;
   return TF_OK;
@@ -754,6 +769,7 @@ extern "C" int tf_tape_create(tf_ctx* c, int nsteps, int K, double dt, int every
 
 extern "C" void tf_tape_destroy(tf_tape* t) {
   if (!t) return;
+  cudaStreamDestroy(t->rev);
   cudaFree(t->mem);
   free(t);
 }
@@ -808,58 +824,112 @@ extern "C" int tf_tape_forward(tf_tape* t, const double* h0, double* hT) {
   return TF_OK;
 }
 
+namespace {
+
+// Pointers to the iterates of segment s (bank s & 1): step i starts from
+// u^{n0+i} (the checkpoint, then the previous step's u_K).
+struct SegPtrs {
+  std::vector<double*> U, W, V;  // (K + 1), K, K per step
+  int len;
+};
+
+void seg_ptrs(tf_tape* t, int s, SegPtrs* P) {
+  const int K = t->K, n0 = s * t->every, b = s & 1;
+  P->len = (n0 + t->every < t->nsteps ? n0 + t->every : t->nsteps) - n0;
+  P->U.assign((size_t)t->every * (K + 1), nullptr);
+  P->W.assign((size_t)t->every * K, nullptr);
+  P->V.assign((size_t)t->every * K, nullptr);
+  for (int i = 0; i < P->len; ++i) {
+    double** Ui = &P->U[(size_t)i * (K + 1)];
+    Ui[0] = i == 0 ? tape_ckpt(t, s) : P->U[(size_t)(i - 1) * (K + 1) + K];
+    for (int k = 0; k < K; ++k) {
+      Ui[k + 1] = tape_iter(t, b, i, k);
+      P->W[(size_t)i * K + k] = tape_iter(t, b, i, K + k);
+      P->V[(size_t)i * K + k] = tape_iter(t, b, i, 2 * K + k);
+    }
+  }
+}
+
+// Runs segment s again on the context's stream, keeping its iterates.
+int seg_forward(tf_tape* t, const SegPtrs& P, double* ms) {
+  tf_ctx& c = *t->c;
+  const int K = t->K;
+  RegionTimer R(c.stream);
+  for (int i = 0; i < P.len; ++i) {
+    const int r = adj_forward(&c, t->dt, K, &P.U[(size_t)i * (K + 1)], &P.W[(size_t)i * K], &P.V[(size_t)i * K]);
+    if (r) return r;
+  }
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return TF_ERR_CUDA;
+  R.stop(ms);
+  return TF_OK;
+}
+
+}  // namespace
+
 extern "C" int tf_tape_backward(tf_tape* t, const double* g, double* g_h0, double* g_kappa, double* g_theta) {
   if (!t || !g || !g_h0 || !t->forward_done) return TF_ERR_ARG;
   tf_ctx& c = *t->c;
   const int K = t->K;
   const size_t gb = c.N * sizeof(double);
-  cudaStream_t st = c.stream;
   for (int k = 1; k < 2 + kGroups; ++k) t->ms[k] = 0.0;
   RevWork Rw;
   int r = rev_workspace(&c, K, false, &Rw);
   if (r) return r;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TF_ERR_CUDA;
+  // the reverse stream starts after everything queued on the context's
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return TF_ERR_CUDA;
   double* cot[2] = {tape_cot(t, 0), tape_cot(t, 1)};
-  if (cudaMemcpyAsync(cot[0], g, gb, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return TF_ERR_CUDA;
+  if (cudaMemcpyAsync(cot[0], g, gb, cudaMemcpyDeviceToDevice, t->rev) != cudaSuccess) return TF_ERR_CUDA;
   int cc = 0;
   double kbar = 0.0;
-  std::vector<double*> U((size_t)t->every * (K + 1)), W((size_t)t->every * K), V((size_t)t->every * K);
+  SegPtrs cur, nxt;
+  seg_ptrs(t, t->nckpt - 1, &cur);
+  r = seg_forward(t, cur, &t->ms[1]);
+  if (r) return r;
   for (int s = t->nckpt - 1; s >= 0; --s) {
-    const int n0 = s * t->every, len = (n0 + t->every < t->nsteps ? n0 + t->every : t->nsteps) - n0;
-    // the segment's iterates: step i starts from u^{n0+i} (the checkpoint,
-    // then the previous step's u_K)
-    for (int i = 0; i < len; ++i) {
-      double** Ui = &U[(size_t)i * (K + 1)];
-      Ui[0] = i == 0 ? tape_ckpt(t, s) : U[(size_t)(i - 1) * (K + 1) + K];
-      for (int k = 0; k < K; ++k) {
-        Ui[k + 1] = tape_iter(t, i, k);
-        W[(size_t)i * K + k] = tape_iter(t, i, K + k);
-        V[(size_t)i * K + k] = tape_iter(t, i, 2 * K + k);
+    // segment s - 1 runs again on a worker thread while s is reversed here
+    int rw = TF_OK;
+    double ms_w = 0.0;
+    std::thread worker;
+    bool ahead = false;  // segment s - 1 already queued on the worker
+    if (s > 0) {
+      seg_ptrs(t, s - 1, &nxt);
+      try {
+        worker = std::thread([&]() {
+          if (cudaSetDevice(dev) != cudaSuccess) {
+            rw = TF_ERR_CUDA;
+            return;
+          }
+          rw = seg_forward(t, nxt, &ms_w);
+        });
+        ahead = true;
+      } catch (...) {  // no thread: run the segments one after the other
       }
     }
-    {
-      RegionTimer R(st);
-      for (int i = 0; i < len; ++i) {
-        r = adj_forward(&c, t->dt, K, &U[(size_t)i * (K + 1)], &W[(size_t)i * K], &V[(size_t)i * K]);
-        if (r) return r;
-      }
-      R.stop(&t->ms[1]);
-    }
-    for (int i = len - 1; i >= 0; --i) {
+    int rr = TF_OK;
+    for (int i = cur.len - 1; i >= 0 && rr == TF_OK; --i) {
       GroupTimer T;
-      T.st = st;
+      T.st = t->rev;
       double gk = 0.0;
-      r = adj_reverse(&c, Rw, &U[(size_t)i * (K + 1)], &W[(size_t)i * K], &V[(size_t)i * K], t->dt, K, cot[cc],
-                      cot[cc ^ 1], &gk, T);
-      if (r) return r;
+      rr = adj_reverse(&c, Rw, &cur.U[(size_t)i * (K + 1)], &cur.W[(size_t)i * K], &cur.V[(size_t)i * K], t->dt,
+                       K, cot[cc], cot[cc ^ 1], &gk, T);
+      if (rr != TF_OK) break;
       double ms[kGroups];
       T.collect(ms);
       for (int k = 0; k < kGroups; ++k) t->ms[2 + k] += ms[k];
       cc ^= 1;
       kbar += gk;
     }
+    if (worker.joinable()) worker.join();
+    if (rr) return rr;
+    if (s > 0 && !ahead) rw = seg_forward(t, nxt, &ms_w);
+    if (rw) return rw;
+    t->ms[1] += ms_w;
+    std::swap(cur, nxt);
   }
-  if (cudaMemcpyAsync(g_h0, cot[cc], gb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
+  if (cudaMemcpyAsync(g_h0, cot[cc], gb, cudaMemcpyDeviceToDevice, t->rev) != cudaSuccess ||
+      cudaStreamSynchronize(t->rev) != cudaSuccess)
     return TF_ERR_CUDA;
   if (g_kappa) *g_kappa = kbar;
   if (g_theta) *g_theta = kbar * dkappa_dtheta(c);

@@ -317,6 +317,22 @@ template <class T> int dalloc(T** p, size_t bytes) {
 }  // namespace
 
 namespace tf {
+int fixed_iterates(tf_ctx& c, double dt, int K, double* const* U, double* const* W, double* const* V) {
+  const int re = explicit_launch(c, U[0], dt, true);
+  if (re) return re;
+  for (int k = 0; k < K; ++k) {
+    const int r = iterate_launch(c, U[k], dt, U[k + 1], W ? W[k] : nullptr, V ? V[k] : nullptr, k == 0);
+    if (r) return r;
+    if (c.timing.enabled) {  // the events are reused by the next iteration
+      TF_CK(cudaStreamSynchronize(c.stream));
+      if (k == 0) explicit_collect(c);
+      Scalars s;
+      iterate_collect(c, W != nullptr, &s);
+    }
+  }
+  return TF_OK;
+}
+
 int fixed_step(tf_ctx& c, const double* h_old, double* h_new, double dt, int K) {
   tf_step_info info;
   const int s = step(c, h_old, h_new, dt, K, &info);

@@ -37,9 +37,19 @@ extern const Ops ops_f32b;
 
 namespace tf {
 
+// The K iterations of a time step with a fixed iteration count, queued on
+// the context's stream without waiting for the GPU: U[0] = u^n, U[1..K]
+// receive the iterates (each distinct from the one before), W and V (or
+// NULL) w_k and v_k.  The kernels and their order are those of
+// tf_newton_adi_step with K fixed iterations (the first fused with the
+// explicit part), so the bits are too.  With timing enabled it waits after
+// every iteration to read the events.
+int fixed_iterates(tf_ctx& c, double dt, int K, double* const* U, double* const* W, double* const* V);
+
 // One time step of exactly K Newton iterations at dt (the step of
-// tf_newton_adi_step with its fixed-iteration override): TF_OK, a step
-// failure (TF_STEP_NONPOSITIVE, TF_STEP_ZERO_PIVOT) or a negative error.
+// tf_newton_adi_step with its fixed-iteration override), every iteration's
+// failure flags checked: TF_OK, a step failure (TF_STEP_NONPOSITIVE,
+// TF_STEP_ZERO_PIVOT) or a negative error.
 int fixed_step(tf_ctx& c, const double* h_old, double* h_new, double dt, int K);
 
 }  // namespace tf
