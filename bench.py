@@ -701,6 +701,8 @@ def run_adjoint(args, w):
     from paper_1806_10550_gb300 import synthetic as S
     rank, world, local, dist = dist_setup()
     tf.library(build_if_missing=True)
+    if args.traj_steps > 0:
+        w = dict(w, steps=args.traj_steps)
     N, K, dt, ns = w["N"], w["fixed_iter"], w["dt_fixed"], w["steps"]
     p = tf.params_for_workload(w, tf.TF_FP64)
     p.kappa, p.contact_angle = 0.0, w["theta_c"]  # kappa from the contact angle
@@ -830,6 +832,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=-1,
                     help="steps of the end-to-end pass (default: all timed steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traj-steps", type=int, default=0,
+                    help="adjoint workload: trajectory length (default: the workload's; shorter for profiles)")
     ap.add_argument("--modes", default="fp64,f32b")
     args = ap.parse_args()
     w = load_workload(args.workload)

@@ -306,34 +306,58 @@ __global__ void k_band(AdjK M, const double* __restrict__ u, Tables T, double* _
 }
 
 // Transposed pentadiagonal solves A^T x = r along every line of direction
-// DIR, one thread per line, elimination without pivoting (bandwidth 2) and
-// back substitution.  Row t of A^T holds A[t+d-2][t] = band[4-d] of row
-// t+d-2.  scratch: 4 values per cell (eliminated row and right side).
+// DIR, elimination without pivoting (bandwidth 2), two threads per line
+// (lanes 2j, 2j+1 of the block): a twisted elimination.  Row t of A^T holds
+// A[t+d-2][t] = band[4-d] of row t+d-2.
+//  - The top thread eliminates the lower entries with pivots 0 .. m-1, in
+//    the line's order; the bottom thread eliminates the upper entries with
+//    pivots n-1 .. m+2, in reversed order (the same code on the reversed
+//    line, bands mirrored).  Both leave rows m, m+1 updated in their window.
+//  - Each side's multipliers read only entries the other side never
+//    changes, so the two updates of rows m, m+1 add: the 2 x 2 system for
+//    x_m, x_{m+1} is the original block plus both sides' changes.
+//  - The top thread solves it and both substitute back, outwards.
+// Lines shorter than 8 are not split.  scratch: 4 values per cell (the
+// eliminated row and right side).
+constexpr int kSolveLines = 4;  // lines per block, two threads each
+
 template <int DIR>
-__global__ void k_solve_t(int nx, int ny, const double* __restrict__ band, const double* __restrict__ r,
-                          double* __restrict__ x, double* __restrict__ scratch) {
-  const int line = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(2 * kSolveLines) k_solve_t(int nx, int ny, const double* __restrict__ band,
+                                                            const double* __restrict__ r, double* __restrict__ x,
+                                                            double* __restrict__ scratch) {
+  const int half = threadIdx.x & 1;
+  const int line = blockIdx.x * kSolveLines + (threadIdx.x >> 1);
   const int nlines = DIR == 0 ? ny : nx, n = DIR == 0 ? nx : ny;
-  if (line >= nlines) return;
+  const bool active = line < nlines;  // inactive threads still join the shuffles
+  const unsigned pair = 3u << (threadIdx.x & ~1);
   const size_t N = (size_t)nx * ny;
+  const int m = n >= 8 ? n / 2 : n;  // top pivots 0 .. m-1
+  const bool twisted = m < n;
+  // pivots and rows (pivots plus the two seam rows) of this thread, in its
+  // own orientation: position p is row p (top) or n-1-p (bottom)
+  const int npiv = !active ? 0 : half == 0 ? m : (twisted ? n - m - 2 : 0);
+  const int nrows = !active ? 0 : (half == 0 ? (twisted ? m + 2 : n) : (twisted ? n - m : 0));
+  auto row_of = [&](int p) -> int { return half == 0 ? p : n - 1 - p; };
   auto idx = [&](int t) -> size_t { return DIR == 0 ? (size_t)line * nx + t : (size_t)t * nx + line; };
   auto B = [&](int row, int d) -> double { return (row < 0 || row >= n) ? 0.0 : band[d * N + idx(row)]; };
-  // transposed row t: (lo2, lo1, dg, up1, up2)
-  auto trow = [&](int t, double& lo2, double& lo1, double& dg, double& up1, double& up2) {
-    lo2 = B(t - 2, 4);
-    lo1 = B(t - 1, 3);
+  // transposed row at position p, oriented: (lo2, lo1, dg, up1, up2)
+  auto trow = [&](int p, double& lo2, double& lo1, double& dg, double& up1, double& up2) {
+    const int t = row_of(p);
+    const double e0 = B(t - 2, 4), e1 = B(t - 1, 3), e3 = B(t + 1, 1), e4 = B(t + 2, 0);
     dg = B(t, 2);
-    up1 = B(t + 1, 1);
-    up2 = B(t + 2, 0);
+    lo2 = half == 0 ? e0 : e4;
+    lo1 = half == 0 ? e1 : e3;
+    up1 = half == 0 ? e3 : e1;
+    up2 = half == 0 ? e4 : e0;
   };
   double* sd = scratch;          // reciprocal of the eliminated diagonal
-  double* s1 = scratch + N;      // eliminated first super-diagonal
-  double* s2 = scratch + 2 * N;  // second super-diagonal
+  double* s1 = scratch + N;      // eliminated first super-diagonal (oriented)
+  double* s2 = scratch + 2 * N;  // second super-diagonal (oriented)
   double* sy = scratch + 3 * N;  // eliminated right side
-  // window: rows k (a*), k+1 (b*), k+2 (c*); rows k+2..k+5 are loaded four
-  // steps ahead into a ring (slot = row mod 4) so that the loads overlap the
-  // elimination chain
-  double a_lo2, a_lo1, a_dg, a_u1, a_u2, a_y;
+  // window: positions k (a*), k+1 (b*), k+2 (c*); positions k+2..k+5 are
+  // loaded four steps ahead into a ring (slot = position mod 4) so that the
+  // loads overlap the elimination chain
+  double a_lo2 = 0.0, a_lo1 = 0.0, a_dg = 1.0, a_u1 = 0.0, a_u2 = 0.0, a_y = 0.0;
   double b_lo2 = 0.0, b_lo1 = 0.0, b_dg = 1.0, b_u1 = 0.0, b_u2 = 0.0, b_y = 0.0;
   double c_lo2 = 0.0, c_lo1 = 0.0, c_dg = 1.0, c_u1 = 0.0, c_u2 = 0.0, c_y = 0.0;
   double p_lo2[4], p_lo1[4], p_dg[4], p_u1[4], p_u2[4], p_y[4];
@@ -342,25 +366,27 @@ __global__ void k_solve_t(int nx, int ny, const double* __restrict__ band, const
     p_lo2[q] = p_lo1[q] = p_u1[q] = p_u2[q] = p_y[q] = 0.0;
     p_dg[q] = 1.0;
   }
-  trow(0, a_lo2, a_lo1, a_dg, a_u1, a_u2);
-  a_y = r[idx(0)];
-  if (n > 1) {
+  if (nrows > 0) {
+    trow(0, a_lo2, a_lo1, a_dg, a_u1, a_u2);
+    a_y = r[idx(row_of(0))];
+  }
+  if (nrows > 1) {
     trow(1, b_lo2, b_lo1, b_dg, b_u1, b_u2);
-    b_y = r[idx(1)];
+    b_y = r[idx(row_of(1))];
   }
 #pragma unroll
   for (int q = 2; q < 6; ++q) {
-    if (q < n) {
+    if (q < nrows) {
       trow(q, p_lo2[q & 3], p_lo1[q & 3], p_dg[q & 3], p_u1[q & 3], p_u2[q & 3]);
-      p_y[q & 3] = r[idx(q)];
+      p_y[q & 3] = r[idx(row_of(q))];
     }
   }
-  for (int k0 = 0; k0 < n; k0 += 4) {
+  for (int k0 = 0; k0 < npiv; k0 += 4) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int k = k0 + q, sl = (q + 2) & 3;  // ring slot of row k + 2
-      if (k < n) {
-        if (k + 2 < n) {
+      const int k = k0 + q, sl = (q + 2) & 3;  // ring slot of position k + 2
+      if (k < npiv) {
+        if (k + 2 < nrows) {
           c_lo2 = p_lo2[sl];
           c_lo1 = p_lo1[sl];
           c_dg = p_dg[sl];
@@ -368,24 +394,24 @@ __global__ void k_solve_t(int nx, int ny, const double* __restrict__ band, const
           c_u2 = p_u2[sl];
           c_y = p_y[sl];
         }
-        if (k + 6 < n) {
+        if (k + 6 < nrows) {
           trow(k + 6, p_lo2[sl], p_lo1[sl], p_dg[sl], p_u1[sl], p_u2[sl]);
-          p_y[sl] = r[idx(k + 6)];
+          p_y[sl] = r[idx(row_of(k + 6))];
         }
         const double inv = 1.0 / a_dg;
-        if (k + 1 < n) {
+        if (k + 1 < nrows) {
           const double l = b_lo1 * inv;
           b_dg -= l * a_u1;
           b_u1 -= l * a_u2;
           b_y -= l * a_y;
         }
-        if (k + 2 < n) {
+        if (k + 2 < nrows) {
           const double l = c_lo2 * inv;
           c_lo1 -= l * a_u1;
           c_dg -= l * a_u2;
           c_y -= l * a_y;
         }
-        const size_t ck = idx(k);
+        const size_t ck = idx(row_of(k));
         sd[ck] = inv;
         s1[ck] = a_u1;
         s2[ck] = a_u2;
@@ -406,18 +432,54 @@ __global__ void k_solve_t(int nx, int ny, const double* __restrict__ band, const
       }
     }
   }
-  double x1 = 0.0, x2 = 0.0;  // x_{k+1}, x_{k+2}
+  // the seam: a = the first row after this thread's pivots, b = the second
+  // (top: rows m, m+1; bottom: rows m+1, m)
+  double x1 = 0.0, x2 = 0.0;  // the two unknowns beyond this thread's pivots, nearest first
+  if (twisted) {
+    // bottom: its changes to rows m (b) and m+1 (a), in the line's orientation
+    double o_lo2, o_lo1, o_dg, o_u1, o_u2;
+    double d_m_dg = 0.0, d_m_up = 0.0, d_m_y = 0.0, d_p_lo = 0.0, d_p_dg = 0.0, d_p_y = 0.0;
+    if (half == 1 && active) {
+      trow(npiv + 1, o_lo2, o_lo1, o_dg, o_u1, o_u2);  // row m, mirrored: lo1 = column m+1
+      d_m_dg = b_dg - o_dg;
+      d_m_up = b_lo1 - o_lo1;
+      d_m_y = b_y - r[idx(m)];
+      trow(npiv, o_lo2, o_lo1, o_dg, o_u1, o_u2);  // row m+1, mirrored: up1 = column m
+      d_p_dg = a_dg - o_dg;
+      d_p_lo = a_u1 - o_u1;
+      d_p_y = a_y - r[idx(m + 1)];
+    }
+    d_m_dg = __shfl_sync(pair, d_m_dg, (threadIdx.x & ~1) + 1);
+    d_m_up = __shfl_sync(pair, d_m_up, (threadIdx.x & ~1) + 1);
+    d_m_y = __shfl_sync(pair, d_m_y, (threadIdx.x & ~1) + 1);
+    d_p_lo = __shfl_sync(pair, d_p_lo, (threadIdx.x & ~1) + 1);
+    d_p_dg = __shfl_sync(pair, d_p_dg, (threadIdx.x & ~1) + 1);
+    d_p_y = __shfl_sync(pair, d_p_y, (threadIdx.x & ~1) + 1);
+    double xm = 0.0, xp = 0.0;
+    if (half == 0 && active) {
+      // top's window: a = row m (dg, up1 = column m+1), b = row m+1 (lo1 = column m, dg)
+      const double S00 = a_dg + d_m_dg, S01 = a_u1 + d_m_up, S10 = b_lo1 + d_p_lo, S11 = b_dg + d_p_dg;
+      const double y0 = a_y + d_m_y, y1 = b_y + d_p_y;
+      const double idet = 1.0 / (S00 * S11 - S01 * S10);
+      xm = (y0 * S11 - S01 * y1) * idet;
+      xp = (S00 * y1 - S10 * y0) * idet;
+      x[idx(m)] = xm;
+    }
+    xm = __shfl_sync(pair, xm, threadIdx.x & ~1);
+    xp = __shfl_sync(pair, xp, threadIdx.x & ~1);
+    if (half == 1 && active) x[idx(m + 1)] = xp;
+    x1 = half == 0 ? xm : xp;
+    x2 = half == 0 ? xp : xm;
+  }
 #pragma unroll 4
-  for (int k = n - 1; k >= 0; --k) {
-    const size_t ck = idx(k);
+  for (int k = npiv - 1; k >= 0; --k) {
+    const size_t ck = idx(row_of(k));
     const double xv = (sy[ck] - s1[ck] * x1 - s2[ck] * x2) * sd[ck];
     x[ck] = xv;
     x2 = x1;
     x1 = xv;
   }
 }
-
-constexpr int kSolveLines = 4;
 
 __global__ void k_axpy(size_t N, double a, const double* __restrict__ x, double* __restrict__ y) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -582,7 +644,7 @@ int adj_reverse(tf_ctx* c, const RevWork& R, const double* const* U, const doubl
     k_band<1><<<g2, b2, 0, st>>>(M, uk, Tb, band);
     T.end(t);
     t = T.begin(kGSolve);
-    k_solve_t<1><<<nl_y, kSolveLines, 0, st>>>(nx, ny, band, g_h, lam_y, scratch);
+    k_solve_t<1><<<nl_y, 2 * kSolveLines, 0, st>>>(nx, ny, band, g_h, lam_y, scratch);
     T.end(t);
     t = T.begin(kGLineY);
     k_vjp_line<1><<<gv, bv, 0, st>>>(M, uk, Tb, V[k], lam_y, -1.0, g_h, Lbar, part + (size_t)(kl++) * npart);
@@ -593,7 +655,7 @@ int adj_reverse(tf_ctx* c, const RevWork& R, const double* const* U, const doubl
     k_band<0><<<g2, b2, 0, st>>>(M, uk, Tb, band);
     T.end(t);
     t = T.begin(kGSolve);
-    k_solve_t<0><<<nl_x, kSolveLines, 0, st>>>(nx, ny, band, lam_y, lam_x, scratch);
+    k_solve_t<0><<<nl_x, 2 * kSolveLines, 0, st>>>(nx, ny, band, lam_y, lam_x, scratch);
     T.end(t);
     t = T.begin(kGLineX);
     k_vjp_line<0><<<gv, bv, 0, st>>>(M, uk, Tb, W[k], lam_x, -1.0, g_h, Lbar, part + (size_t)(kl++) * npart);
