@@ -52,6 +52,12 @@ def peaks() -> dict:
 # 500 G FP64 FMA/s (1.0 TFLOP/s) -- the FP64 pipe runs at 1/62 of FP32.
 FP64_TFLOPS = 1.0
 
+# FP64 operations executed per cell by each FP64-mode kernel (DFMA counted
+# as 2, DADD and DMUL as 1), from the ncu capture summarised in
+# profiles/iteration_kernels_fp64_prof4k.md (4096^2; per cell they do not
+# depend on the grid size).  Valid for the kernels as captured.
+FP64_FLOPS_PER_CELL = {"rhs": 46.14, "x_sweep": 86.90, "y_sweep": 103.90}
+
 
 class ClockSampler:
     """nvidia-smi clock and throttle samples during the timed region."""
@@ -912,12 +918,30 @@ def main():
         v64 = N * N * sum_over_ranks(dist, F["info"]["accepted"]) / (F["ms"] * 1e-3)
         t = F["timing"]
         per = (t["rhs_ms"] + t["x_ms"] + t["y_ms"]) / max(1, t["x_launches"])
+        # FP64 mode is bound by the FP64 pipe: executed FP64 flops of the
+        # dominant kernel (and of the iteration's three kernels) over their
+        # live CUDA-event time
+        kt = {"rhs": (t["rhs_launches"], t["rhs_ms"]), "x_sweep": (t["x_launches"], t["x_ms"]),
+              "y_sweep": (t["y_launches"], t["y_ms"])}
+        dom64 = max(kt, key=lambda k: kt[k][1])
+        n64, ms64 = kt[dom64]
+        ach64 = FP64_FLOPS_PER_CELL[dom64] * N * N * n64 / (ms64 * 1e-3) / 1e12
+        it_fl = sum(FP64_FLOPS_PER_CELL[k] * kt[k][0] for k in kt) * N * N
+        it_ms = sum(kt[k][1] for k in kt)
         line["fp64"] = dict(value=v64, ms_per_step=F["ms"] / max(1, F["info"]["attempts"]),
                             accepted_steps=F["info"]["accepted"],
                             newton_iterations=F["info"]["newton_iterations"],
                             ms_per_iteration=per,
                             roofline=dict(bound="alu", unit="TFLOP/s", peak=FP64_TFLOPS,
-                                          peak_source="measured FP64 FMA throughput probe"))
+                                          peak_source="measured FP64 FMA throughput probe",
+                                          kernel=dom64, flops_per_cell=FP64_FLOPS_PER_CELL[dom64],
+                                          ms_per_launch=round(ms64 / max(1, n64), 4),
+                                          achieved=round(ach64, 4), frac=round(ach64 / FP64_TFLOPS, 4),
+                                          flops="executed FP64 operations per cell counted by ncu (DFMA = 2)",
+                                          iteration=dict(
+                                              achieved=round(it_fl / (it_ms * 1e-3) / 1e12, 4),
+                                              frac=round(it_fl / (it_ms * 1e-3) / 1e12 / FP64_TFLOPS, 4),
+                                              scope="residual, x and y sweeps (explicit parts excluded)")))
         if head == "f32b":
             line["speedup_f32b_vs_fp64"] = value / v64
     cs = clocks.summary()
