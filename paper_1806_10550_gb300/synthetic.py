@@ -43,11 +43,20 @@ def nucleation_film(nx: int, ny: int, ds: float, h0: float, eps: float,
     noise = rng.uniform(-1.0, 1.0, size=(ny, nx))
     cx = rng.uniform(0.0, nx * ds, size=n_holes)
     cy = rng.uniform(0.0, ny * ds, size=n_holes)
-    x = cell_centres(nx, ds)[None, :]
-    y = cell_centres(ny, ds)[:, None]
+    xc = cell_centres(nx, ds)
+    yc = cell_centres(ny, ds)
     dip = np.zeros((ny, nx))
+    # each depression within 8 widths of its centre: beyond, exp(-64) ~ 1e-28
+    # is far below the last bit of h
+    R = 8.0 * width
     for k in range(n_holes):
-        dip += np.exp(-((x - cx[k]) ** 2 + (y - cy[k]) ** 2) / (width * width))
+        i0 = max(0, int(np.floor((cx[k] - R) / ds)) - 1)
+        i1 = min(nx, int(np.ceil((cx[k] + R) / ds)) + 1)
+        j0 = max(0, int(np.floor((cy[k] - R) / ds)) - 1)
+        j1 = min(ny, int(np.ceil((cy[k] + R) / ds)) + 1)
+        x = xc[None, i0:i1]
+        y = yc[j0:j1, None]
+        dip[j0:j1, i0:i1] += np.exp(-((x - cx[k]) ** 2 + (y - cy[k]) ** 2) / (width * width))
     return h0 * (1.0 + eps * noise - depth * dip)
 
 

@@ -71,3 +71,38 @@ def test_fp32_bulk_keeps_mass_and_dominant_wavelength(torch):
     print(f"steps={len(acc)} t={info64['t']:.1f} k_dom={k64:.5f} k_m={km:.5f} "
           f"max|h32-h64|={np.max(np.abs(a32 - a64)):.3e} "
           f"mass err 64={abs(a64.sum() - m0) / m0:.2e} 32={abs(a32.sum() - m0) / m0:.2e}")
+
+
+def test_fp32_bulk_against_fp64_at_full_size(torch):
+    """The precision workload at its full size: 8192^2 on 256 lambda_m
+    (lambda_m / 32), 1e-4 noise plus 64 depressions of depth 0.3 h0 and
+    width lambda_m / 4.  FP64 runs the adaptive controller to 6/sigma_max;
+    FP32-bulk replays its step sizes.  The same requirements as above."""
+    w = W["nucl8k"]
+    N, lam, sm = w["N"], w["lambda_m"], w["sigma_max"]
+    h0 = S.nucleation_film(N, N, w["ds"], w["h0"], w["eps"], w["holes"], w["depth"], w["width"], seed=w["seed"])
+    ctx64 = tf.Context(tf.params_for_workload(w, tf.TF_FP64))
+    h64 = torch.from_numpy(h0).cuda()
+    info64, rec64 = tf.tf_advance(ctx64, h64, 0.0, 6.0 / sm, w["dt0"], 4000)
+    assert info64["status"] in (tf.TF_ADV_DONE, tf.TF_ADV_RUPTURE), info64
+    acc = [r for r in rec64 if r["accepted"]]
+    ctx64.close()
+    ctx32 = tf.Context(tf.params_for_workload(w, tf.TF_FP32_BULK))
+    h32 = torch.from_numpy(h0).cuda()
+    info32, _ = tf.tf_advance(ctx32, h32, 0.0, 1e30, 1.0, len(acc), dt_replay=[r["dt"] for r in acc])
+    assert info32["accepted"] == len(acc), info32
+    m0 = float(np.sum(h0))
+    m64, m32 = float(h64.sum()), float(h32.sum())
+    assert abs(m64 - m0) <= 1e-6 * m0
+    assert abs(m32 - m0) <= 1e-6 * m0
+    km = 2 * math.pi / lam
+    q_cut = 5 * km
+    plan = tf.SpectrumPlan(N, N, w["ds"], tf.tf_spectrum_params_default(H0=w["h0"], q_cut=q_cut))
+    k64 = tf.tf_spectrum_run(plan, h64, outputs=False)["q_dominant"]
+    k32 = tf.tf_spectrum_run(plan, h32, outputs=False)["q_dominant"]
+    assert abs(k64 - k32) <= 1e-3 * km
+    assert abs(k64 - km) <= 0.25 * km
+    dmax = float(torch.max(torch.abs(h32 - h64)))
+    assert dmax <= 1e-5
+    print(f"steps={len(acc)} t={info64['t']:.1f} k_dom={k64:.5f} k_m={km:.5f} max|h32-h64|={dmax:.3e} "
+          f"mass err 64={abs(m64 - m0) / m0:.2e} 32={abs(m32 - m0) / m0:.2e}")
