@@ -209,6 +209,49 @@ def test_scale2k_prefix_parity_fp64(torch):
     assert rel <= 1e-10, rel
 
 
+def test_scale2k_full_run_to_rupture(torch):
+    """The plain method at scale in full: 2048^2 on 64 lambda_m, FP64, the
+    adaptive controller until min h < 2b (rupture).  Mass stays conserved to
+    round-off over the whole run, the run stops on rupture with min h below
+    2b, and FP32-bulk replaying the accepted step sizes stays within 1e-6 of
+    the FP64 film with the same mass and the same dominant wavenumber.
+    Near rupture some replayed steps need more than the 10 iterations FP64
+    takes at most (the FP32 solves slow the contraction a little, and the
+    large steps there contract slowly already), so the replay may take up
+    to 20."""
+    w = _workload("scale2k")
+    N = w["N"]
+    h0 = S.spinodal_film(N, N, w["h0"], w["eps"], w["seed"])
+    m0 = float(np.sum(h0))
+    ctx = tf.Context(tf.params_for_workload(w, tf.TF_FP64))
+    h = dev(torch, h0)
+    info, recs = tf.tf_advance(ctx, h, 0.0, w["T"], w["dt0"], 5000)
+    assert info["status"] == tf.TF_ADV_RUPTURE, info
+    acc = [r for r in recs if r["accepted"]]
+    assert len(acc) == info["accepted"] and len(acc) > 100
+    assert acc[-1]["hmin"] < 2 * w["b"] <= min(r["hmin"] for r in acc[:-1])
+    assert float(torch.min(h)) == acc[-1]["hmin"]
+    assert max(abs(r["mass"] - m0) for r in acc) <= 1e-12 * m0
+    ctx32 = tf.Context(tf.params_for_workload(w, tf.TF_FP32_BULK, newton_max_iter=20))
+    h32 = dev(torch, h0)
+    info32, rec32 = tf.tf_advance(ctx32, h32, 0.0, 1e30, 1.0, len(acc), dt_replay=[r["dt"] for r in acc])
+    assert info32["accepted"] == len(acc), info32
+    assert abs(float(h32.sum()) - m0) <= 1e-6 * m0
+    it64 = [r["iterations"] for r in acc]
+    it32 = [r["iterations"] for r in rec32]
+    print(f"iterations FP64 {sum(it64)} (max {max(it64)}), FP32-bulk {sum(it32)} (max {max(it32)}, "
+          f"{sum(i > 10 for i in it32)} steps over 10)")
+    assert float(torch.max(torch.abs(h32 - h))) <= 1e-6
+    km = 2 * math.pi / w["lambda_m"]
+    plan = tf.SpectrumPlan(N, N, w["ds"], tf.tf_spectrum_params_default(H0=w["h0"], q_cut=5 * km))
+    k64 = tf.tf_spectrum_run(plan, h, outputs=False)["q_dominant"]
+    k32 = tf.tf_spectrum_run(plan, h32, outputs=False)["q_dominant"]
+    assert abs(k64 - k32) <= 1e-3 * km
+    assert abs(k64 - km) <= 0.25 * km
+    print(f"attempts={info['attempts']} accepted={len(acc)} t={info['t']:.1f} hmin={acc[-1]['hmin']:.4f} "
+          f"k_dom={k64:.5f} k_m={km:.5f} max|h32-h64|={float(torch.max(torch.abs(h32 - h))):.3e}")
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_full_size_one_iteration(torch, mode):
     """8192^2 (the benchmark's grid and launch configuration): one Newton
