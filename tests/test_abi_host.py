@@ -92,7 +92,8 @@ def test_params_default():
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-3), dict(ds=0.0), dict(theta=1.5),
                                  dict(newton_max_iter=0), dict(precision=7), dict(model=9),
                                  dict(n=2, m=2), dict(b=-1.0), dict(dt_shrink=1.0),
-                                 dict(nx=70000, ny=70000)])
+                                 dict(nx=70000, ny=70000), dict(nx=65537, ny=1), dict(nx=1, ny=65537),
+                                 dict(nx=65536, ny=32768), dict(nx=46341, ny=46341)])
 def test_init_rejects_bad_parameters(bad):
     p = tf.tf_params_default(nx=16, ny=16, ds=1.0)
     for k, v in bad.items():

@@ -111,6 +111,28 @@ def test_one_iteration_parity(torch, mode, nx, ny):
 
 
 @pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("nx,ny", [(65536, 40), (40, 65536), (65536, 3), (3, 65536)])
+def test_longest_lines_one_iteration(torch, mode, nx, ny):
+    """Lines of the largest length the library takes (65536 cells: halves of
+    32768 in the twisted solves, 1366 chunks of 24): one Newton iteration
+    against the oracle over the whole grid, with the tolerances above."""
+    ds, dt = 1.9, 20.0
+    om, p = models(nx, ny, ds, mode)
+    h_old = S.spinodal_film(nx, ny, 1.0, 0.05, seed=nx + 7 * ny)
+    ctx = tf.Context(p)
+    w, v, hn = (torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3))
+    hk = dev(torch, h_old)
+    info = tf.tf_newton_iteration(ctx, hk, hk, dt, hn, w=w, v=v)
+    r = O.newton_iteration(om, h_old, O.explicit_part(om, h_old, dt), dt)
+    sw, sv = np.max(np.abs(r["w"])), np.max(np.abs(r["v"]))
+    rt = 1e-11 if mode == tf.TF_FP64 else 2e-4
+    assert np.max(np.abs(host(w) - r["w"])) <= rt * sw
+    assert np.max(np.abs(host(v) - r["v"])) <= rt * sv
+    assert np.max(np.abs(host(hn) - r["unew"])) <= 1e-14 + rt * sv
+    assert info["gnorm"] == pytest.approx(r["gnorm"], rel=1e-6)
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_step_parity(torch, mode):
     nx, ny, ds, dt = 48, 40, 3.2, 1.0
     om, p = models(nx, ny, ds, mode)
