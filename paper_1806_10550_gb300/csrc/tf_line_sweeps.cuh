@@ -502,29 +502,36 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
       // finish backward chunk t-1: update, store, reduce
       if (t >= 1) {
         const int bq = t - 1, slot = bq % 3;
-        // 2 * kRY * 32 cells of both halves over the producers, one body
-        // (unrolled twice) so that the update's code stays small
-#pragma unroll 2
-        for (int k2 = p; k2 < 2 * kRY * 32; k2 += kNP) {
-          const int h = k2 >= kRY * 32 ? 1 : 0, k = k2 - h * kRY * 32;
-          const int q = nchh(h) - 1 - bq;
-          if (q < 0) continue;
-          const int r = k >> 5, c = k & 31;
-          const int j = r0_of(h, q) + r, col = i0 + c;
-          if (j >= r1_of(h, q) || col >= nx) continue;
-          const LP x = S.s.b.xb[bq & 1][h][r][c];
-          const double uk = S.s.b.ukt[slot][h][r][c];
-          double un;
-          // one native FP64 add per cell, correctly rounded (with the float
-          // widened exactly on the FP64 pipe: fewer instructions than the
-          // integer add of tf_numeric.cuh, measured)
-          un = uk + (double)x;
-          const size_t idx = (size_t)j * nx + col;
-          unew[idx] = un;
-          if (vout) vout[idx] = to_f64(x);
-          LP ru = rel_update(x, uk);
-          if (!(ru <= err)) err = ru;
-          if (!positive_finite_bits(un)) nonfinite = 1;
+        // the 2 * kRY * 32 cells of both halves over the producers: thread p
+        // takes column p & 31 and rows rg, rg + 8, rg + 16 of each half, so
+        // the row and address arithmetic is done once per half
+        const int c = p & 31, rg = p >> 5, col = i0 + c;
+        static_assert(kRY % 8 == 0 && kNP == 256, "eight row groups of 32 columns");
+        if (col < nx) {
+#pragma unroll 1
+          for (int h = 0; h < 2; ++h) {
+            const int q = nchh(h) - 1 - bq;
+            if (q < 0) continue;
+            const int r0 = r0_of(h, q), nr = r1_of(h, q) - r0;
+            const size_t base = (size_t)(r0 + rg) * nx + col, step8 = (size_t)8 * nx;
+#pragma unroll
+            for (int i = 0; i < kRY / 8; ++i) {
+              const int r = rg + 8 * i;
+              if (r >= nr) break;
+              const LP x = S.s.b.xb[bq & 1][h][r][c];
+              const double uk = S.s.b.ukt[slot][h][r][c];
+              // one native FP64 add per cell, correctly rounded (with the
+              // float widened exactly on the FP64 pipe: fewer instructions
+              // than the integer add of tf_numeric.cuh, measured)
+              const double un = uk + (double)x;
+              const size_t idx = base + i * step8;
+              unew[idx] = un;
+              if (vout) vout[idx] = to_f64(x);
+              LP ru = rel_update(x, uk);
+              if (!(ru <= err)) err = ru;
+              if (!positive_finite_bits(un)) nonfinite = 1;
+            }
+          }
         }
       }
       // prefetch: factors two chunks ahead, u_k one chunk ahead of the solvers
