@@ -380,22 +380,22 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
             const int ja = r0 + kG * g, jb = min(r1, ja + kG);
             if (ja < jb) {
               // band in the solver's processing order (see lu_chunk)
-              LP* B = &S.s.f.band[t & 1][h][0][0][0];
-              LP* Ba = B + (h ? 4 : 0) * kRY * 32;
-              LP* Bb = B + (h ? 3 : 1) * kRY * 32;
-              LP* Bd = B + (h ? 1 : 3) * kRY * 32;
-              LP* Be = B + (h ? 0 : 4) * kRY * 32;
+              // row of cell ja + s at P + s * ks; the second half's band
+              // reversed (e..a) by swapping values, so that every store is
+              // an immediate offset from one pointer
+              LP* P = &S.s.f.band[t & 1][h][0][0][0] + (h ? r1 - 1 - ja : ja - r0) * 32 + c;
+              const int ks = h ? -32 : 32;
+              const LP* W = &S.s.f.wt[slot][h][ja - r0][c];
               const LP* T = &S.s.f.ut[slot][h][ja - r0 + 2][c + 4];  // cell ja in the tile
               auto A = [&](int s, int dr, int dc) { return T[(s + dr) * 40 + dc]; };
               auto out = [&](int s, LP a, LP b, LP cc, LP d, LP e) {
-                const int j = ja + s;
-                const int k = (h ? r1 - 1 - j : j - r0) * 32 + c;
-                Ba[k] = a;
-                Bb[k] = b;
-                B[2 * kRY * 32 + k] = cc;
-                Bd[k] = d;
-                Be[k] = e;
-                B[5 * kRY * 32 + k] = S.s.f.wt[slot][h][j - r0][c];
+                LP* q = P + s * ks;
+                q[0] = h ? e : a;
+                q[kRY * 32] = h ? d : b;
+                q[2 * kRY * 32] = cc;
+                q[3 * kRY * 32] = h ? b : d;
+                q[4 * kRY * 32] = h ? a : e;
+                q[5 * kRY * 32] = W[s * 32];
               };
               const bool edge = !(ja >= 2 && ja + kG + 1 < ny);
               if (!L.ml.pl32)  // general exponents or the linear model
@@ -654,22 +654,20 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
             const int ia = c0 + kG * g, ib = min(c1, ia + kG);
             if (ia < ib) {
               // band in the solver's processing order (see lu_chunk)
-              LP* B = &S.s.f.band[t & 1][h][0][0][0];
-              LP* Ba = B + (h ? 4 : 0) * kCX * 32;
-              LP* Bb = B + (h ? 3 : 1) * kCX * 32;
-              LP* Bd = B + (h ? 1 : 3) * kCX * 32;
-              LP* Be = B + (h ? 0 : 4) * kCX * 32;
+              // row of cell ia + s at P + s * ks, stored as in the y sweep
+              LP* P = &S.s.f.band[t & 1][h][0][0][0] + (h ? c1 - 1 - ia : ia - c0) * 32 + r;
+              const int ks = h ? -32 : 32;
+              const LP* R = &S.s.f.rt[slot][h][r][ia - c0];
               const LP* T = &S.s.f.ut[slot][h][r + 1][ia - c0 + 2];  // cell ia in the tile
               auto A = [&](int s, int dr, int dc) { return T[dr * (kCX + 5) + s + dc]; };
               auto out = [&](int s, LP a, LP b, LP c, LP d, LP e) {
-                const int i = ia + s;
-                const int k = (h ? c1 - 1 - i : i - c0) * 32 + r;
-                Ba[k] = a;
-                Bb[k] = b;
-                B[2 * kCX * 32 + k] = c;
-                Bd[k] = d;
-                Be[k] = e;
-                B[5 * kCX * 32 + k] = S.s.f.rt[slot][h][r][i - c0];
+                LP* q = P + s * ks;
+                q[0] = h ? e : a;
+                q[kCX * 32] = h ? d : b;
+                q[2 * kCX * 32] = c;
+                q[3 * kCX * 32] = h ? b : d;
+                q[4 * kCX * 32] = h ? a : e;
+                q[5 * kCX * 32] = R[s];
               };
               const bool edge = !(ia >= 2 && ia + kG + 1 < nx);
               if (!L.ml.pl32)  // general exponents or the linear model
@@ -752,15 +750,18 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
     } else {
       if (t >= 1) {  // store w of backward chunk t-1, coalesced along rows
         const int bq = t - 1;
+        static_assert((32 * kCX) % kNP == 0, "whole copy rounds");
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           const int q = nchh(h) - 1 - bq;
           if (q < 0) continue;
-          const int c0 = c0_of(h, q), c1 = c1_of(h, q);
-#pragma unroll 1
-          for (int k = p; k < 32 * kCX; k += kNP) {
-            int r = k / kCX, c = k - r * kCX;
-            if (j0 + r < ny && c0 + c < c1) rw[(size_t)(j0 + r) * nx + c0 + c] = S.s.b.xb[bq & 1][h][c][r];
+          const int c0 = c0_of(h, q), nc = c1_of(h, q) - c0;
+          LP* dst = rw + (size_t)j0 * nx + c0;
+          const LP* X = &S.s.b.xb[bq & 1][h][0][0];
+#pragma unroll
+          for (int i = 0; i < 32 * kCX / kNP; ++i) {
+            const int k = p + i * kNP, r = k / kCX, c = k - r * kCX;
+            if (j0 + r < ny && c < nc) dst[(size_t)r * nx + c] = X[c * 33 + r];
           }
         }
       }
