@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   // issue the film and w tiles of chunk q of both halves into ring slot q & 1
   auto issue_fwd = [&](int q) {
     const int slot = q & 1;
-#pragma unroll 1
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (q >= nchh(h)) continue;
       const int r0 = r0_of(h, q), r1 = r1_of(h, q);
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   // chunk order: b-th backward chunk of half h is chunk nchh(h)-1-b.
   auto issue_bwd_f = [&](int bq) {  // factor tiles of backward chunk bq
     const int slot = bq % 3;
-#pragma unroll 1
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int q = nchh(h) - 1 - bq;
       if (q < 0) continue;
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   };
   auto issue_bwd_u = [&](int bq) {  // u_k tiles of backward chunk bq
     const int slot = bq % 3;
-#pragma unroll 1
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int q = nchh(h) - 1 - bq;
       if (q < 0) continue;
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
 
   auto issue_fwd = [&](int q) {
     const int slot = q & 1;
-#pragma unroll 1
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (q >= nchh(h)) continue;
       const int c0 = c0_of(h, q), c1 = c1_of(h, q);
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
   __syncthreads();
   auto issue_bwd = [&](int bq) {
     const int slot = bq % 3;
-#pragma unroll 1
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int q = nchh(h) - 1 - bq;
       if (q < 0) continue;
