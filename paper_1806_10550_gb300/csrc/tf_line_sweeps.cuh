@@ -247,8 +247,7 @@ __device__ __forceinline__ void band_rows(const LineK<LP>& L, Acc A, int ia, int
 template <class LP, int L>
 __device__ __forceinline__ void lu_chunk(LUState<LP>& lu, const LP* B, int lane, int n, LP* Q, int& bad) {
   LP chk = LP(0);
-#pragma unroll 8
-  for (int s = 0; s < n; ++s) {
+  auto one = [&](int s) {
     const int k = s * 32 + lane;
     LP g, dl, z;
     lu.step(B[k], B[L * 32 + k], B[2 * L * 32 + k], B[3 * L * 32 + k], B[4 * L * 32 + k], B[5 * L * 32 + k],
@@ -256,6 +255,13 @@ __device__ __forceinline__ void lu_chunk(LUState<LP>& lu, const LP* B, int lane,
     Q[s * 32] = g;
     Q[L * 32 + s * 32] = dl;
     Q[2 * L * 32 + s * 32] = z;
+  };
+  if (n == L) {  // a whole chunk: every address is an immediate offset
+#pragma unroll
+    for (int s = 0; s < L; ++s) one(s);
+  } else {
+#pragma unroll 8
+    for (int s = 0; s < n; ++s) one(s);
   }
   if (!(chk == chk)) bad = 1;
 }
@@ -277,7 +283,7 @@ template <int L> __host__ __device__ inline size_t fac_slab(int blk, int h, int 
 // processing order s = 0..n-1 (outward from the seam).  F(f, s) reads factor
 // f (g, d, z) of cell s; cells with IS_SEAM(s) take the seam solution XS(s);
 // PUT(s, x) stores x.  Chunks without seam cells run unrolled.
-template <class LP, class Fac, class SeamF, class XsF, class Put>
+template <class LP, int L, class Fac, class SeamF, class XsF, class Put>
 __device__ __forceinline__ void bs_chunk(LP& x1, LP& x2, int n, bool any_seam, Fac F, SeamF is_seam,
                                          XsF xs, Put put) {
   auto one = [&](int s, bool chk) {
@@ -286,7 +292,10 @@ __device__ __forceinline__ void bs_chunk(LP& x1, LP& x2, int n, bool any_seam, F
     x1 = x;
     put(s, x);
   };
-  if (!any_seam) {
+  if (!any_seam && n == L) {
+#pragma unroll
+    for (int s = 0; s < L; ++s) one(s, false);
+  } else if (!any_seam) {
 #pragma unroll 8
     for (int s = 0; s < n; ++s) one(s, false);
   } else {
@@ -495,7 +504,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
             const int j = r0 + rb + rs * s;
             return twisted && (h ? j <= m + 1 : j >= m - 2);
           };
-          bs_chunk<LP>(x1, x2, n, twisted && (h ? r0 <= m + 1 : r1 > m - 2), F, is_seam, xs, put);
+          bs_chunk<LP, kRY>(x1, x2, n, twisted && (h ? r0 <= m + 1 : r1 > m - 2), F, is_seam, xs, put);
         }
       }
     } else {
@@ -508,7 +517,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
         const int c = p & 31, rg = p >> 5, col = i0 + c;
         static_assert(kRY % 8 == 0 && kNP == 256, "eight row groups of 32 columns");
         if (col < nx) {
-#pragma unroll 1
+#pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int q = nchh(h) - 1 - bq;
             if (q < 0) continue;
@@ -744,14 +753,14 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
             const int i = c0 + cb + cs * s;
             return twisted && (h ? i <= m + 1 : i >= m - 2);
           };
-          bs_chunk<LP>(x1, x2, n, twisted && (h ? c0 <= m + 1 : c1 > m - 2), F, is_seam, xs, put);
+          bs_chunk<LP, kCX>(x1, x2, n, twisted && (h ? c0 <= m + 1 : c1 > m - 2), F, is_seam, xs, put);
         }
       }
     } else {
       if (t >= 1) {  // store w of backward chunk t-1, coalesced along rows
         const int bq = t - 1;
         static_assert((32 * kCX) % kNP == 0, "whole copy rounds");
-#pragma unroll 1
+#pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int q = nchh(h) - 1 - bq;
           if (q < 0) continue;
