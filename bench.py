@@ -257,7 +257,7 @@ def kernel_table(res, N, lp):
 # from the ncu capture summarised in profiles/iteration_kernels_f32b_prof4k.md
 # (4096^2; traffic scales with the cells).  Valid for the kernels as
 # captured; set an entry to None when that kernel changes.
-TRAFFIC_PER_CELL_F32B = {"rhs": 22.26, "x_sweep": None, "y_sweep": None, "explicit": None}
+TRAFFIC_PER_CELL_F32B = {"rhs": 22.31, "x_sweep": 31.42, "y_sweep": 44.57, "explicit": None}
 
 
 def roofline_hbm(res, N, lp_bytes, pk, traffic_per_cell=None):
