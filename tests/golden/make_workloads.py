@@ -34,7 +34,7 @@ ensemble  256 independent films (the many-film statistics runs of Sec.
           512, 1024, contact angle uniform in [10, 40] deg (numpy
           default_rng(1240)), power law, h0 = 1, eps = 0.01, each on
           16 lambda_m of its own (so N/16 cells per wavelength), dt0 =
-          1e-7/sigma_max, dt_max = 0.01/sigma_max, 30 attempts per film.
+          1e-7/sigma_max, dt_max = 0.01/sigma_max, 500 attempts per film.
 
 spectrum8k  the radial Fourier analysis (App. Radial Fourier Transform) of
           an 8192^2 film at scale8k's spacing (lambda_m / 128): a ring film
@@ -92,7 +92,7 @@ def main():
         lv = 2.0 * math.pi / qv
         films.append(dict(N=N, theta_c_deg=thc, kappa=kv, lambda_m=lv, sigma_max=sv,
                           ds=16.0 * lv / N, seed=2000 + i, dt0=1e-7 / sv, dt_max=0.01 / sv))
-    W["ensemble"] = dict(common, P=16, eps=0.01, attempts=30, films=films)
+    W["ensemble"] = dict(common, P=16, eps=0.01, attempts=500, films=films)
     W["spectrum8k"] = dict(common, N=8192, P=64, ds=64 * lam / 8192, seed=1241, eps=0.05,
                            spread=0.05, modes=256, noise=0.002, q_cut=5.0 * qm, sigma=1.0,
                            points_per_interval=10, n_eval=400, steps=50)
