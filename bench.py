@@ -260,6 +260,14 @@ def kernel_table(res, N, lp):
 TRAFFIC_PER_CELL_F32B = {"rhs": 22.31, "x_sweep": 31.42, "y_sweep": 44.57, "explicit": None}
 
 
+def ncu_counters_apply(w) -> bool:
+    """True when workload w runs the kernels that the ncu counters behind
+    TRAFFIC_PER_CELL_F32B and FP64_FLOPS_PER_CELL were taken on: those of the
+    (3, 2) power law.  The other models evaluate their mobilities in other
+    code (an out-of-line call per cell, Pi in FP64 inside the residual)."""
+    return w.get("model", 0) == 0 and (w["n"], w["m"]) == (3, 2)
+
+
 def roofline_hbm(res, N, lp_bytes, pk, traffic_per_cell=None):
     """Dominant kernel (largest total time): achieved algorithmic GB/s; plus
     the whole Newton iteration (all three kernels) against the same peak."""
@@ -889,9 +897,7 @@ def main():
                                    dist, e2e_steps=args.e2e_steps, clocks=clocks)
     head = "f32b" if "f32b" in res else "fp64"
     R = res[head]
-    # the ncu counters behind TRAFFIC_PER_CELL_F32B and FP64_FLOPS_PER_CELL were
-    # taken on the kernels of the (3, 2) power law; other models run other code
-    profiled = w.get("model", 0) == 0 and (w["n"], w["m"]) == (3, 2)
+    profiled = ncu_counters_apply(w)
     acc_local = R["info"]["accepted"]
     acc_all = sum_over_ranks(dist, acc_local)
     value = N * N * acc_all / (R["ms"] * 1e-3)
