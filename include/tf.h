@@ -107,7 +107,10 @@ typedef struct tf_ctx tf_ctx;
 typedef struct {
   double gnorm; /* max |G| over the grid                                     */
   double mass;  /* sum of the grid values (of h_k): each value rounded to a
-                   multiple of 2^-36, summed exactly (heights below 16)   */
+                   multiple of 2^-36 and summed exactly in 128-bit integer
+                   arithmetic (heights below 2^27), so the sum does not
+                   depend on the order of the additions; converted to
+                   double once                                          */
   double hmin;  /* min of h_k                                                 */
 } tf_norms;
 
@@ -246,11 +249,13 @@ int tf_timing_get(const tf_ctx* ctx, tf_timing* out);
  * every allocation, a latency-bounded loop, a plugin handed buffers but no
  * right to create a context).  It computes what tf_residual computes,
  *   G = h_k + theta dt D(h_k) - [h_old - (1-theta) dt D(h_old)],
- * for the parameters *p (validated as tf_init does; workspace-free) on the
- * given stream (cudaStream_t as void*, NULL = legacy default stream).
+ * for the parameters *p on the given stream (cudaStream_t as void*, NULL = legacy default stream).
  * h_k, h_old: device grids [ny][nx]; G: device output grid (required);
  * out: host struct or NULL (gnorm = max|G|, mass and hmin of h_k; when
  * given, the call synchronises the stream).
+ * Models: TF_MODEL_POWERLAW and TF_MODEL_LINEAR only (TF_MODEL_NLC and
+ * TF_MODEL_POLYMER return TF_ERR_ARG); the other fields of *p are checked
+ * as tf_init checks them.
  * Scratch: one fixed device array of this library (TF_NOALLOC_MAX_CELLS
  * cells plus partial results, about 16.3 MiB), present on every GPU that
  * loads the library until the process exits; grids larger than

@@ -27,7 +27,6 @@ int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? TF_ERR_NO
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-double mass_of(double fixed) { return fixed * 0x1p-36; }
 
 // Reduce the partials of the last passes into the pinned c.hsc: the launch
 // and the copy are queued on the context's stream; finalize() also waits.
@@ -145,7 +144,7 @@ void fill_info(tf_step_info* info, int status, int it, const Scalars& s) {
   info->iterations = it;
   info->err = s.err;
   info->gnorm = s.gnorm;
-  info->mass = mass_of(s.mass);
+  info->mass = tf::mass_value(s.mass);
   info->hmin = s.hmin;
 }
 
@@ -529,7 +528,7 @@ int tf_residual(tf_ctx* c, const double* h_k, const double* h_old, double dt, do
   if (r) return r;
   if (out) {
     out->gnorm = c->hsc->gnorm;
-    out->mass = mass_of(c->hsc->mass);
+    out->mass = tf::mass_value(c->hsc->mass);
     out->hmin = c->hsc->hmin;
   }
   return TF_OK;

@@ -55,14 +55,34 @@ struct PartX {  // per-block partial results of the x pass
   int pivot;
   int pad;
 };
+// Exact sums of the 2^-36 fixed-point images of grid values (the mass
+// diagnostic): a 128-bit unsigned integer as two 64-bit words, so no grid
+// the library accepts (fewer than 2^31 cells, each image below 2^63) can
+// overflow it, and the sum does not depend on the order of the additions.
+struct Mass128 {
+  unsigned long long lo, hi;
+};
+TF_HD void mass_add(Mass128& a, unsigned long long v) {
+  a.lo += v;
+  a.hi += a.lo < v ? 1ull : 0ull;
+}
+TF_HD void mass_add(Mass128& a, const Mass128& b) {
+  a.lo += b.lo;
+  a.hi += b.hi + (a.lo < b.lo ? 1ull : 0ull);
+}
+// The sum as a double (the value times 2^-36), converted once at the end.
+inline double mass_value(const Mass128& m) {
+  return m.hi ? ldexp((double)m.hi, 28) + ldexp((double)m.lo, -36) : ldexp((double)m.lo, -36);
+}
+
 struct PartY {  // per-block partial results of the y pass
   double err, hmin;
-  long long mass;
+  Mass128 mass;
   int nonfinite, pivot;
 };
 struct Scalars {
   double err, gnorm, hmin;
-  double mass;  // sum of the 2^-36 fixed-point images of the grid values
+  Mass128 mass;  // exact sum of the 2^-36 fixed-point images of the grid values
   int nonfinite, pivot;
 };
 
@@ -592,10 +612,12 @@ __device__ __forceinline__ bool positive_finite_bits(double u) {
 static __global__ void __launch_bounds__(256)
     k_finalize(const PartX* __restrict__ px, int nx_part, const PartY* __restrict__ py, int ny_part,
                Scalars* __restrict__ out) {
-  __shared__ double s_err[256], s_g[256], s_h[256], s_m[256];
+  __shared__ double s_err[256], s_g[256], s_h[256];
+  __shared__ Mass128 s_m[256];
   __shared__ int s_nf[256], s_pv[256];
   const int t = threadIdx.x;
-  double err = 0.0, g = 0.0, h = INFINITY, m = 0.0;
+  double err = 0.0, g = 0.0, h = INFINITY;
+  Mass128 m = {0ull, 0ull};
   int nf = 0, pv = 0;
   for (int k = t; k < nx_part; k += 256) {
     if (!(px[k].gnorm <= g)) g = px[k].gnorm;
@@ -604,7 +626,7 @@ static __global__ void __launch_bounds__(256)
   for (int k = t; k < ny_part; k += 256) {
     if (!(py[k].err <= err)) err = py[k].err;
     h = fmin(h, py[k].hmin);
-    m += (double)py[k].mass;
+    mass_add(m, py[k].mass);
     nf |= py[k].nonfinite;
     pv |= py[k].pivot;
   }
@@ -620,7 +642,7 @@ static __global__ void __launch_bounds__(256)
       if (!(s_err[t + o] <= s_err[t])) s_err[t] = s_err[t + o];
       if (!(s_g[t + o] <= s_g[t])) s_g[t] = s_g[t + o];
       s_h[t] = fmin(s_h[t], s_h[t + o]);
-      s_m[t] += s_m[t + o];
+      mass_add(s_m[t], s_m[t + o]);
       s_nf[t] |= s_nf[t + o];
       s_pv[t] |= s_pv[t + o];
     }
@@ -643,13 +665,13 @@ static __global__ void __launch_bounds__(256)
     k_grid_stats(const double* __restrict__ u, size_t N, PartY* __restrict__ part) {
   // min over positive values through their bit patterns (integer compares)
   unsigned long long hb = 0x7ff0000000000000ull;
-  long long m = 0;
+  Mass128 m = {0ull, 0ull};
   int nf = 0;
   auto take = [&](double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     if (!positive_finite_bits(v)) nf = 1;
     else if (b < hb) hb = b;
-    m += fixed36_of_f64(v);
+    mass_add(m, (unsigned long long)fixed36_of_f64(v));
   };
   const size_t T = (size_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   size_t done = 0;
@@ -671,11 +693,14 @@ static __global__ void __launch_bounds__(256)
   for (int o = 16; o > 0; o >>= 1) {
     unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hb, o);
     if (h2 < hb) hb = h2;
-    m += __shfl_xor_sync(0xffffffffu, m, o);
+    Mass128 m2;
+    m2.lo = __shfl_xor_sync(0xffffffffu, m.lo, o);
+    m2.hi = __shfl_xor_sync(0xffffffffu, m.hi, o);
+    mass_add(m, m2);
     nf |= __shfl_xor_sync(0xffffffffu, nf, o);
   }
   __shared__ unsigned long long sh[8];
-  __shared__ long long sm[8];
+  __shared__ Mass128 sm[8];
   __shared__ int sn[8];
   if ((threadIdx.x & 31) == 0) {
     sh[threadIdx.x >> 5] = hb;
@@ -685,11 +710,11 @@ static __global__ void __launch_bounds__(256)
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long hbb = sh[0];
-    long long mb = sm[0];
+    Mass128 mb = sm[0];
     int nb = sn[0];
     for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
       if (sh[k] < hbb) hbb = sh[k];
-      mb += sm[k];
+      mass_add(mb, sm[k]);
       nb |= sn[k];
     }
     PartY p;

@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
     PartY pp;
     pp.err = (double)err;
     pp.hmin = INFINITY;
-    pp.mass = 0;
+    pp.mass.lo = pp.mass.hi = 0ull;
     pp.nonfinite = nonfinite;
     pp.pivot = pivot_bad;
     S.part[warp] = pp;
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
       const PartY& b = S.part[k];
       if (!(b.err <= a.err)) a.err = b.err;
       if (b.hmin < a.hmin) a.hmin = b.hmin;
-      a.mass += b.mass;
+      mass_add(a.mass, b.mass);
       a.nonfinite |= b.nonfinite;
       a.pivot |= b.pivot;
     }

@@ -139,7 +139,7 @@ extern "C" int tf_residual_noalloc(const tf_params* p, void* stream, const doubl
         cudaStreamSynchronize(s) != cudaSuccess)
       return TF_ERR_CUDA;
     out->gnorm = h.gnorm;
-    out->mass = h.mass * 0x1p-36;
+    out->mass = tf::mass_value(h.mass);
     out->hmin = h.hmin;
   }
   return TF_OK;
