@@ -53,9 +53,9 @@ def peaks() -> dict:
 FP64_TFLOPS = 1.0
 
 # FP64 operations executed per cell by each FP64-mode kernel (DFMA counted
-# as 2, DADD and DMUL as 1), from the ncu capture summarised in
-# profiles/iteration_kernels_fp64_prof4k.md (4096^2; per cell they do not
-# depend on the grid size).  Valid for the kernels as captured.
+# as 2, DADD and DMUL as 1), from an ncu capture of the FP64-mode kernels at
+# 4096^2 (per cell they do not depend on the grid size).  Valid for the
+# kernels as captured.
 FP64_FLOPS_PER_CELL = {"rhs": 46.14, "x_sweep": 86.90, "y_sweep": 103.90}
 
 
@@ -180,8 +180,8 @@ def run_mode(tf, torch, w, h0, mode, warmup, steps, dist, replay=None, e2e_steps
     wall0 = time.perf_counter()
     if clocks:
         clocks.__enter__()
-    if replay is None:
-        info, recs = tf.tf_advance(ctx, h, t0, 1e30, dt, steps)
+    if replay is None:  # the controller continues from the warm-up's state
+        info, recs = tf.tf_advance(ctx, h, t0, 1e30, dt, steps, streak=info_w["streak"])
     else:
         info, recs = tf.tf_advance(ctx, h, t0, 1e30, 1.0, steps,
                                    dt_replay=replay[warmup:warmup + steps])
@@ -254,9 +254,9 @@ def kernel_table(res, N, lp):
 
 
 # DRAM bytes (read + write) per cell per launch of each FP32-bulk kernel,
-# from the ncu capture summarised in profiles/iteration_kernels_f32b_prof4k.md
-# (4096^2; traffic scales with the cells).  Valid for the kernels as
-# captured; set an entry to None when that kernel changes.
+# from an ncu capture of the FP32-bulk kernels at 4096^2 (traffic scales
+# with the cells).  Valid for the kernels as captured; set an entry to None
+# when that kernel changes.
 TRAFFIC_PER_CELL_F32B = {"rhs": 22.31, "x_sweep": 31.42, "y_sweep": 44.57, "explicit": None}
 
 
@@ -375,7 +375,8 @@ def reference_arm(args, w):
                 ms_per_step=el * 1e3 / max(1, args.steps), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 impl="reference",
-                config=headline_config(w, args.gpus, replayed="fp64" in args.modes),
+                config=dict(headline_config(w, args.gpus, replayed="fp64" in args.modes),
+                            sample=f"{n}x{n}"),
                 cpu_baseline=dict(value=value, unit="cell-updates/s", cores=O.num_threads(),
                                   kind="oracle",
                                   sample=(f"{acc} accepted FP64 oracle steps of a {n}^2 sample of the "

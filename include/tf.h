@@ -199,10 +199,15 @@ int tf_newton_adi_step(tf_ctx* ctx, const double* h_old, double* h_new, double d
  * if iter_replay != NULL, exactly iter_replay[a] Newton iterations, with
  * no controller; a failed replayed step ends the call with TF_ADV_DT_MIN.
  * records: host array of max_attempts entries or NULL.  info: host, required.
+ * streak: host int or NULL, the controller's count of consecutive accepted
+ * steps since dt last changed: read at the start (NULL = 0; negative values
+ * are refused) and written at the end, so a run split over several calls,
+ * each given the previous call's t, dt and streak, makes the same decisions
+ * and grids as one call.
  * Returns TF_OK or a negative error.                                     */
 int tf_advance(tf_ctx* ctx, double* h, double t0, double t_end, double dt0,
                int max_attempts, const double* dt_replay, const int* iter_replay,
-               tf_step_record* records, tf_advance_info* info);
+               tf_step_record* records, tf_advance_info* info, int* streak);
 
 /* Advance n independent films together.  Film i is advanced exactly as
  * tf_advance(ctx[i], h[i], t0[i], t_end[i], dt0[i], max_attempts[i], NULL,
@@ -214,13 +219,15 @@ int tf_advance(tf_ctx* ctx, double* h, double t0, double t_end, double dt0,
  * implementation).  Give each context its own stream: contexts that share a
  * stream are correct but serialised.  ctx: n distinct contexts; h: n device
  * grids, each of its context's shape (advanced in place); t0, t_end, dt0,
- * max_attempts: n host values each; info: n host records, required.
+ * max_attempts: n host values each; info: n host records, required;
+ * streak: n host values (each film's accept streak, in and out, as in
+ * tf_advance) or NULL.
  * Returns TF_OK, or a negative error at the first failing call (work of
  * other films may then still be queued: synchronise or destroy the
  * contexts).                                                             */
 int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const double* t0,
                         const double* t_end, const double* dt0, const int* max_attempts,
-                        tf_advance_info* info);
+                        tf_advance_info* info, int* streak);
 
 /* Kernel timing of a context, for measurement.  While enabled, the library
  * records CUDA events on its stream around every kernel it launches and

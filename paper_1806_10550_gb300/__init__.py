@@ -133,10 +133,10 @@ def library(build_if_missing: bool = True):
     L.tf_newton_iteration.argtypes = [vp, vp, vp, dp, vp, vp, vp, C.POINTER(TfStepInfo)]
     L.tf_newton_adi_step.argtypes = [vp, vp, vp, dp, C.POINTER(TfStepInfo)]
     L.tf_advance.argtypes = [vp, vp, dp, dp, dp, C.c_int, vp, vp, C.POINTER(TfStepRecord),
-                             C.POINTER(TfAdvanceInfo)]
+                             C.POINTER(TfAdvanceInfo), C.POINTER(C.c_int)]
     L.tf_ensemble_advance.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(dp),
                                       C.POINTER(dp), C.POINTER(dp), C.POINTER(C.c_int),
-                                      C.POINTER(TfAdvanceInfo)]
+                                      C.POINTER(TfAdvanceInfo), C.POINTER(C.c_int)]
     L.tf_timing_enable.argtypes = [vp, C.c_int]
     L.tf_timing_get.argtypes = [vp, C.POINTER(TfTiming)]
     L.tf_adjoint_step.argtypes = [vp, vp, dp, C.c_int, vp, vp, vp, C.POINTER(dp), C.POINTER(dp)]
@@ -276,8 +276,12 @@ def tf_newton_adi_step(ctx: Context, h_old, h_new, dt: float) -> dict:
 
 
 def tf_advance(ctx: Context, h, t0: float, t_end: float, dt0: float, max_attempts: int,
-               dt_replay=None, iter_replay=None, records: bool = True):
-    """Advance ``h`` in place; returns (info dict, list of per-attempt records)."""
+               dt_replay=None, iter_replay=None, records: bool = True, streak: int = 0):
+    """Advance ``h`` in place; returns (info dict, list of per-attempt records).
+
+    ``streak`` is the controller's count of consecutive accepted steps at the
+    start; the info dict's ``streak`` is its value at the end, so passing a
+    call's ``t``, ``dt`` and ``streak`` to the next continues the same run."""
     import numpy as np
     recs = (TfStepRecord * max(1, max_attempts))() if records else None
     dtr = itr = None
@@ -292,23 +296,27 @@ def tf_advance(ctx: Context, h, t0: float, t_end: float, dt0: float, max_attempt
             raise ValueError("iter_replay shorter than max_attempts")
         itr = C.c_void_p(itr_a.ctypes.data)
     info = TfAdvanceInfo()
+    st = C.c_int(int(streak))
     _check(library().tf_advance(ctx.handle, ctx.ptr(h, "h"), float(t0), float(t_end), float(dt0),
-                                int(max_attempts), dtr, itr, recs, C.byref(info)), "tf_advance")
+                                int(max_attempts), dtr, itr, recs, C.byref(info), C.byref(st)),
+           "tf_advance")
     out = []
     if records:
         for r in recs[: info.attempts]:
             out.append(dict(t=r.t, dt=r.dt, accepted=bool(r.accepted), iterations=r.iterations,
                             status=r.status, err=r.err, gnorm=r.gnorm, mass=r.mass, hmin=r.hmin))
     return dict(status=info.status, attempts=info.attempts, accepted=info.accepted,
-                newton_iterations=info.newton_iterations, t=info.t, dt=info.dt), out
+                newton_iterations=info.newton_iterations, t=info.t, dt=info.dt,
+                streak=st.value), out
 
 
-def tf_ensemble_advance(ctxs, hs, t0, t_end, dt0, max_attempts):
+def tf_ensemble_advance(ctxs, hs, t0, t_end, dt0, max_attempts, streak=0):
     """Advance independent films together (``tf_advance`` on each, their
     work interleaved on the contexts' streams).  ``ctxs``: contexts, one per
     film, each best on its own stream; ``hs``: their grids (advanced in
-    place); ``t0``, ``t_end``, ``dt0``, ``max_attempts``: one value or one per
-    film.  Returns one info dict per film."""
+    place); ``t0``, ``t_end``, ``dt0``, ``max_attempts``, ``streak``: one
+    value or one per film.  Returns one info dict per film (with its
+    ``streak`` at the end)."""
     n = len(ctxs)
     if len(hs) != n:
         raise ValueError("one grid per context")
@@ -322,11 +330,13 @@ def tf_ensemble_advance(ctxs, hs, t0, t_end, dt0, max_attempts):
     ctx_a = (C.c_void_p * max(1, n))(*[c.handle.value for c in ctxs])
     h_a = (C.c_void_p * max(1, n))(*[c.ptr(h, "h").value for c, h in zip(ctxs, hs)])
     infos = (TfAdvanceInfo * max(1, n))()
+    st = arr(streak, C.c_int)
     _check(library().tf_ensemble_advance(n, ctx_a, h_a, arr(t0, C.c_double), arr(t_end, C.c_double),
-                                         arr(dt0, C.c_double), arr(max_attempts, C.c_int), infos),
+                                         arr(dt0, C.c_double), arr(max_attempts, C.c_int), infos, st),
            "tf_ensemble_advance")
     return [dict(status=i.status, attempts=i.attempts, accepted=i.accepted,
-                 newton_iterations=i.newton_iterations, t=i.t, dt=i.dt) for i in infos[:n]]
+                 newton_iterations=i.newton_iterations, t=i.t, dt=i.dt, streak=st[k])
+            for k, i in enumerate(infos[:n])]
 
 
 def tf_adjoint_step(ctx: Context, h_old, dt: float, K: int, g, g_h=None, h_new=None) -> dict:

@@ -191,6 +191,7 @@ struct FilmRun {
   double t, t_end, dt;
   int max_att;
   tf_advance_info* info;
+  int* streak_io;  // the caller's accept streak (in and out), or NULL
   double *cur, *nxt;
   int streak, a, status;
   bool done;
@@ -206,6 +207,7 @@ int film_finish(FilmRun& F) {
   if (F.status == TF_ADV_MAX_ATTEMPTS && F.t >= F.t_end) F.status = TF_ADV_DONE;
   if (F.cur != F.h)
     TF_CK(cudaMemcpyAsync(F.h, F.cur, F.c->N * sizeof(double), cudaMemcpyDeviceToDevice, F.c->stream));
+  if (F.streak_io) *F.streak_io = F.streak;
   F.info->status = F.status;
   F.info->attempts = F.a;
   F.info->t = F.t;
@@ -556,14 +558,15 @@ int tf_newton_adi_step(tf_ctx* c, const double* h_old, double* h_new, double dt,
 
 int tf_advance(tf_ctx* c, double* h, double t0, double t_end, double dt0, int max_attempts,
                const double* dt_replay, const int* iter_replay, tf_step_record* records,
-               tf_advance_info* info) {
+               tf_advance_info* info, int* streak_io) {
   if (!c || !h || !info || max_attempts < 0 || !(dt0 > 0.0) || !isfinite(t0)) return TF_ERR_ARG;
+  if (streak_io && *streak_io < 0) return TF_ERR_ARG;
   memset(info, 0, sizeof(*info));
   const tf_params& P = c->p;
   double* cur = h;
   double* nxt = c->ubuf2;
   double t = t0, dt = dt0;
-  int streak = 0, a = 0, status = TF_ADV_MAX_ATTEMPTS;
+  int streak = streak_io ? *streak_io : 0, a = 0, status = TF_ADV_MAX_ATTEMPTS;
   while (a < max_attempts) {
     if (t >= t_end) {
       status = TF_ADV_DONE;
@@ -630,6 +633,7 @@ int tf_advance(tf_ctx* c, double* h, double t0, double t_end, double dt0, int ma
     TF_CK(cudaMemcpyAsync(h, cur, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     TF_CK(cudaStreamSynchronize(c->stream));
   }
+  if (streak_io) *streak_io = streak;
   info->status = status;
   info->attempts = a;
   info->t = t;
@@ -639,11 +643,12 @@ int tf_advance(tf_ctx* c, double* h, double t0, double t_end, double dt0, int ma
 
 int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const double* t0,
                         const double* t_end, const double* dt0, const int* max_attempts,
-                        tf_advance_info* info) {
+                        tf_advance_info* info, int* streak) {
   if (n < 0 || (n > 0 && (!ctx || !h || !t0 || !t_end || !dt0 || !max_attempts || !info)))
     return TF_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     if (!ctx[i] || !h[i] || max_attempts[i] < 0 || !(dt0[i] > 0.0) || !isfinite(t0[i])) return TF_ERR_ARG;
+    if (streak && streak[i] < 0) return TF_ERR_ARG;
     for (int j = 0; j < i; ++j)
       if (ctx[j] == ctx[i]) return TF_ERR_ARG;  // one context per film
   }
@@ -660,6 +665,8 @@ int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const doubl
     f.max_att = max_attempts[i];
     f.info = &info[i];
     memset(f.info, 0, sizeof(*f.info));
+    f.streak_io = streak ? &streak[i] : nullptr;
+    f.streak = streak ? streak[i] : 0;
     f.cur = h[i];
     f.nxt = ctx[i]->ubuf2;
     f.status = TF_ADV_MAX_ATTEMPTS;

@@ -109,7 +109,7 @@ def test_null_arguments_rejected():
     assert L.tf_init(None, None, None) == tf.TF_ERR_ARG
     assert L.tf_newton_adi_step(None, None, None, 1.0, None) == tf.TF_ERR_ARG
     assert L.tf_residual(None, None, None, 1.0, None, None) == tf.TF_ERR_ARG
-    assert L.tf_advance(None, None, 0.0, 1.0, 1.0, 1, None, None, None, None) == tf.TF_ERR_ARG
+    assert L.tf_advance(None, None, 0.0, 1.0, 1.0, 1, None, None, None, None, None) == tf.TF_ERR_ARG
     assert tf.tf_strerror(tf.TF_ERR_ARG) == "invalid argument"
     L.tf_destroy(None)
     out = C.c_void_p(123)
