@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtfadi.so")
-UNITS = ["tf_api", "tf_mode_fp64", "tf_mode_f32b", "tf_noalloc", "tf_spectrum", "tf_adjoint"]
+UNITS = ["tf_api", "tf_mode_fp64", "tf_mode_f32b", "tf_part", "tf_noalloc", "tf_spectrum", "tf_adjoint"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -36,6 +36,14 @@ int finalize_async(tf_ctx& c, int n_px, int n_py) {
   TF_CK(cudaMemcpyAsync(c.hsc, c.dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
   return TF_OK;
 }
+// The same after an iteration of the partitioned path: the residual's
+// partials and the accumulators of the partitioned kernels.
+int finalize_part_async(tf_ctx& c) {
+  TF_CK(tf::part::finalize(c));
+  TF_CK(cudaGetLastError());
+  TF_CK(cudaMemcpyAsync(c.hsc, c.dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
+  return TF_OK;
+}
 int finalize(tf_ctx& c, int n_px, int n_py) {
   int r = finalize_async(c, n_px, n_py);
   if (r) return r;
@@ -66,7 +74,7 @@ int iterate_launch(tf_ctx& c, const double* u_k, double dt, double* u_next, doub
   if (tm) TF_CK(cudaEventRecord(c.ev[3], c.stream));
   TF_CK(c.ops->ysweep(c, u_k, dt, u_next, v_out));
   if (tm) TF_CK(cudaEventRecord(c.ev[4], c.stream));
-  return finalize_async(c, c.n_rhs_parts + c.grid_x, c.grid_y);
+  return c.part ? finalize_part_async(c) : finalize_async(c, c.n_rhs_parts + c.grid_x, c.grid_y);
 }
 void iterate_collect(tf_ctx& c, bool w_out, Scalars* s) {
   if (c.timing.enabled) {
@@ -78,7 +86,8 @@ void iterate_collect(tf_ctx& c, bool w_out, Scalars* s) {
     c.timing.y_ms += elapsed(c.ev[3], c.ev[4]);
     c.timing.x_launches++;
     c.timing.y_launches++;
-    c.timing.launches += (c.rhs_fused ? 3 : 4) + (w_out && c.ops->lp_bytes != sizeof(double) ? 1 : 0);
+    const int sweeps = c.part ? tf::part::launches(c) : 2;
+    c.timing.launches += (c.rhs_fused ? 2 : 3) + sweeps + (w_out && c.ops->lp_bytes != sizeof(double) ? 1 : 0);
   }
   *s = *c.hsc;
 }
@@ -398,6 +407,11 @@ void tf_destroy(tf_ctx* c) {
   cudaFree(c->ulp);
   cudaFree(c->fac_x);
   cudaFree(c->fac_y);
+  cudaFree(c->recx);
+  cudaFree(c->recy);
+  cudaFree(c->xsx);
+  cudaFree(c->xsy);
+  cudaFree(c->acc);
   cudaFree(c->ubuf);
   cudaFree(c->ubuf2);
   cudaFree(c->px);
@@ -496,8 +510,21 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   if (!r) r = dalloc(&c->bn, c->N * hp);
   if (!r) r = dalloc(&c->w, c->N * lp);
   if (!r && lp != sizeof(double)) r = dalloc(&c->ulp, c->N * lp);
-  if (!r) r = dalloc(&c->fac_x, facx * lp);
-  if (!r) r = dalloc(&c->fac_y, facy * lp);
+  c->part = c->packed_rhs;
+  c->nsx = tf::part::nseg_x(p->nx);
+  c->nsy = tf::part::nseg_y(p->ny);
+  if (c->part) {
+    const size_t rx = (size_t)(c->nsx - 1) * p->ny, ry = (size_t)(c->nsy - 1) * p->nx;
+    if (!r) r = dalloc(&c->recx, rx * tf::part::kRecordValues * sizeof(float));
+    if (!r) r = dalloc(&c->recy, ry * tf::part::kRecordValues * sizeof(float));
+    if (!r) r = dalloc(&c->xsx, rx * 2 * sizeof(float));
+    if (!r) r = dalloc(&c->xsy, ry * 2 * sizeof(float));
+    if (!r) r = dalloc(&c->acc, tf::part::acc_bytes());
+    if (!r && cudaMemset(c->acc, 0, tf::part::acc_bytes()) != cudaSuccess) r = TF_ERR_CUDA;
+  } else {
+    if (!r) r = dalloc(&c->fac_x, facx * lp);
+    if (!r) r = dalloc(&c->fac_y, facy * lp);
+  }
   if (!r) r = dalloc(&c->ubuf, c->N * sizeof(double));
   if (!r) r = dalloc(&c->ubuf2, c->N * sizeof(double));
   if (!r) r = dalloc(&c->px, (size_t)c->n_px * sizeof(tf::PartX));

@@ -33,6 +33,24 @@ struct Ops {
 extern const Ops ops_fp64;
 extern const Ops ops_f32b;
 
+// Partitioned line solves of the FP32-bulk path (tf_part.cu, kernels in
+// tf_partition.cuh).
+namespace part {
+struct Acc;
+constexpr int kRecordValues = 20;  // reduced-system values per separator and line
+int nseg_x(int nx);  // segments of an x line
+int nseg_y(int ny);  // segments of a y line
+size_t acc_bytes();
+cudaError_t prepare();
+// x phases 1-3 (writes w over the right side in c.w) and y phases 1-2
+cudaError_t xsweep(tf_ctx& c, double dt);
+// y phase 3, the Newton update and the reductions
+cudaError_t ysweep(tf_ctx& c, const double* u_k, double dt, double* u_next, double* v_out);
+// the iteration's scalars into c.dsc (clears the accumulators)
+cudaError_t finalize(tf_ctx& c);
+int launches(const tf_ctx& c);  // kernels of one xsweep + ysweep
+}  // namespace part
+
 }  // namespace tf
 
 namespace tf {
@@ -74,6 +92,14 @@ struct tf_ctx {
   void* ulp;       // FP32 copy of the iterate u_k (FP32-bulk only), written by k_rhs
   void* fac_x;     // x-sweep LU factors, LP
   void* fac_y;     // y-sweep LU factors, LP
+  // partitioned line solves (FP32-bulk, (3, 2) power law; tf_partition.cuh)
+  bool part;       // this context uses them
+  int nsx, nsy;    // segments per x line and per y line
+  float* recx;     // x records [nsx-1][20][ny]
+  float* recy;     // y records [nsy-1][20][nx]
+  float* xsx;      // x separators' values [nsx-1][2][ny]
+  float* xsy;      // y separators' values [nsy-1][2][nx]
+  tf::part::Acc* acc;  // iteration accumulators (cleared by each finalize)
   double* ubuf;    // iterate buffer
   double* ubuf2;   // state buffer of tf_advance
   tf::PartX* px;

@@ -42,6 +42,7 @@ template <class Mode> struct Launch {
     if ((e = cudaFuncSetAttribute(k_rhs<Mode, kRhsExplicit>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if ((e = cudaFuncSetAttribute(k_rhs<Mode, kRhsBoth>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if constexpr (kF32B) {
+      if ((e = part::prepare())) return e;
       const int sp = (int)sizeof(RhsPackedSmem);
       const int maxc = (int)cudaSharedmemCarveoutMaxShared;
       if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsResidual>, A, sp))) return e;
@@ -111,6 +112,9 @@ template <class Mode> struct Launch {
     return sizeof(LP) == sizeof(double) ? (const LP*)u_k : (const LP*)c.ulp;
   }
   static cudaError_t xsweep_c(tf_ctx& c, double dt, const double* u_k) {
+    if constexpr (kF32B) {
+      if (c.part) return part::xsweep(c, dt);
+    }
     k_xsweep<Mode><<<c.grid_x, kSweepThreads, smem_x, c.stream>>>(c.mk, line_consts<LP>(c.mk, step(c, dt)),
                                                        film_lp(c, u_k), (LP*)c.w,
                                                        (LP*)c.fac_x, c.px + c.n_rhs_parts);
@@ -118,6 +122,9 @@ template <class Mode> struct Launch {
   }
   static cudaError_t ysweep_c(tf_ctx& c, const double* u_k, double dt, double* u_next,
                               double* v_out) {
+    if constexpr (kF32B) {
+      if (c.part) return part::ysweep(c, u_k, dt, u_next, v_out);
+    }
     k_ysweep<Mode><<<c.grid_y, kSweepThreads, smem_y, c.stream>>>(c.mk, line_consts<LP>(c.mk, step(c, dt)),
                                                        u_k, film_lp(c, u_k),
                                                        (const LP*)c.w,
