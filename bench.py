@@ -48,9 +48,10 @@ def peaks() -> dict:
     return dict(hbm_gbs=6800.0, source="fallback")
 
 
-# Measured on this machine's GB300 with a dependent-FMA throughput probe:
-# 500 G FP64 FMA/s (1.0 TFLOP/s) -- the FP64 pipe runs at 1/62 of FP32.
-FP64_TFLOPS = 1.0
+# The FP64 peak of the FP64-mode roofline is measured live by the library's
+# FMA throughput probe (tf_probe_fma: 8 independent FMA chains per thread,
+# 8 blocks of 256 threads per SM); no measured FP64 figure comes with the
+# HBM and bf16 peaks.
 
 # FP64 operations executed per cell by each FP64-mode kernel (DFMA counted
 # as 2, DADD and DMUL as 1), from an ncu capture of the FP64-mode kernels at
@@ -257,7 +258,7 @@ def kernel_table(res, N, lp):
 # from an ncu capture of the FP32-bulk kernels at 4096^2 (traffic scales
 # with the cells).  Valid for the kernels as captured; set an entry to None
 # when that kernel changes.
-TRAFFIC_PER_CELL_F32B = {"rhs": 22.31, "x_sweep": 31.42, "y_sweep": 44.57, "explicit": None}
+TRAFFIC_PER_CELL_F32B = {"rhs": None, "x_sweep": 31.42, "y_sweep": 44.57, "explicit": None}
 
 
 def ncu_counters_apply(w) -> bool:
@@ -387,14 +388,15 @@ def reference_arm(args, w):
     print(json.dumps(line))
 
 
-def ensemble_params(tf, w, f, mode):
+def ensemble_params(tf, w, f, mode, solver=0):
     """tf_params of one film of the ensemble workload."""
     import math
     return tf.tf_params_default(
         nx=f["N"], ny=f["N"], ds=f["ds"], b=w["b"], n=w["n"], m=w["m"], kappa=f["kappa"],
         contact_angle=math.radians(f["theta_c_deg"]), theta=w["theta"], newton_tol=w["tol"],
         newton_max_iter=w["max_iter"], dt_min=w["dt_min"], dt_max=f["dt_max"],
-        dt_shrink=w["dt_shrink"], dt_grow=w["dt_grow"], grow_after=w["grow_after"], precision=mode)
+        dt_shrink=w["dt_shrink"], dt_grow=w["dt_grow"], grow_after=w["grow_after"], precision=mode,
+        line_solver=solver)
 
 
 ENSEMBLE_METRIC = "film cell-updates/s over a 256-film ensemble"
@@ -402,8 +404,9 @@ ENSEMBLE_METRIC = "film cell-updates/s over a 256-film ensemble"
 
 def ensemble_config(w, A, world):
     sizes = sorted({f["N"] for f in w["films"]})
-    return dict(workload=(f"{len(w['films'])} spinodal films, N in {sizes}, contact angle "
-                          f"10-40 deg, each on {w['P']} of its lambda_m, {A} attempts each"),
+    return dict(workload=(f"{len(w['films'])} spinodal films, N drawn from {sizes}, contact angle "
+                          f"10-40 deg, {w['cells_per_lambda']} cells per lambda_m of each film, "
+                          f"{A} attempts each"),
                 mode="FP32-bulk", global_batch=len(w["films"]),
                 l2="working set larger than L2 (5 GB of films and workspace)",
                 parallelism=f"films sharded over {world} rank(s)")
@@ -463,34 +466,56 @@ def run_ensemble(args, w):
     mode = tf.TF_FP32_BULK
     films = w["films"][rank::world]
     A = args.steps if args.steps != 200 else w["attempts"]
-    ctxs, init, grids = [], [], []
-    for f in films:
-        ctxs.append(tf.Context(ensemble_params(tf, w, f, mode), stream=torch.cuda.Stream()))
-        init.append(torch.from_numpy(S.spinodal_film(f["N"], f["N"], w["h0"], w["eps"], f["seed"])).cuda())
-        grids.append(torch.empty_like(init[-1]))
+    init = [torch.from_numpy(S.spinodal_film(f["N"], f["N"], w["h0"], w["eps"], f["seed"])).cuda()
+            for f in films]
+    grids = [torch.empty_like(h) for h in init]
     dt0 = [f["dt0"] for f in films]
+    # the line-solver tuner: once per film size, on that size's first film
+    tuned = {}
+    for f, h in zip(films, init):
+        if f["N"] not in tuned:
+            r = tf.tf_tune_line_solver(ensemble_params(tf, w, f, mode, tf.TF_SOLVER_AUTO), h, f["dt0"], iters=5)
+            tuned[f["N"]] = dict(solver=("partitioned" if r["best"] == tf.TF_SOLVER_PARTITIONED else "twisted"),
+                                 ms_per_iteration=dict(twisted=round(r["ms"][0], 4),
+                                                       partitioned=round(r["ms"][1], 4)))
+
+    def contexts(solver):
+        return [tf.Context(ensemble_params(tf, w, f, mode, solver), stream=torch.cuda.Stream()) for f in films]
 
     def reset():
         for g, h in zip(grids, init):
             g.copy_(h)
         torch.cuda.synchronize()
 
-    # warm-up: W attempts per film
-    reset()
-    tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, dt0, args.warmup)
-    for c in ctxs:
-        tf.tf_timing_enable(c, True)
-    reset()
-    barrier(dist)
-    clocks = ClockSampler(local)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with clocks:
+    def timed(ctxs, clocks=None):
+        # warm-up: W attempts per film, then the timed run from the initial films
+        reset()
+        tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, dt0, args.warmup)
+        for c in ctxs:
+            tf.tf_timing_enable(c, True)
+        reset()
+        barrier(dist)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if clocks:
+            clocks.__enter__()
         e0.record()
         infos = tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, dt0, A)
         e1.record()
         torch.cuda.synchronize()
-    barrier(dist)
-    ms = e0.elapsed_time(e1)
+        if clocks:
+            clocks.__exit__()
+        barrier(dist)
+        return infos, e0.elapsed_time(e1)
+
+    # the fixed shape (every film on the twisted sweeps), then the tuned one
+    fixed_ctxs = contexts(tf.TF_SOLVER_TWISTED)
+    infos_fixed, ms_fixed = timed(fixed_ctxs)
+    cells_fixed = sum(f["N"] ** 2 * i["accepted"] for f, i in zip(films, infos_fixed))
+    for c in fixed_ctxs:
+        c.close()
+    ctxs = contexts(tf.TF_SOLVER_AUTO)
+    clocks = ClockSampler(local)
+    infos, ms = timed(ctxs, clocks)
     launches = sum(tf.tf_timing_get(c)["launches"] for c in ctxs)
     cells = sum(f["N"] ** 2 * i["accepted"] for f, i in zip(films, infos))
     iters = sum(i["newton_iterations"] for i in infos)
@@ -513,6 +538,8 @@ def run_ensemble(args, w):
         config=ensemble_config(w, A, world),
         accepted_steps=sum(i["accepted"] for i in infos), newton_iterations=iters,
         sequential_value=job_rate(dist, cells, ms_seq), speedup_vs_sequential=ms_seq / ms,
+        fixed_shape_value=job_rate(dist, cells_fixed, ms_fixed),
+        line_solver_by_size={str(k): v for k, v in sorted(tuned.items())},
         gpu_launches=launches,
         clocks=dict(sm_mhz=cs["sm_mhz"], sm_max_mhz=cs["sm_max_mhz"], reasons=cs["reasons"]),
     )
@@ -923,8 +950,12 @@ def main():
         line["e2e"] = dict(value=N * N * R["e2e_steps"] * world / (R["e2e_ms"] * 1e-3),
                            unit="cell-updates/s", h2d_bytes_per_step=R["e2e_bytes"],
                            d2h_bytes_per_step=R["e2e_bytes"], steps=R["e2e_steps"])
+    alu = dict(fp64_tflops=tf.tf_probe_fma(tf.TF_FP64), fp32_tflops=tf.tf_probe_fma(tf.TF_FP32_BULK),
+               source="measured live by tf_probe_fma (2 flops per FMA)")
+    line["alu_peaks"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in alu.items()}
     if "fp64" in res:
         F = res["fp64"]
+        FP64_TFLOPS = alu["fp64_tflops"]
         v64 = N * N * sum_over_ranks(dist, F["info"]["accepted"]) / (F["ms"] * 1e-3)
         t = F["timing"]
         per = (t["rhs_ms"] + t["x_ms"] + t["y_ms"]) / max(1, t["x_launches"])
@@ -942,8 +973,8 @@ def main():
                             accepted_steps=F["info"]["accepted"],
                             newton_iterations=F["info"]["newton_iterations"],
                             ms_per_iteration=per,
-                            roofline=None if not profiled else dict(bound="alu", unit="TFLOP/s", peak=FP64_TFLOPS,
-                                          peak_source="measured FP64 FMA throughput probe",
+                            roofline=None if not profiled else dict(bound="alu", unit="TFLOP/s", peak=round(FP64_TFLOPS, 4),
+                                          peak_source="measured live by tf_probe_fma",
                                           kernel=dom64, flops_per_cell=FP64_FLOPS_PER_CELL[dom64],
                                           ms_per_launch=round(ms64 / max(1, n64), 4),
                                           achieved=round(ach64, 4), frac=round(ach64 / FP64_TFLOPS, 4),

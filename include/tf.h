@@ -68,6 +68,20 @@ extern "C" {
                           the FP32 pipes; Jacobian assembly and pentadiagonal
                           solves in FP32; state stays IEEE double           */
 
+/* line solvers of the pentadiagonal systems (eq. LUFactorization); both
+   solve every line exactly, without pivoting                              */
+#define TF_SOLVER_TWISTED 0     /* two threads per line meet in the middle;
+                                   LU factors kept in device scratch        */
+#define TF_SOLVER_PARTITIONED 1 /* lines cut into segments of 64 (x) and 32
+                                   (y) cells solved independently, with a
+                                   2 x 2 block-tridiagonal reduced system on
+                                   two-cell separators per line (the
+                                   partition idea of Sec. Conclusions); only
+                                   TF_FP32_BULK with the (3, 2) power law   */
+#define TF_SOLVER_AUTO 2        /* the solver tf_tune_line_solver chose for
+                                   this grid shape and arithmetic, else
+                                   TF_SOLVER_TWISTED                        */
+
 typedef struct {
   int nx, ny;            /* cells in x and y, 1..65536 each, nx*ny < 2^31       */
   double ds;             /* grid spacing (both directions), > 0               */
@@ -100,6 +114,10 @@ typedef struct {
      Polymer_scales) is C = 0.00581, Cp = 1.181, A_SiOx = 41.25,
      A_Si = -243.75, d = 191.  Cp > 0, d >= 0.                            */
   double pol_C, pol_A_SiOx, pol_A_Si, pol_d;
+  int line_solver;       /* TF_SOLVER_TWISTED (default), TF_SOLVER_PARTITIONED or
+                            TF_SOLVER_AUTO; the solvers give the same
+                            solutions to FP32 rounding, at speeds that
+                            depend on the grid                              */
 } tf_params;
 
 typedef struct tf_ctx tf_ctx;
@@ -141,8 +159,8 @@ typedef struct {
 /* Fill *p with the defaults: power-law model, C = 1, b = 0.1, n = 3, m = 2,
  * contact angle 20 degrees (kappa derived), theta = 0.5, tol 1e-10, K = 10,
  * dt_min 1e-9, dt_max 1e30, shrink 0.5, grow 1.25 after 5, no rupture stop,
- * TF_FP64; the NLC and polymer parameters hold the paper's sets (C and b
- * must still be set for those models).  nx, ny, ds are set to 0 and must
+ * TF_FP64, TF_SOLVER_TWISTED; the NLC and polymer parameters hold the
+ * paper's sets (C and b must still be set for those models).  nx, ny, ds are set to 0 and must
  * be filled in.                                                          */
 void tf_params_default(tf_params* p);
 
@@ -228,6 +246,39 @@ int tf_advance(tf_ctx* ctx, double* h, double t0, double t_end, double dt0,
 int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const double* t0,
                         const double* t_end, const double* dt0, const int* max_attempts,
                         tf_advance_info* info, int* streak);
+
+/* ---- line-solver tuning ---------------------------------------------------
+ * The paper has no counterpart to this: it picks, per grid shape, the
+ * faster of the line solvers for the many-film runs of Sec. Results, whose
+ * films range from 128^2 (too few lines to fill the GPU with two threads
+ * per line) to 1024^2.  tf_tune_line_solver times `iters` (>= 1) Newton
+ * iterations from the device film h (of p's shape; not modified) at step
+ * dt with each solver that applies to *p (after one untimed iteration
+ * each), on the given stream, and keeps the faster in a table of this
+ * process keyed by (nx, ny, precision, model, n, m).  *best receives the
+ * chosen solver; ms (host, 2 entries, or NULL) the milliseconds per
+ * iteration of TF_SOLVER_TWISTED and TF_SOLVER_PARTITIONED (-1 where a
+ * solver does not apply).  A later call for the same key replaces the
+ * entry.  Contexts created with line_solver = TF_SOLVER_AUTO read the
+ * table once, in tf_init, so a context never changes solver.  Allocates
+ * two temporary contexts; synchronises the stream.  Returns TF_OK,
+ * TF_ERR_ARG or a context's error.                                        */
+int tf_tune_line_solver(const tf_params* p, void* stream, const double* h, double dt, int iters,
+                        int* best, double* ms);
+/* The table's entry for *p's key (TF_SOLVER_*), or -1 if there is none.   */
+int tf_tuned_line_solver(const tf_params* p);
+/* The solver a context uses (TF_SOLVER_TWISTED or TF_SOLVER_PARTITIONED),
+ * or -1 for NULL.                                                         */
+int tf_line_solver(const tf_ctx* ctx);
+
+/* FMA throughput of the current GPU, for the roofline of arithmetic-bound
+ * kernels (the paper has no counterpart): precision TF_FP64 times FP64
+ * fused multiply-adds, TF_FP32_BULK FP32 ones; 8 independent chains per
+ * thread, 8 blocks of 256 threads per SM, on the given stream.  *tflops
+ * receives 2 x FMAs / s / 1e12.  Allocates a small output buffer;
+ * synchronises the stream.  Returns TF_OK, TF_ERR_ARG, TF_ERR_NOMEM or
+ * TF_ERR_CUDA.                                                            */
+int tf_probe_fma(int precision, void* stream, double* tflops);
 
 /* Kernel timing of a context, for measurement.  While enabled, the library
  * records CUDA events on its stream around every kernel it launches and

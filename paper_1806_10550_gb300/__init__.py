@@ -43,6 +43,9 @@ TF_MODEL_NLC = 2
 TF_MODEL_POLYMER = 3
 TF_FP64 = 0
 TF_FP32_BULK = 1
+TF_SOLVER_TWISTED = 0
+TF_SOLVER_PARTITIONED = 1
+TF_SOLVER_AUTO = 2
 
 
 class TfParams(C.Structure):
@@ -58,7 +61,7 @@ class TfParams(C.Structure):
         ("nlc_K", C.c_double), ("nlc_N", C.c_double), ("nlc_beta", C.c_double),
         ("nlc_w", C.c_double),
         ("pol_C", C.c_double), ("pol_A_SiOx", C.c_double), ("pol_A_Si", C.c_double),
-        ("pol_d", C.c_double),
+        ("pol_d", C.c_double), ("line_solver", C.c_int),
     ]
 
 
@@ -137,6 +140,13 @@ def library(build_if_missing: bool = True):
     L.tf_ensemble_advance.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(dp),
                                       C.POINTER(dp), C.POINTER(dp), C.POINTER(C.c_int),
                                       C.POINTER(TfAdvanceInfo), C.POINTER(C.c_int)]
+    L.tf_tune_line_solver.argtypes = [C.POINTER(TfParams), vp, vp, dp, C.c_int, C.POINTER(C.c_int),
+                                      C.POINTER(dp)]
+    L.tf_tuned_line_solver.argtypes = [C.POINTER(TfParams)]
+    L.tf_tuned_line_solver.restype = C.c_int
+    L.tf_line_solver.argtypes = [vp]
+    L.tf_line_solver.restype = C.c_int
+    L.tf_probe_fma.argtypes = [C.c_int, vp, C.POINTER(dp)]
     L.tf_timing_enable.argtypes = [vp, C.c_int]
     L.tf_timing_get.argtypes = [vp, C.POINTER(TfTiming)]
     L.tf_adjoint_step.argtypes = [vp, vp, dp, C.c_int, vp, vp, vp, C.POINTER(dp), C.POINTER(dp)]
@@ -163,7 +173,7 @@ def library(build_if_missing: bool = True):
               "tf_adjoint_timing", "tf_tape_create", "tf_tape_info", "tf_tape_forward",
               "tf_tape_backward", "tf_tape_timing",
               "tf_spectrum_plan_create",
-              "tf_spectrum_plan_info", "tf_spectrum_run", "tf_spectrum_timing"):
+              "tf_spectrum_plan_info", "tf_spectrum_run", "tf_spectrum_timing", "tf_tune_line_solver", "tf_probe_fma"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -214,6 +224,11 @@ class Context:
     @property
     def kappa(self) -> float:
         return library().tf_kappa(self.handle)
+
+    @property
+    def line_solver(self) -> int:
+        """The line solver this context uses (TF_SOLVER_TWISTED or _PARTITIONED)."""
+        return library().tf_line_solver(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -308,6 +323,41 @@ def tf_advance(ctx: Context, h, t0: float, t_end: float, dt0: float, max_attempt
     return dict(status=info.status, attempts=info.attempts, accepted=info.accepted,
                 newton_iterations=info.newton_iterations, t=info.t, dt=info.dt,
                 streak=st.value), out
+
+
+def tf_tune_line_solver(params: TfParams, h, dt: float, iters: int = 3, stream=None) -> dict:
+    """Time the line solvers that apply to ``params`` on the CUDA film ``h``
+    and keep the faster for contexts created with ``TF_SOLVER_AUTO``;
+    returns dict(best=solver, ms=[twisted, partitioned]) (ms per Newton
+    iteration, -1 where a solver does not apply)."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if tuple(h.shape) != (params.ny, params.nx) or h.dtype != torch.float64 or not h.is_cuda:
+        raise ValueError("h must be a CUDA float64 tensor of the params' shape")
+    best = C.c_int()
+    ms = (C.c_double * 2)()
+    _check(library().tf_tune_line_solver(C.byref(params), C.c_void_p(stream.cuda_stream),
+                                         C.c_void_p(h.contiguous().data_ptr()), float(dt), int(iters),
+                                         C.byref(best), ms), "tf_tune_line_solver")
+    return dict(best=best.value, ms=[ms[0], ms[1]])
+
+
+def tf_probe_fma(precision: int, stream=None) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (2 flops per
+    FMA), FP64 (TF_FP64) or FP32 (TF_FP32_BULK)."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = C.c_double()
+    _check(library().tf_probe_fma(int(precision), C.c_void_p(stream.cuda_stream), C.byref(out)),
+           "tf_probe_fma")
+    return out.value
+
+
+def tf_tuned_line_solver(params: TfParams) -> int:
+    """The tuned solver for ``params``' key, or -1."""
+    return library().tf_tuned_line_solver(C.byref(params))
 
 
 def tf_ensemble_advance(ctxs, hs, t0, t_end, dt0, max_attempts, streak=0):

@@ -1,7 +1,8 @@
 """Build of the CUDA library ``libtfadi.so`` (sm_103a) in the package tree.
 
-Six translation units (the C-ABI host layer, one per precision mode, the
-allocation-free residual, the radial Fourier analysis and the adjoint)
+The translation units (the C-ABI host layer, one per precision mode, the
+partitioned line solver, the allocation-free residual, the radial Fourier
+analysis, the adjoint and the throughput probe)
 compile in parallel with ``nvcc -gencode arch=compute_103a,code=sm_103a``
 and link into ``paper_1806_10550_gb300/_build/libtfadi.so``.  The build is
 skipped when the library is newer than every source.
@@ -19,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtfadi.so")
-UNITS = ["tf_api", "tf_mode_fp64", "tf_mode_f32b", "tf_part", "tf_noalloc", "tf_spectrum", "tf_adjoint"]
+UNITS = ["tf_api", "tf_mode_fp64", "tf_mode_f32b", "tf_part", "tf_noalloc", "tf_spectrum", "tf_adjoint", "tf_probe"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

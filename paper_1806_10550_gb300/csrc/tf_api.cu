@@ -10,7 +10,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "tf_internal.h"
@@ -316,6 +318,20 @@ int film_on_stats(FilmRun& F) {
   return film_start_attempt(F);
 }
 
+// ---------------------------------------------------------------------------
+// Line-solver tuning table of the process: (nx, ny, precision, model, n, m)
+// -> solver.
+
+struct TuneKey {
+  int nx, ny, precision, model, n, m;
+  bool operator==(const TuneKey& o) const {
+    return nx == o.nx && ny == o.ny && precision == o.precision && model == o.model && n == o.n && m == o.m;
+  }
+};
+std::mutex g_tune_mutex;
+std::vector<std::pair<TuneKey, int>> g_tune;
+TuneKey tune_key(const tf_params& p) { return TuneKey{p.nx, p.ny, p.precision, p.model, p.n, p.m}; }
+
 template <class T> int dalloc(T** p, size_t bytes) {
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
@@ -384,6 +400,7 @@ void tf_params_default(tf_params* p) {
   p->pol_A_SiOx = 41.25;
   p->pol_A_Si = -243.75;
   p->pol_d = 191.0;
+  p->line_solver = TF_SOLVER_TWISTED;
 }
 
 const char* tf_strerror(int code) {
@@ -444,6 +461,10 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   if (!(p->dt_shrink > 0.0 && p->dt_shrink < 1.0) || !(p->dt_grow >= 1.0) || p->grow_after < 1)
     return TF_ERR_ARG;
   if (p->precision != TF_FP64 && p->precision != TF_FP32_BULK) return TF_ERR_ARG;
+  if (p->line_solver < TF_SOLVER_TWISTED || p->line_solver > TF_SOLVER_AUTO) return TF_ERR_ARG;
+  if (p->line_solver == TF_SOLVER_PARTITIONED &&
+      !(p->precision == TF_FP32_BULK && p->model == TF_MODEL_POWERLAW && p->n == 3 && p->m == 2))
+    return TF_ERR_ARG;
   double kappa = p->kappa;
   if (p->model == TF_MODEL_POWERLAW) {
     if (!(p->b > 0.0) || p->m < 1 || p->n <= p->m || p->n > 12 || !(p->cap_C > 0.0)) return TF_ERR_ARG;
@@ -510,7 +531,14 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   if (!r) r = dalloc(&c->bn, c->N * hp);
   if (!r) r = dalloc(&c->w, c->N * lp);
   if (!r && lp != sizeof(double)) r = dalloc(&c->ulp, c->N * lp);
-  c->part = c->packed_rhs;
+  {
+    int solver = p->line_solver;
+    if (solver == TF_SOLVER_AUTO) {
+      solver = tf_tuned_line_solver(p);
+      if (solver < 0) solver = TF_SOLVER_TWISTED;
+    }
+    c->part = c->packed_rhs && solver == TF_SOLVER_PARTITIONED;
+  }
   c->nsx = tf::part::nseg_x(p->nx);
   c->nsy = tf::part::nseg_y(p->ny);
   if (c->part) {
@@ -743,6 +771,72 @@ int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const doubl
   for (int e : err)
     if (e) return e;
   for (FilmRun& f : F) TF_CK(cudaStreamSynchronize(f.c->stream));
+  return TF_OK;
+}
+
+int tf_line_solver(const tf_ctx* c) {
+  if (!c) return -1;
+  return c->part ? TF_SOLVER_PARTITIONED : TF_SOLVER_TWISTED;
+}
+
+int tf_tuned_line_solver(const tf_params* p) {
+  if (!p) return -1;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  const TuneKey k = tune_key(*p);
+  for (const auto& e : g_tune)
+    if (e.first == k) return e.second;
+  return -1;
+}
+
+int tf_tune_line_solver(const tf_params* p, void* stream, const double* h, double dt, int iters, int* best,
+                        double* ms) {
+  if (!p || !h || !best || iters < 1 || !(dt > 0.0) || !isfinite(dt)) return TF_ERR_ARG;
+  double t[2] = {-1.0, -1.0};
+  for (int s = TF_SOLVER_TWISTED; s <= TF_SOLVER_PARTITIONED; ++s) {
+    tf_params q = *p;
+    q.line_solver = s;
+    tf_ctx* c = nullptr;
+    const int r = tf_init(&q, stream, &c);
+    if (r == TF_ERR_ARG && s == TF_SOLVER_PARTITIONED) continue;  // not applicable
+    if (r) return r;
+    // one untimed iteration, then `iters` timed ones, each from h (the same
+    // work every time), with the host round trip of a real iteration
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = TF_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = TF_ERR_CUDA;
+    if (!rc && c->ops->explicit_part(*c, h, dt) != cudaSuccess) rc = TF_ERR_CUDA;
+    Scalars sc;
+    for (int k = 0; k <= iters && !rc; ++k) {
+      if (k == 1 && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = TF_ERR_CUDA;
+      if (!rc) rc = iterate(*c, h, dt, c->ubuf2, nullptr, nullptr, &sc);
+    }
+    if (!rc && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+      rc = TF_ERR_CUDA;
+    float el = 0.0f;
+    if (!rc && cudaEventElapsedTime(&el, e0, e1) != cudaSuccess) rc = TF_ERR_CUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    tf_destroy(c);
+    if (rc) return rc;
+    t[s] = (double)el / iters;
+  }
+  const int choice = (t[1] >= 0.0 && t[1] < t[0]) ? TF_SOLVER_PARTITIONED : TF_SOLVER_TWISTED;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    const TuneKey k = tune_key(*p);
+    bool found = false;
+    for (auto& e : g_tune)
+      if (e.first == k) {
+        e.second = choice;
+        found = true;
+      }
+    if (!found) g_tune.emplace_back(k, choice);
+  }
+  *best = choice;
+  if (ms) {
+    ms[0] = t[0];
+    ms[1] = t[1];
+  }
   return TF_OK;
 }
 

@@ -28,20 +28,35 @@
 // Every segment of every line is an independent block of work, so all SMs
 // stay busy and no LU factors travel through HBM.
 //
-// Kernels (FP32 film and solves, the (3, 2) power law or any model through
-// band_rows):
-//   k_part_x1  x phase 1 on a tile of 32 rows x one x segment (reads the
-//              FP32 film and the right side r = -G written by the residual);
-//   k_part_red phase 2 of one direction, one thread per line;
-//   k_part_xy  x phase 3 on a tile of one y segment x one x segment (writes
-//              w), then y phase 1 on the same tile's columns;
-//   k_part_yc  y phase 3 on a tile of one y segment x 64 columns, the Newton
-//              update u_{k+1} = u_k + v and the iteration's reductions.
+// Every per-line operation here runs on two lines at once, one in each lane
+// of the paired FP32 instructions (float2 add/mul/fma): band rows, the
+// elimination passes and the interior solves.  Only the 4 x 4 seam solves,
+// which pivot, run one line at a time.
+//
+// This header holds the device building blocks (the (3, 2) power law); the
+// kernels are in tf_part.cu:
+//   x phase 1 on a tile of 32 rows x one x segment, from the FP32 film and
+//              the right side r = -G written by the residual kernel;
+//   phase 2 of one direction, one warp per line;
+//   x phase 3 on a tile of one y segment x one x segment (writes w), then
+//              y phase 1 on the same tile's columns;
+//   y phase 3 on a tile of one y segment x 64 columns, the Newton update
+//              u_{k+1} = u_k + v and the iteration's reductions.
 #pragma once
 
 #include "tf_line_sweeps.cuh"
 
 namespace tf {
+
+// paired FP32 operations (one IEEE operation per lane)
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, p_neg(b)); }
+__device__ __forceinline__ float2 p_splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 p_rcp(float2 a) { return make_float2(rcp(a.x), rcp(a.y)); }
+
 namespace part {
 
 constexpr int kT = 256;    // threads per block
@@ -70,7 +85,7 @@ template <int L> __host__ __device__ __forceinline__ int seg_end(int k, int n) {
   return k + 1 < seg_count<L>(n) ? seg_start<L>(k + 1, n) : n;
 }
 
-// 2 x 2 matrices, row-major [[a, b], [c, d]]
+// 2 x 2 matrices, row-major [[a, b], [c, d]] (one line; phase 2 and records)
 struct M2 {
   float a, b, c, d;
 };
@@ -93,91 +108,172 @@ __device__ __forceinline__ void mv2(const M2& x, float u, float v, float& p, flo
   q = x.c * u + x.d * v;
 }
 
-// Band rows in shared memory: band[(cell * 5 + q) * NL + line], q = a..e
-// (multiplying x_{i-2}..x_{i+2}).  A row in the orientation of a pass:
-// natural, or reversed (the line read backwards: e..a).
-struct Row {
-  float a, b, c, d, e;
+// ---------------------------------------------------------------------------
+// Band rows of two lines.  Layout in shared memory: band[(cell * 5 + q) *
+// NL + line], q = a..e (multiplying x_{i-2}..x_{i+2}); lines 2p and 2p + 1
+// are one float2.
+
+struct Row2 {
+  float2 a, b, c, d, e;
 };
 template <int NL>
-__device__ __forceinline__ Row band_row(const float* band, int cell, int line, bool rev) {
-  const float* p = band + cell * 5 * NL + line;
-  Row r;
+__device__ __forceinline__ Row2 band_row2(const float* band, int cell, int pair, bool rev) {
+  const float2* p = reinterpret_cast<const float2*>(band + cell * 5 * NL) + pair;
+  constexpr int Q = NL / 2;
+  Row2 r;
   if (!rev) {
     r.a = p[0];
-    r.b = p[NL];
-    r.c = p[2 * NL];
-    r.d = p[3 * NL];
-    r.e = p[4 * NL];
+    r.b = p[Q];
+    r.c = p[2 * Q];
+    r.d = p[3 * Q];
+    r.e = p[4 * Q];
   } else {
     r.e = p[0];
-    r.d = p[NL];
-    r.c = p[2 * NL];
-    r.b = p[3 * NL];
-    r.a = p[4 * NL];
+    r.d = p[Q];
+    r.c = p[2 * Q];
+    r.b = p[3 * Q];
+    r.a = p[4 * Q];
   }
   return r;
 }
 
-// Build the band rows of cells [ia0, ia0 + ncell) of nl lines into band
-// (cell index relative to ia0).  film(line, cell, dr, dc) gives the FP32
-// film at line `line`, line cell `cell` (global index along the line),
-// offset by dr cells across and dc along the line.  n: line length.
-template <int NL, class Film>
-__device__ __forceinline__ void build_band(const LineK<float>& L, float* band, int nl, int ia0, int ncell,
-                                           int n, Film film) {
-  const int ngrp = (ncell + kGB - 1) / kGB;
-  for (int task = threadIdx.x; task < ngrp * NL; task += kT) {
-    const int line = task % NL, grp = task / NL;
-    if (line >= nl) continue;
-    const int ia = ia0 + grp * kGB, ib = min(ia0 + ncell, ia + kGB);
-    auto A = [&](int s, int dr, int dc) { return film(line, ia + s, dr, dc); };
-    float* P = band + (ia - ia0) * 5 * NL + line;
-    auto out = [&](int s, float a, float b, float c, float d, float e) {
-      float* q = P + s * 5 * NL;
-      q[0] = a;
-      q[NL] = b;
-      q[2 * NL] = c;
-      q[3 * NL] = d;
-      q[4 * NL] = e;
-    };
-    const bool edge = !(ia >= 2 && ia + kGB + 1 < n);
-    if (!L.ml.pl32)
-      band_rows<float, kGB, true, false>(L, A, ia, ib, n, out);
-    else if (!edge)
-      band_rows<float, kGB, false, true>(L, A, ia, ib, n, out);
-    else
-      band_rows<float, kGB, true, true>(L, A, ia, ib, n, out);
+// Per-cell film values of the (n, m) = (3, 2) power law, pre-scaled for the
+// band (the constants of LineK, as cell_pl32): F0 = k3 C h^3, F1 = k1 A1 -
+// k1 B1 / h, D0 = (k1/ds^2) 3 C h^2, D1 = k1 B1 / h^2, and the unscaled
+// Laplacian.
+struct LineK2 {
+  float2 pF0, pF1a, pF1b, pD0, pD1;
+};
+__device__ __forceinline__ LineK2 pack_consts(const LineK<float>& L) {
+  LineK2 K;
+  K.pF0 = p_splat(L.pF0);
+  K.pF1a = p_splat(L.pF1a);
+  K.pF1b = p_splat(L.pF1b);
+  K.pD0 = p_splat(L.pD0);
+  K.pD1 = p_splat(L.pD1);
+  return K;
+}
+struct Cell2 {
+  float2 u, lap, F0, F1, D0, D1;
+};
+template <class Acc>
+__device__ __forceinline__ Cell2 cell2(const LineK2& K, Acc U) {
+  Cell2 X;
+  const float2 uc = U(0, 0);
+  X.u = uc;
+  X.lap = p_add(p_add(p_sub(U(0, 1), uc), p_sub(U(0, -1), uc)), p_add(p_sub(U(1, 0), uc), p_sub(U(-1, 0), uc)));
+  const float2 s = p_rcp(uc), h2 = p_mul(uc, uc);
+  X.F0 = p_mul(K.pF0, p_mul(h2, uc));
+  X.F1 = p_fma(p_neg(K.pF1b), s, K.pF1a);
+  X.D0 = p_mul(K.pD0, h2);
+  X.D1 = p_mul(K.pD1, p_mul(s, s));
+  return X;
+}
+// derivatives of the scaled flux through the face between line cells p and
+// q = p + 1 (see face_scaled): pl, qr say whether p has a left and q a right
+// neighbour (walls fold the reflected cells away)
+__device__ __forceinline__ void face2(const Cell2& P, const Cell2& Q, bool pl, bool qr, float2 dF[4]) {
+  const float2 dl = p_sub(Q.lap, P.lap), du = p_sub(Q.u, P.u);
+  const float2 c3 = p_add(P.F0, Q.F0), Bd = p_add(P.F1, Q.F1);
+  const float2 tp = p_fma(P.D0, dl, p_mul(P.D1, du)), tq = p_fma(Q.D0, dl, p_mul(Q.D1, du));
+  const float wp = pl ? 1.f : 0.f, wq = qr ? 1.f : 0.f;
+  dF[0] = p_mul(p_splat(-wp), c3);
+  dF[1] = p_fma(p_splat(2.f + wp), c3, p_sub(tp, Bd));
+  dF[2] = p_fma(p_splat(-(2.f + wq)), c3, p_add(tq, Bd));
+  dF[3] = p_mul(p_splat(wq), c3);
+}
+// Band rows of line cells ia .. ib-1 (at most G) of two lines, from the
+// film around them: A(s, dr, dc) gives the film pair at line cell ia + s
+// offset by (dr, dc).  Faces outside 0..n-1 carry nothing.  OUT(s, row).
+// Rolling: two cells and two faces live at a time.
+template <int G, class Acc, class Out>
+__device__ __forceinline__ void band_rows2(const LineK2& K, Acc A, int ia, int ib, int n, Out out) {
+  auto face_at = [&](const Cell2& P, const Cell2& Q, int f, float2 F[4]) {  // cells ia+f-1 | ia+f
+    const int q = ia + f - 1;
+    face2(P, Q, q > 0, q + 2 < n, F);
+    if (!(q >= 0 && q + 1 < n))
+      for (int k = 0; k < 4; ++k) F[k] = p_splat(0.f);
+  };
+  Cell2 Cp = cell2(K, [&](int dr, int dc) { return A(-1, dr, dc); });
+  Cell2 Cq = cell2(K, [&](int dr, int dc) { return A(0, dr, dc); });
+  float2 Fa[4], Fb[4];
+  face_at(Cp, Cq, 0, Fa);
+#pragma unroll
+  for (int s = 0; s < G; ++s) {
+    Cp = Cq;
+    Cq = cell2(K, [&](int dr, int dc) { return A(s + 1, dr, dc); });
+    face_at(Cp, Cq, s + 1, Fb);
+    if (ia + s < ib) {
+      Row2 R;
+      R.a = p_neg(Fa[0]);
+      R.b = p_sub(Fb[0], Fa[1]);
+      R.c = p_add(p_splat(1.f), p_sub(Fb[1], Fa[2]));
+      R.d = p_sub(Fb[2], Fa[3]);
+      R.e = Fb[3];
+      out(s, R);
+    }
+    for (int k = 0; k < 4; ++k) Fa[k] = Fb[k];
   }
 }
 
-// Phase 1: one elimination pass over an interior of m >= 2 rows, LU without
-// pivoting of the interior's own matrix (entries that reach outside it
-// dropped), with the right sides f and the unit vectors e_0, e_1.  X
-// receives rows m-2 and m-1 (in the pass's orientation) of A^-1 applied to
-// [f, e_0, e_1, e_{m-2}, e_{m-1}].  ROW(i) gives row i in the pass's
-// orientation; RHS(i) its right side.  A zero or non-finite pivot sets bad.
+// Build the band rows of cells [ia0, ia0 + ncell) of the nl lines of a tile
+// (NL lines at most, in pairs) with NT threads.  film(pair, cell, dr, dc)
+// gives the film of lines 2 pair, 2 pair + 1 at line cell `cell` (global
+// index along the line), offset by dr across and dc along the line.
+template <int NL, int NT, class Film>
+__device__ __forceinline__ void build_band(const LineK2& K, float* band, int nl, int ia0, int ncell, int n,
+                                           Film film) {
+  constexpr int NP = NL / 2;
+  const int ngrp = (ncell + kGB - 1) / kGB, npair = (nl + 1) / 2;
+  for (int task = threadIdx.x; task < ngrp * NP; task += NT) {
+    const int pair = task % NP, grp = task / NP;
+    if (pair >= npair) continue;
+    const int ia = ia0 + grp * kGB, ib = min(ia0 + ncell, ia + kGB);
+    auto A = [&](int s, int dr, int dc) { return film(pair, ia + s, dr, dc); };
+    float2* P = reinterpret_cast<float2*>(band + (ia - ia0) * 5 * NL) + pair;
+    auto out = [&](int s, const Row2& R) {
+      float2* q = P + s * 5 * NP;
+      q[0] = R.a;
+      q[NP] = R.b;
+      q[2 * NP] = R.c;
+      q[3 * NP] = R.d;
+      q[4 * NP] = R.e;
+    };
+    band_rows2<kGB>(K, A, ia, ib, n, out);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase 1: one elimination pass over an interior of m >= 2 rows of two
+// lines, LU without pivoting of the interior's own matrix (entries that
+// reach outside it dropped), with the right sides f and the unit vectors
+// e_0, e_1.  X receives rows m-2 and m-1 (in the pass's orientation) of
+// A^-1 applied to [f, e_0, e_1, e_{m-2}, e_{m-1}].  ROW(i) gives row i in
+// the pass's orientation; RHS(i) its right side.  A zero or non-finite
+// pivot sets bad.
 template <class RowF, class RhsF>
-__device__ __forceinline__ void elim_pass(RowF ROW, RhsF RHS, int m, float X[2][5], int& bad) {
-  float g1 = 0.f, d1 = 0.f, g2 = 0.f, d2 = 0.f;
-  float zf1 = 0.f, zf2 = 0.f, za1 = 0.f, za2 = 0.f, zb1 = 0.f, zb2 = 0.f;
-  float gm2 = 0.f, im2 = 0.f, bm1 = 0.f, im1 = 0.f, chk = 0.f;
-#pragma unroll 4
+__device__ __forceinline__ void elim_pass2(RowF ROW, RhsF RHS, int m, float2 X[2][5], int& bad, bool two) {
+  const float2 z0 = p_splat(0.f), one = p_splat(1.f);
+  float2 g1 = z0, d1 = z0, g2 = z0, d2 = z0;
+  float2 zf1 = z0, zf2 = z0, za1 = z0, za2 = z0, zb1 = z0, zb2 = z0;
+  float2 gm2 = z0, im2 = z0, bm1 = z0, im1 = z0, chk = z0;
   for (int i = 0; i < m; ++i) {
-    Row R = ROW(i);
-    const float f = RHS(i);
-    if (i == 0) R.b = 0.f;
-    if (i <= 1) R.a = 0.f;
-    if (i + 1 >= m) R.d = 0.f;
-    if (i + 2 >= m) R.e = 0.f;
-    const float beta = R.b - R.a * g2;
-    const float mu = R.c - R.a * d2 - beta * g1;
-    const float inv = rcp(mu);
-    chk = fmaf(mu, inv, chk);
-    const float g = (R.d - beta * d1) * inv, dl = R.e * inv;
-    const float zf = (f - R.a * zf2 - beta * zf1) * inv;
-    const float za = ((i == 0 ? 1.f : 0.f) - R.a * za2 - beta * za1) * inv;
-    const float zb = ((i == 1 ? 1.f : 0.f) - R.a * zb2 - beta * zb1) * inv;
+    Row2 R = ROW(i);
+    const float2 f = RHS(i);
+    // rows 0 and 1 lose the entries reaching left of the interior, rows
+    // m-2 and m-1 those reaching right of it
+    if (i == 0) R.b = z0;
+    if (i <= 1) R.a = z0;
+    if (i + 1 >= m) R.d = z0;
+    if (i + 2 >= m) R.e = z0;
+    const float2 beta = p_fma(p_neg(R.a), g2, R.b);
+    const float2 mu = p_fma(p_neg(beta), g1, p_fma(p_neg(R.a), d2, R.c));
+    const float2 inv = p_rcp(mu);
+    chk = p_fma(mu, inv, chk);
+    const float2 g = p_mul(p_fma(p_neg(beta), d1, R.d), inv), dl = p_mul(R.e, inv);
+    const float2 zf = p_mul(p_fma(p_neg(beta), zf1, p_fma(p_neg(R.a), zf2, f)), inv);
+    const float2 za = p_mul(p_fma(p_neg(beta), za1, p_fma(p_neg(R.a), za2, i == 0 ? one : z0)), inv);
+    const float2 zb = p_mul(p_fma(p_neg(beta), zb1, p_fma(p_neg(R.a), zb2, i == 1 ? one : z0)), inv);
     if (i == m - 2) {
       gm2 = g;
       im2 = inv;
@@ -200,28 +296,30 @@ __device__ __forceinline__ void elim_pass(RowF ROW, RhsF RHS, int m, float X[2][
   X[1][0] = zf1;
   X[1][1] = za1;
   X[1][2] = zb1;
-  X[0][0] = zf2 - gm2 * zf1;
-  X[0][1] = za2 - gm2 * za1;
-  X[0][2] = zb2 - gm2 * zb1;
+  X[0][0] = p_fma(p_neg(gm2), zf1, zf2);
+  X[0][1] = p_fma(p_neg(gm2), za1, za2);
+  X[0][2] = p_fma(p_neg(gm2), zb1, zb2);
   // e_{m-2}: z_{m-2} = 1/mu_{m-2}, z_{m-1} = -beta_{m-1} z_{m-2}/mu_{m-1};
   // e_{m-1}: z_{m-1} = 1/mu_{m-1}
-  X[1][3] = -bm1 * im2 * im1;
-  X[0][3] = im2 - gm2 * X[1][3];
+  X[1][3] = p_mul(p_neg(bm1), p_mul(im2, im1));
+  X[0][3] = p_fma(p_neg(gm2), X[1][3], im2);
   X[1][4] = im1;
-  X[0][4] = -gm2 * im1;
-  if (!(chk == chk)) bad = 1;
+  X[0][4] = p_mul(p_neg(gm2), im1);
+  if (!(chk.x == chk.x) || (two && !(chk.y == chk.y))) bad = 1;  // two: the second line exists
 }
 
 // The record of one line of segment k (see the file comment): for the
 // separator k (own: values 0..9, written by segment k) and separator k + 1
-// (next: values 10..19 of separator k + 1, written by segment k).
+// (next: values 10..19 of separator k + 1, written by segment k).  Records
+// are stored rec[separator - 1][20][line]: a warp over 32 consecutive lines
+// reads each value of a row with one coalesced access.
 //   own:  Dp = A_ss - T M_FF P (4), U = -T M_FL Q (4), rp = f_s - T y_F (2)
 //   next: Lw = -R M_LF P (4), Dm = -R M_LL Q (4), rm = -R y_L (2)
 // with P, Q the interior's couplings to its left and right separators, T
 // and R the separators' couplings into the interior, A_ss the separator's
-// own 2 x 2 block.  XF, XL: the two passes' results (XF of the reversed
-// pass).  Cells are local (0 = the segment's first cell); p1 = segment
-// length; the band holds cells 0 .. p1 + 1.
+// own 2 x 2 block.  XF, XL: the two passes' results for this line (XF of
+// the reversed pass).  Cells are local (0 = the segment's first cell); p1 =
+// segment length; the band holds cells 0 .. p1 + 1.
 template <int NL, class RhsF>
 __device__ __forceinline__ void write_record(const float* band, int line, int k, int S, int p1, const float XL[2][5],
                                              const float XF[2][5], RhsF RHS, float* rec, size_t nlines,
@@ -245,7 +343,7 @@ __device__ __forceinline__ void write_record(const float* band, int line, int k,
     const M2 U = mul2(mul2(T, MFL), Q);  // negated below
     float t0, t1;
     mv2(T, yF0, yF1, t0, t1);
-    float* o = rec + ((size_t)(k - 1) * kRec) * nlines + gline;
+    float* o = rec + (size_t)(k - 1) * kRec * nlines + gline;
     const float v[10] = {Dp.a, Dp.b, Dp.c, Dp.d, -U.a, -U.b, -U.c, -U.d, RHS(0) - t0, RHS(1) - t1};
 #pragma unroll
     for (int q = 0; q < 10; ++q) o[q * nlines] = v[q];
@@ -263,116 +361,190 @@ __device__ __forceinline__ void write_record(const float* band, int line, int k,
   }
 }
 
-// Phase 3 for the lines of a tile: the interior [p0, p1) of every line
+// Phase 1 of a tile after its band: warp 0 (one thread per pair of lines)
+// runs the forward pass, warp 1 the reversed one, over the interior of every
+// line of segment k (len cells); then one thread per line writes the
+// records.  RHS(line, cell) is the right side of the line's local cell.
+// X: scratch [2][NL][10].  All threads of the block call it (it
+// synchronises).
+template <int NL, class RhsF>
+__device__ __forceinline__ void phase1(const float* band, float (*X)[NL][10], int nl, int k, int S, int len,
+                                       RhsF RHS, float* rec, size_t nlines, size_t gline0, int& bad) {
+  constexpr int NP = NL / 2;
+  static_assert(NP <= 32, "one warp per pass direction");
+  // the two directions run in different warps (no divergence between them)
+  const int t = threadIdx.x, pair = t & 31, dir = t >> 5;
+  const int p0 = k > 0 ? 2 : 0, m = len - p0;
+  if (dir < 2 && pair < NP && 2 * pair < nl) {
+    auto rhs2 = [&](int cell) { return make_float2(RHS(2 * pair, cell), RHS(2 * pair + 1, cell)); };
+    float2 Xv[2][5];
+    const bool two = 2 * pair + 1 < nl;
+    if (dir == 0)
+      elim_pass2([&](int i) { return band_row2<NL>(band, p0 + i, pair, false); },
+                 [&](int i) { return rhs2(p0 + i); }, m, Xv, bad, two);
+    else
+      elim_pass2([&](int i) { return band_row2<NL>(band, p0 + m - 1 - i, pair, true); },
+                 [&](int i) { return rhs2(p0 + m - 1 - i); }, m, Xv, bad, two);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 5; ++b) {
+        X[dir][2 * pair][a * 5 + b] = Xv[a][b].x;
+        X[dir][2 * pair + 1][a * 5 + b] = Xv[a][b].y;
+      }
+  }
+  __syncthreads();
+  if (t < nl) {
+    float XL[2][5], XF[2][5];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 5; ++b) {
+        XL[a][b] = X[0][t][a * 5 + b];
+        XF[a][b] = X[1][t][a * 5 + b];
+      }
+    write_record<NL>(band, t, k, S, len, XL, XF, [&](int i) { return RHS(t, i); }, rec, nlines, gline0 + t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase 3 for the lines of a tile: the interior [p0, p0+m) of every line
 // solved with the separators' values on the right side, by a twisted LU:
-// thread role 0 eliminates rows 0..h-1 top-down, role 1 rows m-1..h
-// bottom-up, a 4 x 4 seam solve gives x_{h-2..h+1}, and both substitute
-// back outward (m >= 4; shorter interiors: role 0 alone).  Factors (g, dl,
-// z) overwrite the band slots a, b, c of each row.  All threads of the
-// block must call it (it synchronises).  Lines line0 + lane of role r are
-// handled by threads [r * NL, (r + 1) * NL).  RHS(line, i): right side of
-// interior row i (separator terms included).  PUT(line, i, x): solution.
+// role 0 eliminates rows 0..h-1 top-down, role 1 rows m-1..h bottom-up, a
+// 4 x 4 seam solve gives x_{h-2..h+1}, and both substitute back outward
+// (m >= 4; shorter interiors: role 0 alone).  Each thread carries two lines
+// (a pair).  Factors (g, dl, z) overwrite the band slots a, b, c of each
+// row.  All threads of the block must call it (it synchronises).  Role r
+// is warp r, one thread per pair of lines.  RHS(pair, i): right side of
+// interior row i (separator terms included).  PUT(pair, i, x): solution.
+
+struct LU2 {
+  float2 g1, d1, z1, g2, d2, z2;
+};
 template <int NL>
-struct Seam {
-  LUState<float> top[NL], bot[NL];
+struct Seam2 {
+  LU2 top[NL / 2], bot[NL / 2];
   float x[NL][4];
 };
+__device__ __forceinline__ void lu2_step(LU2& s, const Row2& R, float2 r, float2& g, float2& dl, float2& z,
+                                         float2& chk) {
+  const float2 beta = p_fma(p_neg(R.a), s.g2, R.b);
+  const float2 mu = p_fma(p_neg(beta), s.g1, p_fma(p_neg(R.a), s.d2, R.c));
+  const float2 inv = p_rcp(mu);
+  g = p_mul(p_fma(p_neg(beta), s.d1, R.d), inv);
+  dl = p_mul(R.e, inv);
+  z = p_mul(p_fma(p_neg(beta), s.z1, p_fma(p_neg(R.a), s.z2, r)), inv);
+  s.g2 = s.g1;
+  s.d2 = s.d1;
+  s.z2 = s.z1;
+  s.g1 = g;
+  s.d1 = dl;
+  s.z1 = z;
+  chk = p_fma(mu, inv, chk);
+}
+__device__ __forceinline__ LUState<float> lane_state(const LU2& s, int lane) {
+  LUState<float> r;
+  r.g1 = lane ? s.g1.y : s.g1.x;
+  r.d1 = lane ? s.d1.y : s.d1.x;
+  r.z1 = lane ? s.z1.y : s.z1.x;
+  r.g2 = lane ? s.g2.y : s.g2.x;
+  r.d2 = lane ? s.d2.y : s.d2.x;
+  r.z2 = lane ? s.z2.y : s.z2.x;
+  return r;
+}
+
 template <int NL, class RhsF, class PutF>
-__device__ __forceinline__ void twisted_solve(float* band, Seam<NL>& SM, int nl, int p0, int m, RhsF RHS, PutF PUT,
-                                              int& bad) {
-  const int t = threadIdx.x, role = t / NL, line = t % NL;
-  const bool act = role < 2 && line < nl;
+__device__ __forceinline__ void twisted_solve2(float* band, Seam2<NL>& SM, int nl, int p0, int m, RhsF RHS, PutF PUT,
+                                               int& bad) {
+  constexpr int NP = NL / 2;
+  static_assert(NP <= 32, "one warp per role");
+  // the two roles run in different warps (no divergence between them)
+  const int t = threadIdx.x, role = t >> 5, pair = t & 31;
+  const bool act = role < 2 && pair < NP && 2 * pair < nl;
+  const bool two = 2 * pair + 1 < nl;  // the pair's second line exists
   const bool tw = m >= 4;
   const int h = tw ? m / 2 : m;
-  LUState<float> lu;
-  lu.reset();
-  float chk = 0.f;
-  auto fac = [&](int i) { return band + (p0 + i) * 5 * NL + line; };
+  const float2 z0 = p_splat(0.f);
+  LU2 lu;
+  lu.g1 = lu.d1 = lu.z1 = lu.g2 = lu.d2 = lu.z2 = z0;
+  float2 chk = z0;
+  auto fac = [&](int i) { return reinterpret_cast<float2*>(band + (p0 + i) * 5 * NL) + pair; };
   auto row_nat = [&](int i) {
-    Row R = band_row<NL>(band, p0 + i, line, false);
-    if (i == 0) R.b = 0.f;
-    if (i <= 1) R.a = 0.f;
-    if (i + 1 >= m) R.d = 0.f;
-    if (i + 2 >= m) R.e = 0.f;
+    Row2 R = band_row2<NL>(band, p0 + i, pair, false);
+    if (i == 0) R.b = z0;
+    if (i <= 1) R.a = z0;
+    if (i + 1 >= m) R.d = z0;
+    if (i + 2 >= m) R.e = z0;
     return R;
   };
   if (act && role == 0) {
-#pragma unroll 4
     for (int i = 0; i < h; ++i) {
-      const Row R = row_nat(i);
-      float g, dl, z;
-      lu.step(R.a, R.b, R.c, R.d, R.e, RHS(line, i), g, dl, z, chk);
-      float* q = fac(i);
+      const Row2 R = row_nat(i);
+      float2 g, dl, z;
+      lu2_step(lu, R, RHS(pair, i), g, dl, z, chk);
+      float2* q = fac(i);
       q[0] = g;
-      q[NL] = dl;
-      q[2 * NL] = z;
+      q[NP] = dl;
+      q[2 * NP] = z;
     }
-    SM.top[line] = lu;
+    SM.top[pair] = lu;
   }
   if (act && role == 1 && tw) {
-#pragma unroll 4
     for (int i = m - 1; i >= h; --i) {
-      const Row R = row_nat(i);
-      float g, dl, z;
-      lu.step(R.e, R.d, R.c, R.b, R.a, RHS(line, i), g, dl, z, chk);
-      float* q = fac(i);
+      const Row2 R = row_nat(i);
+      Row2 Rr;
+      Rr.a = R.e;
+      Rr.b = R.d;
+      Rr.c = R.c;
+      Rr.d = R.b;
+      Rr.e = R.a;
+      float2 g, dl, z;
+      lu2_step(lu, Rr, RHS(pair, i), g, dl, z, chk);
+      float2* q = fac(i);
       q[0] = g;
-      q[NL] = dl;
-      q[2 * NL] = z;
+      q[NP] = dl;
+      q[2 * NP] = z;
     }
-    SM.bot[line] = lu;
+    SM.bot[pair] = lu;
   }
   __syncthreads();
-  if (act && role == 0 && tw) {
+  if (tw && t < nl) {  // one seam per line
     float x[4] = {0.f, 0.f, 0.f, 0.f};
-    if (!seam(SM.top[line], SM.bot[line], x)) bad = 1;
-    for (int q = 0; q < 4; ++q) SM.x[line][q] = x[q];
+    if (!seam(lane_state(SM.top[t >> 1], t & 1), lane_state(SM.bot[t >> 1], t & 1), x)) bad = 1;
+    for (int q = 0; q < 4; ++q) SM.x[t][q] = x[q];
   }
   __syncthreads();
   if (act && role == 0) {
-    float x1, x2;
+    float2 xa, xb;  // x_{i+1}, x_{i+2}
     int i0;
     if (tw) {
-      x2 = SM.x[line][1];  // x_{h-1}
-      x1 = SM.x[line][0];  // x_{h-2}
-      PUT(line, h - 1, x2);
-      PUT(line, h - 2, x1);
+      xa = make_float2(SM.x[2 * pair][0], SM.x[2 * pair + 1][0]);  // x_{h-2}
+      xb = make_float2(SM.x[2 * pair][1], SM.x[2 * pair + 1][1]);  // x_{h-1}
+      PUT(pair, h - 1, xb);
+      PUT(pair, h - 2, xa);
       i0 = h - 3;
-      float xa = x1, xb = x2;  // x_{i+1}, x_{i+2}
-#pragma unroll 4
-      for (int i = i0; i >= 0; --i) {
-        const float* q = fac(i);
-        const float x = q[2 * NL] - q[0] * xa - q[NL] * xb;
-        PUT(line, i, x);
-        xb = xa;
-        xa = x;
-      }
     } else {
-      float xa = 0.f, xb = 0.f;
-#pragma unroll 4
-      for (int i = h - 1; i >= 0; --i) {
-        const float* q = fac(i);
-        const float x = q[2 * NL] - q[0] * xa - q[NL] * xb;
-        PUT(line, i, x);
-        xb = xa;
-        xa = x;
-      }
+      xa = xb = z0;
+      i0 = h - 1;
     }
-    if (!(chk == chk)) bad = 1;
-  }
-  if (act && role == 1 && tw) {
-    float xa = SM.x[line][3], xb = SM.x[line][2];  // x_{h+1}, x_h
-    PUT(line, h, xb);
-    PUT(line, h + 1, xa);
-#pragma unroll 4
-    for (int i = h + 2; i < m; ++i) {
-      const float* q = fac(i);
-      const float x = q[2 * NL] - q[0] * xa - q[NL] * xb;
-      PUT(line, i, x);
+    for (int i = i0; i >= 0; --i) {
+      const float2* q = fac(i);
+      const float2 x = p_fma(p_neg(q[NP]), xb, p_fma(p_neg(q[0]), xa, q[2 * NP]));
+      PUT(pair, i, x);
       xb = xa;
       xa = x;
     }
-    if (!(chk == chk)) bad = 1;
+    if (!(chk.x == chk.x) || (two && !(chk.y == chk.y))) bad = 1;
+  }
+  if (act && role == 1 && tw) {
+    float2 xa = make_float2(SM.x[2 * pair][3], SM.x[2 * pair + 1][3]);  // x_{h+1}
+    float2 xb = make_float2(SM.x[2 * pair][2], SM.x[2 * pair + 1][2]);  // x_h
+    PUT(pair, h, xb);
+    PUT(pair, h + 1, xa);
+    for (int i = h + 2; i < m; ++i) {
+      const float2* q = fac(i);
+      const float2 x = p_fma(p_neg(q[NP]), xb, p_fma(p_neg(q[0]), xa, q[2 * NP]));
+      PUT(pair, i, x);
+      xb = xa;
+      xa = x;
+    }
+    if (!(chk.x == chk.x) || (two && !(chk.y == chk.y))) bad = 1;
   }
 }
 
@@ -393,409 +565,56 @@ __device__ __forceinline__ void flag_bad(Acc* acc, int bad) {
 // Film tiles.  The FP32 film of the power-law path is the truncated leading
 // float of each height (what the residual kernel writes).  Tiles hold
 // wall-reflected values (eq. BoundaryConditions), so a missing neighbour
-// equals the cell itself.
+// equals the cell itself.  R x C tiles (compile-time shape; rows [0, nr)
+// and columns [0, nc) filled): inside the grid, pairs of values per thread
+// and only constant divisions; at the walls, element by element with
+// reflected indices.
 
-template <int P>
-__device__ __forceinline__ void load_film_f32(float* dst, const float* __restrict__ src, int row0, int nr, int col0,
+template <int R, int C, int P, int NT>
+__device__ __forceinline__ void load_tile_f32(float* dst, const float* __restrict__ src, int row0, int nr, int col0,
                                               int nc, int ny, int nx) {
-  for (int k = threadIdx.x; k < nr * nc; k += kT) {
-    const int r = k / nc, c = k - r * nc;
-    dst[r * P + c] = __ldg(src + (size_t)reflect_index(row0 + r, ny) * nx + reflect_index(col0 + c, nx));
+  const bool inner = row0 >= 0 && row0 + nr <= ny && col0 >= 0 && col0 + nc <= nx;
+  if (inner && ((col0 | nx | nc) & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 7) == 0 && (P & 1) == 0) {
+    constexpr int C2 = C / 2;
+    const int nc2 = nc / 2;
+    const float2* s2 = reinterpret_cast<const float2*>(src + (size_t)row0 * nx + col0);
+    const size_t pitch2 = (size_t)nx / 2;
+    for (int k = threadIdx.x; k < R * C2; k += NT) {
+      const int r = k / C2, c = k - r * C2;
+      if (r < nr && c < nc2) *reinterpret_cast<float2*>(dst + r * P + 2 * c) = __ldg(s2 + r * pitch2 + c);
+    }
+    return;
+  }
+  for (int k = threadIdx.x; k < R * C; k += NT) {
+    const int r = k / C, c = k - r * C;
+    if (r < nr && c < nc)
+      dst[r * P + c] = __ldg(src + (size_t)reflect_index(row0 + r, ny) * nx + reflect_index(col0 + c, nx));
   }
 }
-template <int P>
-__device__ __forceinline__ void load_film_f64(float* dst, const double* __restrict__ src, int row0, int nr, int col0,
+template <int R, int C, int P, int NT>
+__device__ __forceinline__ void load_tile_f64(float* dst, const double* __restrict__ src, int row0, int nr, int col0,
                                               int nc, int ny, int nx) {
-  for (int k = threadIdx.x; k < nr * nc; k += kT) {
-    const int r = k / nc, c = k - r * nc;
-    dst[r * P + c] =
-        f32_of_pos_f64_fast(__ldg(src + (size_t)reflect_index(row0 + r, ny) * nx + reflect_index(col0 + c, nx)));
-  }
-}
-// rows [row0, row0 + nr) x columns [col0, col0 + nc) inside the grid
-template <int P>
-__device__ __forceinline__ void load_block(float* dst, const float* __restrict__ src, int row0, int nr, int col0,
-                                           int nc, int nx) {
-  for (int k = threadIdx.x; k < nr * nc; k += kT) {
-    const int r = k / nc, c = k - r * nc;
-    dst[r * P + c] = __ldg(src + (size_t)(row0 + r) * nx + col0 + c);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// x phase 1: tile of kRX rows x x segment blockIdx.x (the block exists only
-// for grids with more than one x segment).
-
-struct X1Smem {
-  float film[(kRX + 2) * (kLX + 7)];   // rows j0-1.., cols c0-2.. (pitch kLX + 7, odd)
-  float rt[kRX * (kLX + 1)];           // right side [row][cell]
-  float band[(kLX + 2) * 5 * kRX];     // cells c0 .. c1+1
-  float X[2][kRX][10];
-};
-
-__global__ void __launch_bounds__(kT, 3)
-    k_part_x1(ModelK M, LineK<float> L, const float* __restrict__ ul, const float* __restrict__ r,
-              float* __restrict__ rec, Acc* __restrict__ acc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  X1Smem& S = *reinterpret_cast<X1Smem*>(smem_raw);
-  constexpr int FP = kLX + 7, RP = kLX + 1;
-  const int nx = M.nx, ny = M.ny, nS = seg_count<kLX>(nx);
-  const int k = blockIdx.x, j0 = blockIdx.y * kRX;
-  const int c0 = seg_start<kLX>(k, nx), c1 = seg_end<kLX>(k, nx), len = c1 - c0;
-  const bool next = k + 1 < nS;
-  const int ncell = len + (next ? 2 : 0);
-  const int nrow = min(kRX, ny - j0);
-  load_film_f32<FP>(S.film, ul, j0 - 1, nrow + 2, c0 - 2, ncell + 4, ny, nx);
-  load_block<RP>(S.rt, r, j0, nrow, c0, len, nx);
-  __syncthreads();
-  auto film = [&](int line, int cell, int dr, int dc) {
-    return S.film[(line + 1 + dr) * FP + (cell - c0 + 2 + dc)];
-  };
-  build_band<kRX>(L, S.band, nrow, c0, ncell, nx, film);
-  __syncthreads();
-  const int p0 = k > 0 ? 2 : 0, m = len - p0;
-  const int t = threadIdx.x, line = t & 31, dir = t >> 5;
-  int bad = 0;
-  if (dir < 2 && line < nrow) {
-    float X[2][5];
-    if (dir == 0) {
-      elim_pass([&](int i) { return band_row<kRX>(S.band, p0 + i, line, false); },
-                [&](int i) { return S.rt[line * RP + p0 + i]; }, m, X, bad);
-    } else {
-      elim_pass([&](int i) { return band_row<kRX>(S.band, p0 + m - 1 - i, line, true); },
-                [&](int i) { return S.rt[line * RP + p0 + m - 1 - i]; }, m, X, bad);
-    }
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 5; ++b) S.X[dir][line][a * 5 + b] = X[a][b];
-  }
-  if (dir < 2) flag_bad(acc, bad);
-  __syncthreads();
-  if (dir == 0 && line < nrow) {
-    float XL[2][5], XF[2][5];
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 5; ++b) {
-        XL[a][b] = S.X[0][line][a * 5 + b];
-        XF[a][b] = S.X[1][line][a * 5 + b];
+  const bool inner = row0 >= 0 && row0 + nr <= ny && col0 >= 0 && col0 + nc <= nx;
+  if (inner && ((col0 | nx | nc) & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (P & 1) == 0) {
+    constexpr int C2 = C / 2;
+    const int nc2 = nc / 2;
+    const double2* s2 = reinterpret_cast<const double2*>(src + (size_t)row0 * nx + col0);
+    const size_t pitch2 = (size_t)nx / 2;
+    for (int k = threadIdx.x; k < R * C2; k += NT) {
+      const int r = k / C2, c = k - r * C2;
+      if (r < nr && c < nc2) {
+        const double2 v = __ldg(s2 + r * pitch2 + c);
+        *reinterpret_cast<float2*>(dst + r * P + 2 * c) =
+            make_float2(f32_of_pos_f64_fast(v.x), f32_of_pos_f64_fast(v.y));
       }
-    write_record<kRX>(S.band, line, k, nS, len, XL, XF, [&](int i) { return S.rt[line * RP + i]; }, rec,
-                      (size_t)ny, (size_t)(j0 + line));
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Phase 2: the reduced block-tridiagonal system of every line (one thread
-// per line).  rec is [S-1][kRec][nlines]; the forward sweep overwrites
-// values 10..15 of each separator with W^-1 and the reduced right side.
-// xs receives the separators' values, [S-1][2][nlines].
-
-__global__ void __launch_bounds__(128)
-    k_part_red(float* __restrict__ rec, int nS, int nlines, float* __restrict__ xs, Acc* __restrict__ acc) {
-  const int line = blockIdx.x * blockDim.x + threadIdx.x;
-  int bad = 0;
-  if (line < nlines) {
-    const size_t NL = (size_t)nlines;
-    M2 Wi = mk2(0.f, 0.f, 0.f, 0.f), Up = mk2(0.f, 0.f, 0.f, 0.f);
-    float g0 = 0.f, g1 = 0.f;
-    for (int s = 1; s < nS; ++s) {
-      float* R = rec + (size_t)(s - 1) * kRec * NL + line;
-      float v[kRec];
-#pragma unroll
-      for (int q = 0; q < kRec; ++q) v[q] = R[q * NL];
-      M2 D = mk2(v[0] + v[14], v[1] + v[15], v[2] + v[16], v[3] + v[17]);
-      float h0 = v[8] + v[18], h1 = v[9] + v[19];
-      if (s >= 2) {
-        const M2 Lam = mul2(mk2(v[10], v[11], v[12], v[13]), Wi);
-        D = sub2(D, mul2(Lam, Up));
-        float l0, l1;
-        mv2(Lam, g0, g1, l0, l1);
-        h0 -= l0;
-        h1 -= l1;
-      }
-      const float det = D.a * D.d - D.b * D.c;
-      const float id = 1.f / det;
-      if (!(det != 0.f) || !(id - id == 0.f)) bad = 1;
-      Wi = mk2(D.d * id, -D.b * id, -D.c * id, D.a * id);
-      Up = mk2(v[4], v[5], v[6], v[7]);
-      g0 = h0;
-      g1 = h1;
-      R[10 * NL] = Wi.a;
-      R[11 * NL] = Wi.b;
-      R[12 * NL] = Wi.c;
-      R[13 * NL] = Wi.d;
-      R[14 * NL] = g0;
-      R[15 * NL] = g1;
     }
-    // back substitution: x_s = W_s^-1 (g_s - U_s x_{s+1})
-    float x0 = 0.f, x1 = 0.f;
-    for (int s = nS - 1; s >= 1; --s) {
-      const float* R = rec + (size_t)(s - 1) * kRec * NL + line;
-      float h0 = R[14 * NL], h1 = R[15 * NL];
-      if (s + 1 < nS) {
-        float u0, u1;
-        mv2(mk2(R[4 * NL], R[5 * NL], R[6 * NL], R[7 * NL]), x0, x1, u0, u1);
-        h0 -= u0;
-        h1 -= u1;
-      }
-      mv2(mk2(R[10 * NL], R[11 * NL], R[12 * NL], R[13 * NL]), h0, h1, x0, x1);
-      float* o = xs + (size_t)(s - 1) * 2 * NL + line;
-      o[0] = x0;
-      o[NL] = x1;
-    }
+    return;
   }
-  flag_bad(acc, bad);
-}
-
-// ---------------------------------------------------------------------------
-// x phase 3 + y phase 1: tile = y segment blockIdx.y x x segment blockIdx.x.
-
-struct XYSmem {
-  float film[(kLY + 6) * (kLX + 5)];   // rows r0-2 .. r1+3, cols c0-2 .. c1+1 (pitch kLX + 5)
-  float wt[kLY * (kLX + 1)];           // right side r, then w, [row][col]
-  // x band [cell < kLX][5][row < kLY], then y band [cell < kLY + 2][5][col < kLX]
-  float band[(kLX * kLY > (kLY + 2) * kLX ? kLX * kLY : (kLY + 2) * kLX) * 5];
-  Seam<kLY> seam;
-  float xsl[kLY][2], xsr[kLY][2];
-};
-
-__global__ void __launch_bounds__(kT, 3)
-    k_part_xy(ModelK M, LineK<float> L, const float* __restrict__ ul, float* __restrict__ rw,
-              const float* __restrict__ xsx, float* __restrict__ recy, Acc* __restrict__ acc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  XYSmem& S = *reinterpret_cast<XYSmem*>(smem_raw);
-  constexpr int FP = kLX + 5, WP = kLX + 1;
-  const int nx = M.nx, ny = M.ny;
-  const int nSx = seg_count<kLX>(nx), nSy = seg_count<kLY>(ny);
-  const int kx = blockIdx.x, ky = blockIdx.y;
-  const int c0 = seg_start<kLX>(kx, nx), c1 = seg_end<kLX>(kx, nx), nc = c1 - c0;
-  const int r0 = seg_start<kLY>(ky, ny), r1 = seg_end<kLY>(ky, ny), nr = r1 - r0;
-  const bool nexty = ky + 1 < nSy;
-  const int nrowy = nr + (nexty ? 2 : 0);  // y band rows: segment + next separator
-  load_film_f32<FP>(S.film, ul, r0 - 2, nrowy + 4, c0 - 2, nc + 4, ny, nx);
-  load_block<WP>(S.wt, rw, r0, nr, c0, nc, nx);
-  for (int q = threadIdx.x; q < 2 * nr; q += kT) {
-    const int row = q >> 1, e = q & 1;
-    S.xsl[row][e] = kx > 0 ? xsx[((size_t)(kx - 1) * 2 + e) * ny + r0 + row] : 0.f;
-    S.xsr[row][e] = kx + 1 < nSx ? xsx[((size_t)kx * 2 + e) * ny + r0 + row] : 0.f;
-  }
-  __syncthreads();
-  // ---- x band of the tile's rows, cells c0 .. c1-1
-  {
-    auto film = [&](int line, int cell, int dr, int dc) {
-      return S.film[(line + 2 + dr) * FP + (cell - c0 + 2 + dc)];
-    };
-    build_band<kLY>(L, S.band, nr, c0, nc, nx, film);
-  }
-  __syncthreads();
-  int bad = 0;
-  // ---- x phase 3: interiors of the tile's rows; separators from phase 2
-  {
-    const int p0 = kx > 0 ? 2 : 0, m = nc - p0;
-    const bool right = kx + 1 < nSx;
-    auto B = [&](int cell, int q, int line) { return S.band[(cell * 5 + q) * kLY + line]; };
-    auto rhs = [&](int line, int i) {
-      const int cell = p0 + i;
-      float f = S.wt[line * WP + cell];
-      if (kx > 0) {
-        if (i == 0) f -= B(cell, 0, line) * S.xsl[line][0] + B(cell, 1, line) * S.xsl[line][1];
-        if (i == 1) f -= B(cell, 0, line) * S.xsl[line][1];
-      }
-      if (right) {
-        if (i == m - 2) f -= B(cell, 4, line) * S.xsr[line][0];
-        if (i == m - 1) f -= B(cell, 3, line) * S.xsr[line][0] + B(cell, 4, line) * S.xsr[line][1];
-      }
-      return f;
-    };
-    auto put = [&](int line, int i, float x) { S.wt[line * WP + p0 + i] = x; };
-    twisted_solve<kLY>(S.band, S.seam, nr, p0, m, rhs, put, bad);
-    if (kx > 0)
-      for (int q = threadIdx.x; q < 2 * nr; q += kT) S.wt[(q >> 1) * WP + (q & 1)] = S.xsl[q >> 1][q & 1];
-  }
-  __syncthreads();
-  // ---- store w; y band of the tile's columns, rows r0 .. r1 (+ next separator)
-  for (int k = threadIdx.x; k < nr * nc; k += kT) {
-    const int rr = k / nc, cc = k - rr * nc;
-    rw[(size_t)(r0 + rr) * nx + c0 + cc] = S.wt[rr * WP + cc];
-  }
-  {
-    auto film = [&](int line, int cell, int dr, int dc) {
-      return S.film[(cell - r0 + 2 + dr) * FP + (line + 2 + dc)];
-    };
-    build_band<kLX>(L, S.band, nc, r0, nrowy, ny, film);
-  }
-  __syncthreads();
-  // ---- y phase 1 (lines = the tile's columns)
-  if (nSy > 1) {
-    float(*X)[kLX][10] = reinterpret_cast<float(*)[kLX][10]>(S.film);  // film no longer needed
-    const int t = threadIdx.x, line = t % kLX, dir = t / kLX;
-    const int p0 = ky > 0 ? 2 : 0, m = nr - p0;
-    if (dir < 2 && line < nc) {
-      float Xv[2][5];
-      if (dir == 0)
-        elim_pass([&](int i) { return band_row<kLX>(S.band, p0 + i, line, false); },
-                  [&](int i) { return S.wt[(p0 + i) * WP + line]; }, m, Xv, bad);
-      else
-        elim_pass([&](int i) { return band_row<kLX>(S.band, p0 + m - 1 - i, line, true); },
-                  [&](int i) { return S.wt[(p0 + m - 1 - i) * WP + line]; }, m, Xv, bad);
-      for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 5; ++b) X[dir][line][a * 5 + b] = Xv[a][b];
-    }
-    __syncthreads();
-    if (dir == 0 && line < nc) {
-      float XL[2][5], XF[2][5];
-      for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 5; ++b) {
-          XL[a][b] = X[0][line][a * 5 + b];
-          XF[a][b] = X[1][line][a * 5 + b];
-        }
-      write_record<kLX>(S.band, line, ky, nSy, nr, XL, XF, [&](int i) { return S.wt[i * WP + line]; }, recy,
-                        (size_t)nx, (size_t)(c0 + line));
-    }
-  }
-  flag_bad(acc, bad);
-}
-
-// ---------------------------------------------------------------------------
-// y phase 3, Newton update and reductions: tile = y segment blockIdx.y x
-// kCY columns from blockIdx.x * kCY.
-
-struct YCSmem {
-  float film[(kLY + 4) * (kCY + 3)];   // rows r0-2 .. r1+1, cols i0-1 .. (pitch kCY + 3)
-  float wt[kLY * (kCY + 1)];           // w, then v
-  float band[kLY * 5 * kCY];
-  Seam<kCY> seam;
-  float ysl[kCY][2], ysr[kCY][2];
-  float red[kT / 32];
-  int nf[kT / 32];
-};
-
-__global__ void __launch_bounds__(kT, 3)
-    k_part_yc(ModelK M, LineK<float> L, const double* __restrict__ u, const float* __restrict__ w,
-              const float* __restrict__ xsy, double* __restrict__ unew, double* __restrict__ vout,
-              Acc* __restrict__ acc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  YCSmem& S = *reinterpret_cast<YCSmem*>(smem_raw);
-  constexpr int FP = kCY + 3, WP = kCY + 1;
-  const int nx = M.nx, ny = M.ny, nSy = seg_count<kLY>(ny);
-  const int i0 = blockIdx.x * kCY, ky = blockIdx.y;
-  const int nc = min(kCY, nx - i0);
-  const int r0 = seg_start<kLY>(ky, ny), r1 = seg_end<kLY>(ky, ny), nr = r1 - r0;
-  load_film_f64<FP>(S.film, u, r0 - 2, nr + 4, i0 - 1, nc + 2, ny, nx);
-  load_block<WP>(S.wt, w, r0, nr, i0, nc, nx);
-  for (int q = threadIdx.x; q < 2 * nc; q += kT) {
-    const int col = q >> 1, e = q & 1;
-    S.ysl[col][e] = ky > 0 ? xsy[((size_t)(ky - 1) * 2 + e) * nx + i0 + col] : 0.f;
-    S.ysr[col][e] = ky + 1 < nSy ? xsy[((size_t)ky * 2 + e) * nx + i0 + col] : 0.f;
-  }
-  __syncthreads();
-  {
-    auto film = [&](int line, int cell, int dr, int dc) {
-      return S.film[(cell - r0 + 2 + dr) * FP + (line + 1 + dc)];
-    };
-    build_band<kCY>(L, S.band, nc, r0, nr, ny, film);
-  }
-  __syncthreads();
-  int bad = 0;
-  {
-    const int p0 = ky > 0 ? 2 : 0, m = nr - p0;
-    const bool right = ky + 1 < nSy;
-    auto B = [&](int cell, int q, int line) { return S.band[(cell * 5 + q) * kCY + line]; };
-    auto rhs = [&](int line, int i) {
-      const int cell = p0 + i;
-      float f = S.wt[cell * WP + line];
-      if (ky > 0) {
-        if (i == 0) f -= B(cell, 0, line) * S.ysl[line][0] + B(cell, 1, line) * S.ysl[line][1];
-        if (i == 1) f -= B(cell, 0, line) * S.ysl[line][1];
-      }
-      if (right) {
-        if (i == m - 2) f -= B(cell, 4, line) * S.ysr[line][0];
-        if (i == m - 1) f -= B(cell, 3, line) * S.ysr[line][0] + B(cell, 4, line) * S.ysr[line][1];
-      }
-      return f;
-    };
-    auto put = [&](int line, int i, float x) { S.wt[(p0 + i) * WP + line] = x; };
-    twisted_solve<kCY>(S.band, S.seam, nc, p0, m, rhs, put, bad);
-    if (ky > 0)
-      for (int q = threadIdx.x; q < 2 * nc; q += kT) S.wt[(q & 1) * WP + (q >> 1)] = S.ysl[q >> 1][q & 1];
-  }
-  flag_bad(acc, bad);
-  __syncthreads();
-  // ---- u_{k+1} = u_k + v (one native FP64 add per cell), max |v/u_k|, positivity
-  float err = 0.f;
-  int nonfinite = 0;
-  for (int k = threadIdx.x; k < nr * kCY; k += kT) {
-    const int rr = k / kCY, cc = k - rr * kCY;
-    if (cc >= nc) continue;
-    const size_t idx = (size_t)(r0 + rr) * nx + i0 + cc;
-    const float x = S.wt[rr * WP + cc];
-    const double uk = __ldg(u + idx);
-    const double un = uk + (double)x;
-    unew[idx] = un;
-    if (vout) vout[idx] = (double)x;
-    const float ru = rel_update(x, uk);
-    if (!(ru <= err)) err = ru;
-    if (!positive_finite_bits(un)) nonfinite = 1;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const float e2 = __shfl_xor_sync(0xffffffffu, err, o);
-    if (!(e2 <= err)) err = e2;
-    nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    S.red[threadIdx.x >> 5] = err;
-    S.nf[threadIdx.x >> 5] = nonfinite;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float e = S.red[0];
-    int n = S.nf[0];
-    for (int q = 1; q < kT / 32; ++q) {
-      if (!(S.red[q] <= e)) e = S.red[q];
-      n |= S.nf[q];
-    }
-    atomicMax(&acc->err_bits, __float_as_uint(fabsf(e)) | (e == e ? 0u : 0x7fc00000u));
-    if (n) atomicOr(&acc->nonfinite, 1);
-  }
-}
-
-// The iteration's scalars: max |G| from the residual kernel's partials,
-// the accumulators of the partitioned kernels (then cleared for the next
-// iteration).  One block.
-static __global__ void __launch_bounds__(256)
-    k_part_finalize(const PartX* __restrict__ px, int nx_part, Acc* __restrict__ acc, Scalars* __restrict__ out) {
-  __shared__ double s_g[256];
-  __shared__ int s_pv[256];
-  const int t = threadIdx.x;
-  double g = 0.0;
-  int pv = 0;
-  for (int k = t; k < nx_part; k += 256) {
-    if (!(px[k].gnorm <= g)) g = px[k].gnorm;
-    pv |= px[k].pivot;
-  }
-  s_g[t] = g;
-  s_pv[t] = pv;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (t < o) {
-      if (!(s_g[t + o] <= s_g[t])) s_g[t] = s_g[t + o];
-      s_pv[t] |= s_pv[t + o];
-    }
-    __syncthreads();
-  }
-  if (t == 0) {
-    Scalars s;
-    s.err = (double)__uint_as_float(acc->err_bits);
-    s.gnorm = s_g[0];
-    s.hmin = INFINITY;
-    s.mass.lo = s.mass.hi = 0ull;
-    s.nonfinite = acc->nonfinite;
-    s.pivot = s_pv[0] | acc->pivot;
-    *out = s;
-    Acc z;
-    z.err_bits = 0u;
-    z.nonfinite = 0;
-    z.pivot = 0;
-    z.pad = 0;
-    *acc = z;
+  for (int k = threadIdx.x; k < R * C; k += NT) {
+    const int r = k / C, c = k - r * C;
+    if (r < nr && c < nc)
+      dst[r * P + c] =
+          f32_of_pos_f64_fast(__ldg(src + (size_t)reflect_index(row0 + r, ny) * nx + reflect_index(col0 + c, nx)));
   }
 }
 

@@ -1,19 +1,31 @@
 // tf_rhs_packed.cuh -- the FP32-bulk residual kernel on packed FP32x2 pipes.
 //
-// Same computation as k_rhs<ModeF32B> (tf_sweeps.cuh): the residual
-// G = u_k + theta dt D(u_k) - b^n of eq. CrankNicolson in double-float,
-// with D the flux-form operator of Sec. Flux Discretization, or the explicit
-// part b^n = u^n - (1 - theta) dt D(u^n).  Each thread carries two
-// horizontally adjacent cells through every double-float operation, one
-// lane each of the sm_100+ paired FP32 instructions (add/mul/fma on float2),
-// in the same per-lane operation order as the scalar double-float code, so
-// the results are the scalar kernel's bit for bit.  Shared memory holds the
-// high and low parts in separate planes, so a pair of cells is one 8-byte
-// load.  Used for the (n, m) = (3, 2) power law; other models take the scalar
-// kernel.
+// The residual G = u_k + theta dt D(u_k) - b^n of eq. CrankNicolson in
+// double-float, with D the flux-form operator of Sec. Flux Discretization,
+// or the explicit part b^n = u^n - (1 - theta) dt D(u^n) (the computation of
+// k_rhs<ModeF32B>, tf_sweeps.cuh, with fewer FP32 operations).  Each thread
+// carries two horizontally adjacent cells through every double-float
+// operation, one lane each of the sm_100+ paired FP32 instructions
+// (add/mul/fma on float2).  Shared memory holds the high and low parts in
+// separate planes, so a pair of cells is one 8-byte load.  Used for the
+// (n, m) = (3, 2) power law; other models take the scalar kernel.
+//
+// Where the operations are saved:
+//   * differences of neighbouring heights.  On a tile whose heights (halo
+//     included) all lie within 25% of each other, the difference of two
+//     leading floats is exact (Sterbenz) and so are the sums of up to four
+//     of them (they stay below the smallest height's binade), so a height
+//     difference is (hi - hi', lo - lo') and the Laplacian's leading part a
+//     plain sum; the trailing parts round at 2^-24 of values that are
+//     themselves 2^-24 of the heights.  Other tiles take the general
+//     double-float operations (TwoSum throughout), chosen per block.
+//   * 1/h: the MUFU reciprocal y of the leading float refined by one Newton
+//     step in double-float arithmetic, 1/h = y + y (1 - h y), which carries
+//     the square of the reciprocal's 2^-23 error.
+//   * face fluxes and the divergence stay unnormalised until G is formed.
 #pragma once
 
-#include "tf_sweeps.cuh"
+#include "tf_partition.cuh"
 
 namespace tf {
 
@@ -24,12 +36,7 @@ struct df2 {
   float2 hi, lo;
 };
 
-__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, p_neg(b)); }
-__device__ __forceinline__ float2 p_splat(float a) { return make_float2(a, a); }
+// (the paired FP32 operations p_add, p_mul, p_fma, ... are in tf_partition.cuh)
 
 __device__ __forceinline__ void p_two_sum(float2 a, float2 b, float2& s, float2& e) {
   s = p_add(a, b);
@@ -123,70 +130,31 @@ __device__ __forceinline__ df2 mid2(df2 A, df2 B) {
   return d2(make_float2(A.hi.y, B.hi.x), make_float2(A.lo.y, B.lo.x));
 }
 
-// KIND: kRhsResidual (G from u_k and the stored b^n), kRhsExplicit (b^n from
-// u^n) or kRhsBoth (b^n from u^n, stored, and G of the first iteration,
-// u_0 = u^n, from the same stored b^n -- what kRhsResidual would compute).
-template <int KIND>
-__global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per SM: up to 64 registers
-    k_rhs_packed(ModelK M, RhsK<df64> RK, const double* __restrict__ u, df64* __restrict__ bn,
-                 float* __restrict__ rhs, float* __restrict__ ulp, PartX* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  RhsPackedSmem& S = *reinterpret_cast<RhsPackedSmem*>(smem_raw);
+// the difference of two double-float heights: exact leading part when the
+// two leading floats are within a factor 2 (FAST), else the general one
+template <bool FAST> __device__ __forceinline__ df2 hdiff(df2 a, df2 b) {
+  if constexpr (FAST) return d2(p_sub(a.hi, b.hi), p_sub(a.lo, b.lo));
+  return d2_sub_u(a, b);
+}
+// 1/a for a positive double-float a (the refined MUFU reciprocal)
+__device__ __forceinline__ df2 d2_rcp_fast(df2 a) {
+  const float2 y = make_float2(rcp(a.hi.x), rcp(a.hi.y));
+  float2 e = p_fma(p_neg(a.hi), y, p_splat(1.0f));
+  e = p_fma(p_neg(a.lo), y, e);
+  return d2(y, p_mul(y, e));
+}
+
+// Stages 2-4 of the residual (see k_rhs_packed); FAST selects the height
+// differences.  Returns max|G| over the thread's cells.
+template <int KIND, bool FAST>
+__device__ __forceinline__ float rhs_stages(RhsPackedSmem& S, const RhsK<df64>& RK, int x0, int j0, int nx,
+                                            int ny, df64* __restrict__ bn,
+                                            float* __restrict__ rhs, float* __restrict__ ulp,
+                                            const df64 (&bnr)[kPR * kPC / 2 / kPT][2]) {
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * kPC, j0 = blockIdx.y * kPR;
-  const int nx = M.nx, ny = M.ny;
-  // b^n of this thread's stage-4 cells, loaded first so that its latency
-  // overlaps the stencil stages
-  constexpr int W4 = kPC / 2, N4 = kPR * W4 / kPT;
-  static_assert(kPR * W4 == N4 * kPT, "stage 4 gives every thread the same number of pairs");
-  df64 bnr[N4][2];
-  if constexpr (KIND == kRhsResidual) {
-#pragma unroll
-    for (int e = 0; e < N4; ++e) {
-      const int k = tid + e * kPT, r = k / W4, c = 2 * (k - r * W4);
-      const int gj = j0 + r, gi = x0 + c;
-      bnr[e][0] = bnr[e][1] = df_make(1.0f, 0.0f);
-      if (gj < ny && gi < nx) {
-        const size_t idx = (size_t)gj * nx + gi;
-        bnr[e][0] = bn[idx];
-        if (gi + 1 < nx) bnr[e][1] = bn[idx + 1];
-      }
-    }
-  }
-  // ---- stage 1: film tile (two-cell halo, wall-reflected) as double-float planes
-  {
-    constexpr int W2 = (kPC + 8) / 2;
-    const bool inner_x = x0 - 4 >= 0 && x0 + kPC + 4 <= nx && (nx & 1) == 0 &&
-                         (reinterpret_cast<uintptr_t>(u) & 15) == 0;
-    // all of a thread's loads are issued before the first conversion
-    constexpr int NP = (kPR + 4) * W2, N1 = (NP + kPT - 1) / kPT;
-    double2 v[N1];
-#pragma unroll
-    for (int i = 0; i < N1; ++i) {
-      const int k = min(tid + i * kPT, NP - 1);
-      const int r = k / W2, c = 2 * (k - r * W2);
-      const int gj = reflect_index(j0 - 2 + r, ny);
-      if (inner_x) {
-        v[i] = __ldg(reinterpret_cast<const double2*>(u + (size_t)gj * nx + (x0 - 4 + c)));
-      } else {
-        v[i].x = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 4 + c, nx));
-        v[i].y = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 3 + c, nx));
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < N1; ++i) {
-      const int k = tid + i * kPT;
-      if (k >= NP) break;
-      const int r = k / W2, c = 2 * (k - r * W2);
-      const df64 da = df_of_pos_f64_fast(v[i].x), db = df_of_pos_f64_fast(v[i].y);
-      *reinterpret_cast<float2*>(&S.uh[r][c]) = make_float2(da.hi, db.hi);
-      *reinterpret_cast<float2*>(&S.ul[r][c]) = make_float2(da.lo, db.lo);
-    }
-  }
-  __syncthreads();
   // ---- stage 2: lap, f0, f1 of cells (rs, cs): global (j0-1+rs, x0-2+cs)
   {
-    const df2 four = d2_splat(RK.four), inv_ds2 = d2_splat(RK.inv_ds2);
+    const df2 inv_ds2 = d2_splat(RK.inv_ds2);
     const df2 A1 = d2_splat(RK.mc.A1), B1 = d2_splat(RK.mc.B1), C = d2_splat(RK.mc.C);
     const bool unitC = RK.mc.unitC;
     constexpr int W2 = (kPC + 4) / 2;
@@ -197,15 +165,21 @@ __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per 
       const df2 Wp = ld2(S.uh[tr], S.ul[tr], tc - 2), Ep = ld2(S.uh[tr], S.ul[tr], tc + 2);
       const df2 E = mid2(uc, Ep), Wn = mid2(Wp, uc);
       const df2 Sn = ld2(S.uh[tr + 1], S.ul[tr + 1], tc), Nn = ld2(S.uh[tr - 1], S.ul[tr - 1], tc);
-      const df2 nb = d2_add_u(d2_add_u(E, Wn), d2_add_u(Sn, Nn));
-      st2(S.laph[rs], S.lapl[rs], cs, d2_norm(d2_mul_u(d2_sub_u(nb, d2_mul_u(four, uc)), inv_ds2)));
+      df2 lap;
+      if constexpr (FAST) {
+        const df2 dE = hdiff<true>(E, uc), dW = hdiff<true>(Wn, uc);
+        const df2 dS = hdiff<true>(Sn, uc), dN = hdiff<true>(Nn, uc);
+        lap = d2(p_add(p_add(dE.hi, dW.hi), p_add(dS.hi, dN.hi)), p_add(p_add(dE.lo, dW.lo), p_add(dS.lo, dN.lo)));
+      } else {
+        lap = d2_add_u(d2_add_u(d2_sub_u(E, uc), d2_sub_u(Wn, uc)), d2_add_u(d2_sub_u(Sn, uc), d2_sub_u(Nn, uc)));
+      }
+      st2(S.laph[rs], S.lapl[rs], cs, d2_mul_u(lap, inv_ds2));
       // f0 = C h^3, f1 = A1 - B1 / h (the (3, 2) power law)
-      const df2 s = d2_rcp(uc);
-      const df2 h2 = d2_mul(uc, uc);
-      const df2 f0 = unitC ? d2_mul(h2, uc) : d2_mul(d2_mul(C, h2), uc);
-      const df2 f1 = d2_sub(A1, d2_mul(B1, s));
-      st2(S.f0h[rs], S.f0l[rs], cs, d2_norm(f0));
-      st2(S.f1h[rs], S.f1l[rs], cs, d2_norm(f1));
+      const df2 h2 = d2_mul_u(uc, uc);
+      const df2 f0 = unitC ? d2_mul_u(h2, uc) : d2_mul_u(d2_mul_u(C, h2), uc);
+      const df2 f1 = d2_sub_u(A1, d2_mul_u(B1, d2_rcp_fast(uc)));
+      st2(S.f0h[rs], S.f0l[rs], cs, f0);
+      st2(S.f1h[rs], S.f1l[rs], cs, f1);
     }
   }
   __syncthreads();
@@ -221,8 +195,8 @@ __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per 
         const df2 f1P = ld2(S.f1h[q], S.f1l[q], c + 2), f1Q = ld2(S.f1h[q + 1], S.f1l[q + 1], c + 2);
         const df2 lP = ld2(S.laph[q], S.lapl[q], c + 2), lQ = ld2(S.laph[q + 1], S.lapl[q + 1], c + 2);
         const df2 uP = ld2(S.uh[q + 1], S.ul[q + 1], c + 4), uQ = ld2(S.uh[q + 2], S.ul[q + 2], c + 4);
-        df2 F = d2_norm(d2_add_u(d2_mul_u(d2_add_u(f0P, f0Q), d2_sub_u(lQ, lP)),
-                                 d2_mul_u(d2_add_u(f1P, f1Q), d2_sub_u(uQ, uP))));
+        df2 F = d2_add_u(d2_mul_u(d2_add_u(f0P, f0Q), d2_sub_u(lQ, lP)),
+                         d2_mul_u(d2_add_u(f1P, f1Q), hdiff<FAST>(uQ, uP)));
         const int gp = j0 - 1 + q;
         if (!(gp >= 0 && gp + 1 < ny)) F = d2(p_splat(0.0f), p_splat(0.0f));
         st2(S.fyh[q], S.fyl[q], c, F);
@@ -236,8 +210,8 @@ __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per 
       const df2 lP = ld2(S.laph[rs], S.lapl[rs], kf), lR = ld2(S.laph[rs], S.lapl[rs], kf + 2);
       const df2 uP = ld2(S.uh[tr], S.ul[tr], kf + 2), uR = ld2(S.uh[tr], S.ul[tr], kf + 4);
       const df2 f0Q = mid2(f0P, f0R), f1Q = mid2(f1P, f1R), lQ = mid2(lP, lR), uQ = mid2(uP, uR);
-      df2 F = d2_norm(d2_add_u(d2_mul_u(d2_add_u(f0P, f0Q), d2_sub_u(lQ, lP)),
-                               d2_mul_u(d2_add_u(f1P, f1Q), d2_sub_u(uQ, uP))));
+      df2 F = d2_add_u(d2_mul_u(d2_add_u(f0P, f0Q), d2_sub_u(lQ, lP)),
+                       d2_mul_u(d2_add_u(f1P, f1Q), hdiff<FAST>(uQ, uP)));
       const int gp = x0 - 2 + kf;  // left cell of face kf
       if (!(gp >= 0 && gp + 1 < nx)) F.hi.x = F.lo.x = 0.0f;
       if (!(gp + 1 >= 0 && gp + 2 < nx)) F.hi.y = F.lo.y = 0.0f;
@@ -246,6 +220,7 @@ __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per 
   }
   __syncthreads();
   // ---- stage 4: G (or b^n) of the tile's cells, two per thread
+  constexpr int W4 = kPC / 2, N4 = kPR * W4 / kPT;
   const df2 gscale = d2_splat(RK.gscale);
   float g = 0.0f;  // max |G| in FP32: a norm for reporting, not a decision
 #pragma unroll
@@ -295,6 +270,98 @@ __global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per 
       if (!(ag <= g)) g = ag;
     }
   }
+  return g;
+}
+
+// KIND: kRhsResidual (G from u_k and the stored b^n), kRhsExplicit (b^n from
+// u^n) or kRhsBoth (b^n from u^n, stored, and G of the first iteration,
+// u_0 = u^n, from the same stored b^n -- what kRhsResidual would compute).
+template <int KIND>
+__global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per SM: up to 64 registers
+    k_rhs_packed(ModelK M, RhsK<df64> RK, const double* __restrict__ u, df64* __restrict__ bn,
+                 float* __restrict__ rhs, float* __restrict__ ulp, PartX* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RhsPackedSmem& S = *reinterpret_cast<RhsPackedSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kPC, j0 = blockIdx.y * kPR;
+  const int nx = M.nx, ny = M.ny;
+  // b^n of this thread's stage-4 cells, loaded first so that its latency
+  // overlaps the stencil stages
+  constexpr int W4 = kPC / 2, N4 = kPR * W4 / kPT;
+  static_assert(kPR * W4 == N4 * kPT, "stage 4 gives every thread the same number of pairs");
+  df64 bnr[N4][2];
+  if constexpr (KIND == kRhsResidual) {
+#pragma unroll
+    for (int e = 0; e < N4; ++e) {
+      const int k = tid + e * kPT, r = k / W4, c = 2 * (k - r * W4);
+      const int gj = j0 + r, gi = x0 + c;
+      bnr[e][0] = bnr[e][1] = df_make(1.0f, 0.0f);
+      if (gj < ny && gi < nx) {
+        const size_t idx = (size_t)gj * nx + gi;
+        bnr[e][0] = bn[idx];
+        if (gi + 1 < nx) bnr[e][1] = bn[idx + 1];
+      }
+    }
+  }
+  // ---- stage 1: film tile (two-cell halo, wall-reflected) as double-float
+  // planes, and the range of its leading floats
+  __shared__ unsigned s_lo, s_hi;
+  if (tid == 0) {
+    s_lo = 0xffffffffu;
+    s_hi = 0u;
+  }
+  __syncthreads();
+  {
+    constexpr int W2 = (kPC + 8) / 2;
+    const bool inner_x = x0 - 4 >= 0 && x0 + kPC + 4 <= nx && (nx & 1) == 0 &&
+                         (reinterpret_cast<uintptr_t>(u) & 15) == 0;
+    // all of a thread's loads are issued before the first conversion
+    constexpr int NP = (kPR + 4) * W2, N1 = (NP + kPT - 1) / kPT;
+    double2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const int k = min(tid + i * kPT, NP - 1);
+      const int r = k / W2, c = 2 * (k - r * W2);
+      const int gj = reflect_index(j0 - 2 + r, ny);
+      if (inner_x) {
+        v[i] = __ldg(reinterpret_cast<const double2*>(u + (size_t)gj * nx + (x0 - 4 + c)));
+      } else {
+        v[i].x = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 4 + c, nx));
+        v[i].y = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 3 + c, nx));
+      }
+    }
+    // positive floats order as their bit patterns; anything else (zero,
+    // negative, NaN) makes the range fail the fast-path test below
+    unsigned lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const int k = tid + i * kPT;
+      if (k >= NP) break;
+      const int r = k / W2, c = 2 * (k - r * W2);
+      const df64 da = df_of_pos_f64_fast(v[i].x), db = df_of_pos_f64_fast(v[i].y);
+      *reinterpret_cast<float2*>(&S.uh[r][c]) = make_float2(da.hi, db.hi);
+      *reinterpret_cast<float2*>(&S.ul[r][c]) = make_float2(da.lo, db.lo);
+      const unsigned ba = __float_as_uint(da.hi), bb = __float_as_uint(db.hi);
+      lo = min(lo, min(ba, bb));
+      hi = max(hi, max(ba, bb));
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((tid & 31) == 0) {
+      atomicMin(&s_lo, lo);
+      atomicMax(&s_hi, hi);
+    }
+  }
+  __syncthreads();
+  // the fast path needs every leading float positive, finite and within 25%
+  // of the smallest
+  const float fmn = __uint_as_float(s_lo), fmx = __uint_as_float(s_hi);
+  const bool fast = s_lo > 0u && s_hi < 0x7f800000u && fmx <= 1.25f * fmn;
+  float g;
+  if (fast)
+    g = rhs_stages<KIND, true>(S, RK, x0, j0, nx, ny, bn, rhs, ulp, bnr);
+  else
+    g = rhs_stages<KIND, false>(S, RK, x0, j0, nx, ny, bn, rhs, ulp, bnr);
   if constexpr (KIND == kRhsExplicit) return;
   for (int o = 16; o > 0; o >>= 1) {
     const float g2 = __shfl_xor_sync(0xffffffffu, g, o);

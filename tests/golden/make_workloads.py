@@ -30,11 +30,12 @@ model's own lambda_m and sigma_max, the flat heights of Sec. Validation:
 with dt0 * sigma_max and dt_max * sigma_max equal to scale8k's.
 
 ensemble  256 independent films (the many-film statistics runs of Sec.
-          Results): 64 each of N = 128, 256,
-          512, 1024, contact angle uniform in [10, 40] deg (numpy
-          default_rng(1240)), power law, h0 = 1, eps = 0.01, each on
-          16 lambda_m of its own (so N/16 cells per wavelength), dt0 =
-          1e-7/sigma_max, dt_max = 0.01/sigma_max, 500 attempts per film.
+          Results): per film (numpy default_rng(1240), in this order)
+          N uniform in {128, 256, 512, 1024} and the contact angle
+          uniform in [10, 40] deg; power law, h0 = 1, eps = 0.01, 32
+          cells per lambda_m of the film's own contact angle (so N/32
+          wavelengths per side), dt0 = 1e-7/sigma_max, dt_max =
+          0.01/sigma_max, 500 attempts per film.
 
 spectrum8k  the radial Fourier analysis (App. Radial Fourier Transform) of
           an 8192^2 film at scale8k's spacing (lambda_m / 128): a ring film
@@ -85,14 +86,15 @@ def main():
     import numpy as np
     rng = np.random.default_rng(1240)
     films = []
-    for i, N in enumerate([128, 256, 512, 1024] * 64):
+    for i in range(256):
+        N = int(rng.choice([128, 256, 512, 1024]))
         thc = float(rng.uniform(10.0, 40.0))
         kv = O.kappa_from_contact_angle(math.radians(thc), b, n, m)
         qv, sv = O.lsa(O.Model(nx=1, ny=1, ds=1.0, kappa=kv, b=b, n=n, m=m), 1.0)
         lv = 2.0 * math.pi / qv
         films.append(dict(N=N, theta_c_deg=thc, kappa=kv, lambda_m=lv, sigma_max=sv,
-                          ds=16.0 * lv / N, seed=2000 + i, dt0=1e-7 / sv, dt_max=0.01 / sv))
-    W["ensemble"] = dict(common, P=16, eps=0.01, attempts=500, films=films)
+                          ds=lv / 32.0, P=N / 32.0, seed=2000 + i, dt0=1e-7 / sv, dt_max=0.01 / sv))
+    W["ensemble"] = dict(common, cells_per_lambda=32, eps=0.01, attempts=500, films=films)
     W["spectrum8k"] = dict(common, N=8192, P=64, ds=64 * lam / 8192, seed=1241, eps=0.05,
                            spread=0.05, modes=256, noise=0.002, q_cut=5.0 * qm, sigma=1.0,
                            points_per_interval=10, n_eval=400, steps=50)

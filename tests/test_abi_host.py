@@ -45,6 +45,7 @@ int main(void) {
   O(tf_params, ds); O(tf_params, kappa); O(tf_params, theta); O(tf_params, newton_fixed_iter);
   O(tf_params, grow_after); O(tf_params, rupture_h); O(tf_params, precision);
   O(tf_params, nlc_K); O(tf_params, nlc_w); O(tf_params, pol_C); O(tf_params, pol_d);
+  O(tf_params, line_solver);
   O(tf_step_record, accepted); O(tf_step_record, hmin); O(tf_advance_info, dt);
   printf("tf_spectrum_params %zu\ntf_spectrum_info %zu\ntf_spectrum_out %zu\n",
          sizeof(tf_spectrum_params), sizeof(tf_spectrum_info), sizeof(tf_spectrum_out));
@@ -87,13 +88,19 @@ def test_params_default():
     assert p.model == tf.TF_MODEL_POWERLAW and p.n == 3 and p.m == 2 and p.b == 0.1
     assert p.theta == 0.5 and p.newton_tol == 1e-10 and p.newton_max_iter == 10
     assert p.precision == tf.TF_FP64 and p.nx == 0
+    assert p.line_solver == tf.TF_SOLVER_TWISTED
 
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-3), dict(ds=0.0), dict(theta=1.5),
                                  dict(newton_max_iter=0), dict(precision=7), dict(model=9),
                                  dict(n=2, m=2), dict(b=-1.0), dict(dt_shrink=1.0),
                                  dict(nx=70000, ny=70000), dict(nx=65537, ny=1), dict(nx=1, ny=65537),
-                                 dict(nx=65536, ny=32768), dict(nx=46341, ny=46341)])
+                                 dict(nx=65536, ny=32768), dict(nx=46341, ny=46341),
+                                 dict(line_solver=3), dict(line_solver=-1),
+                                 # the partitioned solver: FP32-bulk with the (3, 2) power law only
+                                 dict(line_solver=1),
+                                 dict(line_solver=1, precision=1, n=4),
+                                 dict(line_solver=1, precision=1, model=1)])
 def test_init_rejects_bad_parameters(bad):
     p = tf.tf_params_default(nx=16, ny=16, ds=1.0)
     for k, v in bad.items():

@@ -1,7 +1,8 @@
 """Ensembles of independent films (tf_ensemble_advance): every film must
 come out exactly as tf_advance leaves it -- the same attempts, decisions,
 iteration counts and bit-identical grids -- and, through that, match the
-oracle."""
+oracle.  Films of one ensemble may use different line solvers (the tuner
+picks one per grid shape); each solver's films match the oracle."""
 import math
 
 import numpy as np
@@ -44,19 +45,22 @@ FILMS = [
 ]
 
 
-def film_params(nx, ny, th, mode):
+def film_params(nx, ny, th, mode, solver=tf.TF_SOLVER_TWISTED):
     kappa = O.kappa_from_contact_angle(math.radians(th), 0.1, 3, 2)
     qm, sm = O.lsa(O.Model(nx=1, ny=1, ds=1.0, kappa=kappa), 1.0)
     ds = 2 * math.pi / qm / 8
-    p = tf.tf_params_default(nx=nx, ny=ny, ds=ds, contact_angle=math.radians(th), precision=mode)
+    p = tf.tf_params_default(nx=nx, ny=ny, ds=ds, contact_angle=math.radians(th), precision=mode,
+                             line_solver=solver)
     return p, sm, kappa, ds
 
 
-@pytest.mark.parametrize("mode", [tf.TF_FP64, tf.TF_FP32_BULK])
-def test_ensemble_matches_per_film_advance(torch, mode):
+@pytest.mark.parametrize("mode,mixed", [(tf.TF_FP64, False), (tf.TF_FP32_BULK, False), (tf.TF_FP32_BULK, True)])
+def test_ensemble_matches_per_film_advance(torch, mode, mixed):
     ctxs, grids, h0s, t_end, dt0, att, params = [], [], [], [], [], [], []
-    for nx, ny, th, seed, fdt, fend, na in FILMS:
-        p, sm, _, _ = film_params(nx, ny, th, mode)
+    for i, (nx, ny, th, seed, fdt, fend, na) in enumerate(FILMS):
+        # mixed: every other film on the partitioned solver
+        solver = tf.TF_SOLVER_PARTITIONED if mixed and i % 2 else tf.TF_SOLVER_TWISTED
+        p, sm, _, _ = film_params(nx, ny, th, mode, solver)
         h = S.spinodal_film(nx, ny, 1.0, 0.01, seed=seed)
         ctxs.append(tf.Context(p, stream=torch.cuda.Stream()))
         grids.append(dev(torch, h))
@@ -107,3 +111,47 @@ def test_ensemble_rejects_shared_context(torch):
     g2 = dev(torch, S.spinodal_film(16, 16, 1.0, 0.01, seed=2))
     with pytest.raises(RuntimeError):
         tf.tf_ensemble_advance([ctx, ctx], [g1, g2], 0.0, 1e30, 1e-3 / sm, 3)
+
+
+@pytest.mark.parametrize("solver", [tf.TF_SOLVER_TWISTED, tf.TF_SOLVER_PARTITIONED])
+def test_fp32_bulk_solvers_match_oracle_replay(torch, solver):
+    """An FP32-bulk film of 150 x 70 cells (three x segments and three y
+    segments of the partitioned solver) replaying the oracle's accepted
+    steps ends within Newton-tolerance level of the FP64 oracle, with
+    either line solver."""
+    nx, ny, th, seed = 150, 70, 25.0, 8
+    p, sm, kappa, ds = film_params(nx, ny, th, tf.TF_FP32_BULK, solver)
+    h = S.spinodal_film(nx, ny, 1.0, 0.01, seed=seed)
+    om = O.Model(nx=nx, ny=ny, ds=ds, kappa=kappa)
+    ref = O.advance(om, O.Control(), h, 0.0, 1e30, 1e-3 / sm, 12)
+    acc = ref.accepted()
+    assert len(acc) >= 8
+    ctx = tf.Context(p)
+    assert ctx.line_solver == solver
+    g = dev(torch, h)
+    info, _ = tf.tf_advance(ctx, g, 0.0, 1e30, 1.0, len(acc), dt_replay=[r["dt"] for r in acc],
+                            records=False)
+    assert info["accepted"] == len(acc)
+    assert np.max(np.abs(host(g) - ref.h)) <= 1e-9
+
+
+def test_tuner_picks_a_solver_per_shape_and_auto_contexts_follow_it(torch):
+    picks = {}
+    for n in (64, 256):
+        p, sm, _, _ = film_params(n, n, 20.0, tf.TF_FP32_BULK, tf.TF_SOLVER_AUTO)
+        assert tf.tf_tuned_line_solver(p) in (-1, tf.TF_SOLVER_TWISTED, tf.TF_SOLVER_PARTITIONED)
+        h = dev(torch, S.spinodal_film(n, n, 1.0, 0.01, seed=n))
+        h_before = h.clone()
+        r = tf.tf_tune_line_solver(p, h, 1e-3 / sm, iters=2)
+        assert torch.equal(h, h_before)  # the film is only read
+        assert r["best"] in (tf.TF_SOLVER_TWISTED, tf.TF_SOLVER_PARTITIONED)
+        assert r["ms"][0] > 0.0 and r["ms"][1] > 0.0
+        assert r["best"] == (tf.TF_SOLVER_PARTITIONED if r["ms"][1] < r["ms"][0] else tf.TF_SOLVER_TWISTED)
+        assert tf.tf_tuned_line_solver(p) == r["best"]
+        assert tf.Context(p).line_solver == r["best"]
+        picks[n] = r["best"]
+    # FP64 has one solver: the tuner reports the other as not applicable
+    p, sm, _, _ = film_params(32, 32, 20.0, tf.TF_FP64, tf.TF_SOLVER_AUTO)
+    r = tf.tf_tune_line_solver(p, dev(torch, S.spinodal_film(32, 32, 1.0, 0.01, seed=1)), 1e-3 / sm, iters=1)
+    assert r["best"] == tf.TF_SOLVER_TWISTED and r["ms"][1] == -1.0
+    assert tf.Context(p).line_solver == tf.TF_SOLVER_TWISTED

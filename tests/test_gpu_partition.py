@@ -1,5 +1,5 @@
-"""Parity of the partitioned line solves (FP32-bulk, (3, 2) power law) at the
-edges of their segment geometry.
+"""Parity of the partitioned line solver (TF_SOLVER_PARTITIONED: FP32-bulk,
+(3, 2) power law) at the edges of its segment geometry.
 
 x lines are cut into segments of 64 cells and y lines into segments of 32,
 with two-cell separators between segments; a last segment that would hold
@@ -39,7 +39,8 @@ def torch():
 def test_partitioned_iteration_matches_oracle(torch, nx, ny, dt):
     ds = 1.9
     om = O.Model(nx=nx, ny=ny, ds=ds, kappa=KAPPA)
-    p = tf.tf_params_default(nx=nx, ny=ny, ds=ds, kappa=KAPPA, precision=tf.TF_FP32_BULK)
+    p = tf.tf_params_default(nx=nx, ny=ny, ds=ds, kappa=KAPPA, precision=tf.TF_FP32_BULK,
+                             line_solver=tf.TF_SOLVER_PARTITIONED)
     h_old = S.spinodal_film(nx, ny, 1.0, 0.05, seed=11 * nx + ny)
     ctx = tf.Context(p)
     w, v, hn = (torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3))
@@ -68,7 +69,8 @@ def test_partitioned_step_converges_to_oracle_step(torch, nx, ny):
     path of the iteration, not its FP64-class fixed point."""
     ds, dt = 3.9, 2.0
     om = O.Model(nx=nx, ny=ny, ds=ds, kappa=KAPPA)
-    p = tf.tf_params_default(nx=nx, ny=ny, ds=ds, kappa=KAPPA, precision=tf.TF_FP32_BULK)
+    p = tf.tf_params_default(nx=nx, ny=ny, ds=ds, kappa=KAPPA, precision=tf.TF_FP32_BULK,
+                             line_solver=tf.TF_SOLVER_PARTITIONED)
     h0 = S.spinodal_film(nx, ny, 1.0, 0.01, seed=nx + ny)
     ref, ri = O.step(om, O.Control(), h0, dt)
     assert ri["status"] == 0
