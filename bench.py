@@ -470,14 +470,21 @@ def run_ensemble(args, w):
             for f in films]
     grids = [torch.empty_like(h) for h in init]
     dt0 = [f["dt0"] for f in films]
-    # the line-solver tuner: once per film size, on that size's first film
+    # the line-solver tuner: once per film size, on that size's first film,
+    # with as many copies running at once as the ensemble has films of that
+    # size (at most 32): the throughput the films will see
     tuned = {}
+    count = {}
+    for f in films:
+        count[f["N"]] = count.get(f["N"], 0) + 1
     for f, h in zip(films, init):
         if f["N"] not in tuned:
-            r = tf.tf_tune_line_solver(ensemble_params(tf, w, f, mode, tf.TF_SOLVER_AUTO), h, f["dt0"], iters=5)
+            r = tf.tf_tune_line_solver(ensemble_params(tf, w, f, mode, tf.TF_SOLVER_AUTO), h, f["dt0"], iters=5,
+                                       copies=min(32, count[f["N"]]))
             tuned[f["N"]] = dict(solver=("partitioned" if r["best"] == tf.TF_SOLVER_PARTITIONED else "twisted"),
-                                 ms_per_iteration=dict(twisted=round(r["ms"][0], 4),
-                                                       partitioned=round(r["ms"][1], 4)))
+                                 copies=min(32, count[f["N"]]),
+                                 ms_per_film_iteration=dict(twisted=round(r["ms"][0], 5),
+                                                            partitioned=round(r["ms"][1], 5)))
 
     def contexts(solver):
         return [tf.Context(ensemble_params(tf, w, f, mode, solver), stream=torch.cuda.Stream()) for f in films]

@@ -250,21 +250,25 @@ int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const doubl
 /* ---- line-solver tuning ---------------------------------------------------
  * The paper has no counterpart to this: it picks, per grid shape, the
  * faster of the line solvers for the many-film runs of Sec. Results, whose
- * films range from 128^2 (too few lines to fill the GPU with two threads
- * per line) to 1024^2.  tf_tune_line_solver times `iters` (>= 1) Newton
- * iterations from the device film h (of p's shape; not modified) at step
- * dt with each solver that applies to *p (after one untimed iteration
- * each), on the given stream, and keeps the faster in a table of this
- * process keyed by (nx, ny, precision, model, n, m).  *best receives the
- * chosen solver; ms (host, 2 entries, or NULL) the milliseconds per
- * iteration of TF_SOLVER_TWISTED and TF_SOLVER_PARTITIONED (-1 where a
- * solver does not apply).  A later call for the same key replaces the
- * entry.  Contexts created with line_solver = TF_SOLVER_AUTO read the
- * table once, in tf_init, so a context never changes solver.  Allocates
- * two temporary contexts; synchronises the stream.  Returns TF_OK,
- * TF_ERR_ARG or a context's error.                                        */
+ * films range from 128^2 to 1024^2.  tf_tune_line_solver runs `copies`
+ * (1..256) films of p's shape at once, each in a context and on a stream of
+ * its own and each iterating from the device film h (not modified) at step
+ * dt: one untimed round, then `iters` (>= 1) timed rounds of one Newton
+ * iteration on every film followed by a wait for all of them; this for
+ * each solver that applies to *p.  The faster (in film iterations per
+ * second) goes into a table of this process keyed by (nx, ny, precision,
+ * model, n, m).  With copies = 1 it measures a film alone; with many it
+ * measures the throughput a solver gives when films share the GPU, which
+ * can rank the solvers the other way.  *best receives the chosen solver;
+ * ms (host, 2 entries, or NULL) the milliseconds per film iteration of
+ * TF_SOLVER_TWISTED and TF_SOLVER_PARTITIONED (-1 where a solver does not
+ * apply).  A later call for the same key replaces the entry.  Contexts
+ * created with line_solver = TF_SOLVER_AUTO read the table once, in
+ * tf_init, so a context never changes solver.  Allocates `copies`
+ * temporary contexts and streams per solver; synchronises the device.
+ * Returns TF_OK, TF_ERR_ARG or a context's error.                        */
 int tf_tune_line_solver(const tf_params* p, void* stream, const double* h, double dt, int iters,
-                        int* best, double* ms);
+                        int copies, int* best, double* ms);
 /* The table's entry for *p's key (TF_SOLVER_*), or -1 if there is none.   */
 int tf_tuned_line_solver(const tf_params* p);
 /* The solver a context uses (TF_SOLVER_TWISTED or TF_SOLVER_PARTITIONED),

@@ -140,8 +140,8 @@ def library(build_if_missing: bool = True):
     L.tf_ensemble_advance.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(dp),
                                       C.POINTER(dp), C.POINTER(dp), C.POINTER(C.c_int),
                                       C.POINTER(TfAdvanceInfo), C.POINTER(C.c_int)]
-    L.tf_tune_line_solver.argtypes = [C.POINTER(TfParams), vp, vp, dp, C.c_int, C.POINTER(C.c_int),
-                                      C.POINTER(dp)]
+    L.tf_tune_line_solver.argtypes = [C.POINTER(TfParams), vp, vp, dp, C.c_int, C.c_int,
+                                      C.POINTER(C.c_int), C.POINTER(dp)]
     L.tf_tuned_line_solver.argtypes = [C.POINTER(TfParams)]
     L.tf_tuned_line_solver.restype = C.c_int
     L.tf_line_solver.argtypes = [vp]
@@ -325,11 +325,13 @@ def tf_advance(ctx: Context, h, t0: float, t_end: float, dt0: float, max_attempt
                 streak=st.value), out
 
 
-def tf_tune_line_solver(params: TfParams, h, dt: float, iters: int = 3, stream=None) -> dict:
-    """Time the line solvers that apply to ``params`` on the CUDA film ``h``
-    and keep the faster for contexts created with ``TF_SOLVER_AUTO``;
-    returns dict(best=solver, ms=[twisted, partitioned]) (ms per Newton
-    iteration, -1 where a solver does not apply)."""
+def tf_tune_line_solver(params: TfParams, h, dt: float, iters: int = 3, copies: int = 1,
+                        stream=None) -> dict:
+    """Time the line solvers that apply to ``params`` on ``copies`` films
+    iterating at once from the CUDA film ``h`` and keep the faster for
+    contexts created with ``TF_SOLVER_AUTO``; returns dict(best=solver,
+    ms=[twisted, partitioned]) (ms per film iteration, -1 where a solver
+    does not apply)."""
     torch = _torch()
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -339,7 +341,7 @@ def tf_tune_line_solver(params: TfParams, h, dt: float, iters: int = 3, stream=N
     ms = (C.c_double * 2)()
     _check(library().tf_tune_line_solver(C.byref(params), C.c_void_p(stream.cuda_stream),
                                          C.c_void_p(h.contiguous().data_ptr()), float(dt), int(iters),
-                                         C.byref(best), ms), "tf_tune_line_solver")
+                                         int(copies), C.byref(best), ms), "tf_tune_line_solver")
     return dict(best=best.value, ms=[ms[0], ms[1]])
 
 

@@ -509,15 +509,24 @@ int tf_init(const tf_params* p, void* stream, tf_ctx** out) {
   c->grid_y = (p->nx + 31) / 32;
   c->grid_rx = (p->nx + 31) / 32;
   c->grid_ry = (p->ny + 31) / 32;
-  c->grid_pkx = (p->nx + 63) / 64;
-  c->grid_pky = (p->ny + 31) / 32;
+  {
+    // residual strips: segments of 64 rows, halved (down to 16) until the
+    // grid holds two waves of warps (about 24 resident per SM)
+    const long strips = (p->nx + tf::kRhsStripCols - 1) / tf::kRhsStripCols;
+    int rows = 64;
+    while (rows > 16 && strips * ((p->ny + rows - 1) / rows) < 2L * 152 * 24) rows /= 2;
+    const long warps = strips * ((p->ny + rows - 1) / rows);
+    c->strip_n = (int)strips;
+    c->strip_rows = rows;
+    c->grid_pkx = (int)((warps + tf::kRhsStripWarps - 1) / tf::kRhsStripWarps);
+  }
   c->packed_rhs = p->precision != TF_FP64 && p->model == TF_MODEL_POWERLAW && p->n == 3 && p->m == 2;
-  c->n_rhs_parts = c->packed_rhs ? c->grid_pkx * c->grid_pky : c->grid_rx * c->grid_ry;
+  c->n_rhs_parts = c->packed_rhs ? c->grid_pkx : c->grid_rx * c->grid_ry;
   c->grid_st_x = (p->nx + 15) / 16;
   c->grid_st_y = (p->ny + 15) / 16;
   c->grid_stats = 1216;  // 8 blocks of 256 threads per SM on 152 SMs
   {
-    int a = c->grid_rx * c->grid_ry + c->grid_x, b = c->grid_st_x * c->grid_st_y;
+    int a = c->n_rhs_parts + c->grid_x, b = c->grid_st_x * c->grid_st_y;
     c->n_px = a > b ? a : b;
   }
   c->n_py = c->grid_y > c->grid_stats ? c->grid_y : c->grid_stats;
@@ -788,37 +797,57 @@ int tf_tuned_line_solver(const tf_params* p) {
   return -1;
 }
 
-int tf_tune_line_solver(const tf_params* p, void* stream, const double* h, double dt, int iters, int* best,
-                        double* ms) {
-  if (!p || !h || !best || iters < 1 || !(dt > 0.0) || !isfinite(dt)) return TF_ERR_ARG;
+int tf_tune_line_solver(const tf_params* p, void* stream, const double* h, double dt, int iters, int copies,
+                        int* best, double* ms) {
+  if (!p || !h || !best || iters < 1 || copies < 1 || copies > 256 || !(dt > 0.0) || !isfinite(dt))
+    return TF_ERR_ARG;
   double t[2] = {-1.0, -1.0};
-  for (int s = TF_SOLVER_TWISTED; s <= TF_SOLVER_PARTITIONED; ++s) {
+  cudaStream_t s0 = (cudaStream_t)stream;
+  for (int sv = TF_SOLVER_TWISTED; sv <= TF_SOLVER_PARTITIONED; ++sv) {
     tf_params q = *p;
-    q.line_solver = s;
-    tf_ctx* c = nullptr;
-    const int r = tf_init(&q, stream, &c);
-    if (r == TF_ERR_ARG && s == TF_SOLVER_PARTITIONED) continue;  // not applicable
-    if (r) return r;
-    // one untimed iteration, then `iters` timed ones, each from h (the same
-    // work every time), with the host round trip of a real iteration
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    q.line_solver = sv;
+    // `copies` films on streams of their own, each iterating from h (read
+    // only): the throughput a solver gives when many films share the GPU
+    std::vector<tf_ctx*> ctx((size_t)copies, nullptr);
+    std::vector<cudaStream_t> st((size_t)copies, nullptr);
     int rc = TF_OK;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = TF_ERR_CUDA;
-    if (!rc && c->ops->explicit_part(*c, h, dt) != cudaSuccess) rc = TF_ERR_CUDA;
-    Scalars sc;
-    for (int k = 0; k <= iters && !rc; ++k) {
-      if (k == 1 && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = TF_ERR_CUDA;
-      if (!rc) rc = iterate(*c, h, dt, c->ubuf2, nullptr, nullptr, &sc);
+    for (int k = 0; k < copies && !rc; ++k) {
+      if (cudaStreamCreateWithFlags(&st[(size_t)k], cudaStreamNonBlocking) != cudaSuccess) {
+        rc = TF_ERR_CUDA;
+        break;
+      }
+      rc = tf_init(&q, st[(size_t)k], &ctx[(size_t)k]);
     }
-    if (!rc && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = TF_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(s0) != cudaSuccess) rc = TF_ERR_CUDA;  // h is ready
+    for (int k = 0; k < copies && !rc; ++k)
+      if (ctx[(size_t)k]->ops->explicit_part(*ctx[(size_t)k], h, dt) != cudaSuccess) rc = TF_ERR_CUDA;
+    // one untimed round, then `iters` timed rounds; each round queues one
+    // Newton iteration on every film, then waits for all of them (a
+    // round's host round trip is part of an iteration's cost)
+    for (int it = 0; it <= iters && !rc; ++it) {
+      if (it == 1) {
+        if (cudaDeviceSynchronize() != cudaSuccess || cudaEventRecord(e0, s0) != cudaSuccess) rc = TF_ERR_CUDA;
+      }
+      for (int k = 0; k < copies && !rc; ++k)
+        rc = iterate_launch(*ctx[(size_t)k], h, dt, ctx[(size_t)k]->ubuf2, nullptr, nullptr);
+      for (int k = 0; k < copies && !rc; ++k)
+        if (cudaStreamSynchronize(st[(size_t)k]) != cudaSuccess) rc = TF_ERR_CUDA;
+    }
+    if (!rc && (cudaEventRecord(e1, s0) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
       rc = TF_ERR_CUDA;
     float el = 0.0f;
     if (!rc && cudaEventElapsedTime(&el, e0, e1) != cudaSuccess) rc = TF_ERR_CUDA;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    tf_destroy(c);
+    for (int k = 0; k < copies; ++k) {
+      tf_destroy(ctx[(size_t)k]);
+      if (st[(size_t)k]) cudaStreamDestroy(st[(size_t)k]);
+    }
+    if (rc == TF_ERR_ARG && sv == TF_SOLVER_PARTITIONED) continue;  // not applicable
     if (rc) return rc;
-    t[s] = (double)el / iters;
+    t[sv] = (double)el / iters / copies;  // ms per film iteration
   }
   const int choice = (t[1] >= 0.0 && t[1] < t[0]) ? TF_SOLVER_PARTITIONED : TF_SOLVER_TWISTED;
   {

@@ -10,6 +10,9 @@
 
 namespace tf {
 
+// strips of the packed FP32-bulk residual kernel (k_rhs_strip, tf_rhs_packed.cuh):
+// output columns per warp and warps per block
+constexpr int kRhsStripCols = 60, kRhsStripWarps = 4;
 
 }  // namespace tf
 
@@ -82,7 +85,8 @@ struct tf_ctx {
   int grid_x;      // blocks of the x sweep (32 rows each)
   int grid_y;      // blocks of the y sweep (32 columns each)
   int grid_rx, grid_ry;      // 2-D residual grid (32 x 32 tiles)
-  int grid_pkx, grid_pky;    // packed FP32-bulk residual grid (64 x 32 tiles)
+  int grid_pkx;              // packed FP32-bulk residual: blocks of kRhsStripWarps strip segments
+  int strip_n, strip_rows;   // its strips across x and rows per segment
   bool packed_rhs;           // FP32-bulk with the (3, 2) power law: packed residual kernel
   int n_rhs_parts;           // partial results written by the residual kernel in use
   int grid_st_x, grid_st_y;  // 2-D stencil grid (16 x 16 tiles)

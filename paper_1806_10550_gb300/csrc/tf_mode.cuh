@@ -7,6 +7,8 @@
 #include "tf_internal.h"
 #include "tf_rhs_packed.cuh"
 
+static_assert(tf::kRhsStripCols == tf::kSW && tf::kRhsStripWarps == tf::kSWarps, "residual strips of the launch grid");
+
 namespace tf {
 
 template <class Mode> struct Launch {
@@ -43,14 +45,6 @@ template <class Mode> struct Launch {
     if ((e = cudaFuncSetAttribute(k_rhs<Mode, kRhsBoth>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if constexpr (kF32B) {
       if ((e = part::prepare())) return e;
-      const int sp = (int)sizeof(RhsPackedSmem);
-      const int maxc = (int)cudaSharedmemCarveoutMaxShared;
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsResidual>, A, sp))) return e;
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsExplicit>, A, sp))) return e;
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsBoth>, A, sp))) return e;
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsResidual>, C, maxc))) return e;
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsExplicit>, C, maxc))) return e;
-      if ((e = cudaFuncSetAttribute(k_rhs_packed<kRhsBoth>, C, maxc))) return e;
     }
     return cudaFuncSetAttribute(k_rhs<Mode, kRhsResidual>, C, (int)cudaSharedmemCarveoutMaxShared);
   }
@@ -59,8 +53,8 @@ template <class Mode> struct Launch {
     c.expl_kernels = 1;
     if constexpr (kF32B) {
       if (c.packed_rhs) {
-        k_rhs_packed<kRhsExplicit><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
-            c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, nullptr, nullptr, nullptr);
+        k_rhs_strip<kRhsExplicit><<<c.grid_pkx, kST, 0, c.stream>>>(
+            c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, nullptr, nullptr, nullptr, c.strip_n, c.strip_rows);
         return cudaGetLastError();
       }
     }
@@ -78,8 +72,8 @@ template <class Mode> struct Launch {
   static cudaError_t rhs_c(tf_ctx& c, const double* u_k, double dt) {
     if constexpr (kF32B) {
       if (c.packed_rhs) {
-        k_rhs_packed<kRhsResidual><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
-            c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px);
+        k_rhs_strip<kRhsResidual><<<c.grid_pkx, kST, 0, c.stream>>>(
+            c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px, c.strip_n, c.strip_rows);
         return cudaGetLastError();
       }
     }
@@ -95,8 +89,8 @@ template <class Mode> struct Launch {
     c.expl_kernels = 1;
     if constexpr (kF32B) {
       if (c.packed_rhs) {
-        k_rhs_packed<kRhsBoth><<<dim3(c.grid_pkx, c.grid_pky), kPT, sizeof(RhsPackedSmem), c.stream>>>(
-            c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px);
+        k_rhs_strip<kRhsBoth><<<c.grid_pkx, kST, 0, c.stream>>>(
+            c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px, c.strip_n, c.strip_rows);
         return cudaGetLastError();
       }
     }

@@ -53,7 +53,11 @@ __device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, p_neg(b)); }
+// a - b as fma(b, -1, a): the same IEEE result as a + (-b) (the product
+// b * -1 is exact), in one paired instruction with no separate negation of
+// b.  (A PTX sub.rn.f32x2 was contracted with a preceding paired multiply,
+// which breaks the error-free transformations built on it.)
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 __device__ __forceinline__ float2 p_splat(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 p_rcp(float2 a) { return make_float2(rcp(a.x), rcp(a.y)); }
 

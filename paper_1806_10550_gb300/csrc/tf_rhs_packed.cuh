@@ -3,26 +3,28 @@
 // The residual G = u_k + theta dt D(u_k) - b^n of eq. CrankNicolson in
 // double-float, with D the flux-form operator of Sec. Flux Discretization,
 // or the explicit part b^n = u^n - (1 - theta) dt D(u^n) (the computation of
-// k_rhs<ModeF32B>, tf_sweeps.cuh, with fewer FP32 operations).  Each thread
+// k_rhs<ModeF32B>, tf_sweeps.cuh, with fewer FP32 operations).  Each lane
 // carries two horizontally adjacent cells through every double-float
 // operation, one lane each of the sm_100+ paired FP32 instructions
-// (add/mul/fma on float2).  Shared memory holds the high and low parts in
-// separate planes, so a pair of cells is one 8-byte load.  Used for the
-// (n, m) = (3, 2) power law; other models take the scalar kernel.
+// (add/mul/fma on float2).  Used for the (n, m) = (3, 2) power law; other
+// models take the scalar kernel.
 //
 // Where the operations are saved:
-//   * differences of neighbouring heights.  On a tile whose heights (halo
-//     included) all lie within 25% of each other, the difference of two
-//     leading floats is exact (Sterbenz) and so are the sums of up to four
-//     of them (they stay below the smallest height's binade), so a height
-//     difference is (hi - hi', lo - lo') and the Laplacian's leading part a
-//     plain sum; the trailing parts round at 2^-24 of values that are
-//     themselves 2^-24 of the heights.  Other tiles take the general
-//     double-float operations (TwoSum throughout), chosen per block.
+//   * differences of neighbouring heights.  Where the heights a row step
+//     reads (three rows of a strip, halo included) all lie within 25% of
+//     each other, the difference of two leading floats is exact (Sterbenz)
+//     and so are the sums of up to four of them (they stay below the
+//     smallest height's binade), so a height difference is (hi - hi',
+//     lo - lo') and the Laplacian's leading part a plain sum; the trailing
+//     parts round at 2^-24 of values that are themselves 2^-24 of the
+//     heights.  Other row steps take the general double-float operations
+//     (TwoSum throughout).
 //   * 1/h: the MUFU reciprocal y of the leading float refined by one Newton
 //     step in double-float arithmetic, 1/h = y + y (1 - h y), which carries
 //     the square of the reciprocal's 2^-23 error.
 //   * face fluxes and the divergence stay unnormalised until G is formed.
+//   * no shared-memory staging of the film or of intermediate values: a
+//     warp keeps its rows in registers and trades neighbours by shuffles.
 #pragma once
 
 #include "tf_partition.cuh"
@@ -61,10 +63,19 @@ __device__ __forceinline__ df2 d2_add_u(df2 a, df2 b) {
   p_two_sum(a.hi, b.hi, s, e);
   return d2(s, p_add(e, p_add(a.lo, b.lo)));
 }
-__device__ __forceinline__ df2 d2_sub_u(df2 a, df2 b) { return d2_add_u(a, d2_neg(b)); }
+// a - b: the TwoSum of (a.hi, -b.hi) written with subtractions, so that no
+// operand is negated on its own ((-b) - bb = -(b + bb) exactly)
+__device__ __forceinline__ df2 d2_sub_u(df2 a, df2 b) {
+  const float2 s = p_sub(a.hi, b.hi);
+  const float2 bb = p_sub(s, a.hi);
+  const float2 e = p_sub(p_sub(a.hi, p_sub(s, bb)), p_add(b.hi, bb));
+  return d2(s, p_add(e, p_sub(a.lo, b.lo)));
+}
+// -p exactly (0 - p), for the product error fma(a, b, -p)
+__device__ __forceinline__ float2 p_negz(float2 p) { return p_sub(make_float2(0.0f, 0.0f), p); }
 __device__ __forceinline__ df2 d2_mul_u(df2 a, df2 b) {
   const float2 p = p_mul(a.hi, b.hi);
-  float2 e = p_fma(a.hi, b.hi, p_neg(p));
+  float2 e = p_fma(a.hi, b.hi, p_negz(p));
   e = p_fma(a.hi, b.lo, e);
   e = p_fma(a.lo, b.hi, e);
   return d2(p, e);
@@ -85,7 +96,7 @@ __device__ __forceinline__ df2 d2_add(df2 a, df2 b) {
 __device__ __forceinline__ df2 d2_sub(df2 a, df2 b) { return d2_add(a, d2_neg(b)); }
 __device__ __forceinline__ df2 d2_mul(df2 a, df2 b) {
   float2 p = p_mul(a.hi, b.hi);
-  float2 e = p_fma(a.hi, b.hi, p_neg(p));
+  float2 e = p_fma(a.hi, b.hi, p_negz(p));
   e = p_fma(a.hi, b.lo, e);
   e = p_fma(a.lo, b.hi, e);
   p_fast_two_sum(p, e, p, e);
@@ -100,35 +111,7 @@ __device__ __forceinline__ df2 d2_rcp(df2 a) {
 }
 
 // ---------------------------------------------------------------------------
-// the kernel
-
-constexpr int kPR = 32;   // tile rows
-constexpr int kPC = 64;   // tile columns
-constexpr int kPT = 512;  // threads
-
-struct RhsPackedSmem {
-  float uh[kPR + 4][kPC + 8], ul[kPR + 4][kPC + 8];  // film, cols x0-4 ..
-  float laph[kPR + 2][kPC + 4], lapl[kPR + 2][kPC + 4];  // cell values, cols x0-2 ..
-  float f0h[kPR + 2][kPC + 4], f0l[kPR + 2][kPC + 4];
-  float f1h[kPR + 2][kPC + 4], f1l[kPR + 2][kPC + 4];
-  float fxh[kPR][kPC + 2], fxl[kPR][kPC + 2];  // face kf: cells x0-2+kf | x0-1+kf
-  float fyh[kPR + 1][kPC], fyl[kPR + 1][kPC];  // face k: rows j0-1+k | j0+k
-};
-
-// load the pair of plane entries at (row, even col)
-template <int W>
-__device__ __forceinline__ df2 ld2(const float (&h)[W], const float (&l)[W], int c) {
-  return d2(*reinterpret_cast<const float2*>(&h[c]), *reinterpret_cast<const float2*>(&l[c]));
-}
-template <int W>
-__device__ __forceinline__ void st2(float (&h)[W], float (&l)[W], int c, df2 v) {
-  *reinterpret_cast<float2*>(&h[c]) = v.hi;
-  *reinterpret_cast<float2*>(&l[c]) = v.lo;
-}
-// the odd-offset pair (A.y, B.x) of two consecutive aligned pairs
-__device__ __forceinline__ df2 mid2(df2 A, df2 B) {
-  return d2(make_float2(A.hi.y, B.hi.x), make_float2(A.lo.y, B.lo.x));
-}
+// height differences and the reciprocal
 
 // the difference of two double-float heights: exact leading part when the
 // two leading floats are within a factor 2 (FAST), else the general one
@@ -139,101 +122,126 @@ template <bool FAST> __device__ __forceinline__ df2 hdiff(df2 a, df2 b) {
 // 1/a for a positive double-float a (the refined MUFU reciprocal)
 __device__ __forceinline__ df2 d2_rcp_fast(df2 a) {
   const float2 y = make_float2(rcp(a.hi.x), rcp(a.hi.y));
-  float2 e = p_fma(p_neg(a.hi), y, p_splat(1.0f));
-  e = p_fma(p_neg(a.lo), y, e);
-  return d2(y, p_mul(y, e));
+  // t = -(1 - a y) exactly: fma(a.hi, y, -1), then fma(a.lo, y, .)
+  float2 t = p_fma(a.hi, y, p_splat(-1.0f));
+  t = p_fma(a.lo, y, t);
+  return d2(y, p_negz(p_mul(y, t)));
 }
 
-// Stages 2-4 of the residual (see k_rhs_packed); FAST selects the height
-// differences.  Returns max|G| over the thread's cells.
+// ---------------------------------------------------------------------------
+// the kernel
+//
+// Each warp walks a strip of kSW = 60 columns down a segment of rows.  Lane
+// l holds the cell pair (x0 - 2 + 2l, x0 - 1 + 2l) of the strip (lanes 0
+// and 31 are halo), and the warp carries from one row to the next, in
+// registers, the heights of the current and the next row, the current
+// row's Laplacian and mobilities and the flux through the face above it.  A
+// row step takes one new row of heights, forms the next row's cell values
+// (x neighbours by warp shuffles), the face between the two rows, the
+// current row's x faces and its G.  A cell's value, a face's flux and G
+// are each formed once per strip, from the same operands in the same order
+// wherever they are formed.  The choice between the exact and the general
+// height differences is made per row step, over the three rows of heights
+// that step reads.
+
+constexpr int kSW = 60;  // output columns of a strip
+constexpr int kST = 128;  // threads per block
+constexpr int kSWarps = kST / 32;
+
+
+// one row of heights of the lane's pair, as stored (reflected at the walls)
+__device__ __forceinline__ double2 strip_load(const double* __restrict__ u, int nx, int ny, int j, int xa,
+                                              bool inner) {
+  const size_t row = (size_t)((unsigned)j < (unsigned)ny ? j : reflect_index(j, ny)) * nx;
+  if (inner) return __ldg(reinterpret_cast<const double2*>(u + row + xa));
+  double2 v;
+  v.x = __ldg(u + row + reflect_index(xa, nx));
+  v.y = __ldg(u + row + reflect_index(xa + 1, nx));
+  return v;
+}
+// the pair as double-float, and the warp's range of leading-float bits
+__device__ __forceinline__ df2 strip_conv(double2 v, unsigned& lo, unsigned& hi) {
+  const df64 a = df_of_pos_f64_fast(v.x), b = df_of_pos_f64_fast(v.y);
+  const unsigned ba = __float_as_uint(a.hi), bb = __float_as_uint(b.hi);
+  lo = __reduce_min_sync(0xffffffffu, min(ba, bb));
+  hi = __reduce_max_sync(0xffffffffu, max(ba, bb));
+  return d2(make_float2(a.hi, b.hi), make_float2(a.lo, b.lo));
+}
+__device__ __forceinline__ bool strip_fast(unsigned lo, unsigned hi) {
+  return lo > 0u && hi < 0x7f800000u && __uint_as_float(hi) <= 1.25f * __uint_as_float(lo);
+}
+
+// Laplacian, f0 and f1 of the pair U with the rows above (Um) and below
+// (Up); (lh, ll) is the left neighbour's height, (rh, rl) the right one's
+template <bool FAST>
+__device__ __forceinline__ void strip_cells(const RhsK<df64>& K, const df2& U, const df2& Um, const df2& Up, float lh,
+                                            float ll, float rh, float rl, df2& lap, df2& f0, df2& f1) {
+  const df2 E = d2(make_float2(U.hi.y, rh), make_float2(U.lo.y, rl));
+  const df2 Wn = d2(make_float2(lh, U.hi.x), make_float2(ll, U.lo.x));
+  df2 l;
+  if constexpr (FAST) {
+    const df2 dE = hdiff<true>(E, U), dW = hdiff<true>(Wn, U);
+    const df2 dS = hdiff<true>(Up, U), dN = hdiff<true>(Um, U);
+    l = d2(p_add(p_add(dE.hi, dW.hi), p_add(dS.hi, dN.hi)), p_add(p_add(dE.lo, dW.lo), p_add(dS.lo, dN.lo)));
+  } else {
+    l = d2_add_u(d2_add_u(d2_sub_u(E, U), d2_sub_u(Wn, U)), d2_add_u(d2_sub_u(Up, U), d2_sub_u(Um, U)));
+  }
+  lap = d2_mul_u(l, d2_splat(K.inv_ds2));
+  const df2 h2 = d2_mul_u(U, U);
+  f0 = K.mc.unitC ? d2_mul_u(h2, U) : d2_mul_u(d2_mul_u(d2_splat(K.mc.C), h2), U);
+  f1 = d2_sub_u(d2_splat(K.mc.A1), d2_mul_u(d2_splat(K.mc.B1), d2_rcp_fast(U)));
+}
+
+struct StripState {
+  df2 U0, U1;           // heights of rows j, j + 1
+  float Lh, Ll;         // left neighbour's height in row j
+  df2 lap, f0, f1;      // cell values of row j
+  df2 FyM;              // flux through the face between rows j - 1 and j
+};
+
+// One row step: from the state at row j and the heights U2 of row j + 2,
+// G of row j (when `out`), then the state at row j + 1.  Returns max|G|
+// of the lane's cells.
 template <int KIND, bool FAST>
-__device__ __forceinline__ float rhs_stages(RhsPackedSmem& S, const RhsK<df64>& RK, int x0, int j0, int nx,
-                                            int ny, df64* __restrict__ bn,
-                                            float* __restrict__ rhs, float* __restrict__ ulp,
-                                            const df64 (&bnr)[kPR * kPC / 2 / kPT][2]) {
-  const int tid = threadIdx.x;
-  // ---- stage 2: lap, f0, f1 of cells (rs, cs): global (j0-1+rs, x0-2+cs)
-  {
-    const df2 inv_ds2 = d2_splat(RK.inv_ds2);
-    const df2 A1 = d2_splat(RK.mc.A1), B1 = d2_splat(RK.mc.B1), C = d2_splat(RK.mc.C);
-    const bool unitC = RK.mc.unitC;
-    constexpr int W2 = (kPC + 4) / 2;
-    for (int k = tid; k < (kPR + 2) * W2; k += kPT) {
-      const int rs = k / W2, cs = 2 * (k - rs * W2);
-      const int tr = rs + 1, tc = cs + 2;  // the pair's position in the film tile
-      const df2 uc = ld2(S.uh[tr], S.ul[tr], tc);
-      const df2 Wp = ld2(S.uh[tr], S.ul[tr], tc - 2), Ep = ld2(S.uh[tr], S.ul[tr], tc + 2);
-      const df2 E = mid2(uc, Ep), Wn = mid2(Wp, uc);
-      const df2 Sn = ld2(S.uh[tr + 1], S.ul[tr + 1], tc), Nn = ld2(S.uh[tr - 1], S.ul[tr - 1], tc);
-      df2 lap;
-      if constexpr (FAST) {
-        const df2 dE = hdiff<true>(E, uc), dW = hdiff<true>(Wn, uc);
-        const df2 dS = hdiff<true>(Sn, uc), dN = hdiff<true>(Nn, uc);
-        lap = d2(p_add(p_add(dE.hi, dW.hi), p_add(dS.hi, dN.hi)), p_add(p_add(dE.lo, dW.lo), p_add(dS.lo, dN.lo)));
-      } else {
-        lap = d2_add_u(d2_add_u(d2_sub_u(E, uc), d2_sub_u(Wn, uc)), d2_add_u(d2_sub_u(Sn, uc), d2_sub_u(Nn, uc)));
-      }
-      st2(S.laph[rs], S.lapl[rs], cs, d2_mul_u(lap, inv_ds2));
-      // f0 = C h^3, f1 = A1 - B1 / h (the (3, 2) power law)
-      const df2 h2 = d2_mul_u(uc, uc);
-      const df2 f0 = unitC ? d2_mul_u(h2, uc) : d2_mul_u(d2_mul_u(C, h2), uc);
-      const df2 f1 = d2_sub_u(A1, d2_mul_u(B1, d2_rcp_fast(uc)));
-      st2(S.f0h[rs], S.f0l[rs], cs, f0);
-      st2(S.f1h[rs], S.f1l[rs], cs, f1);
-    }
+__device__ __forceinline__ float strip_step(StripState& s, const df2& U2, const df2& B, bool out, int j, int a,
+                                            bool lane_out, const RhsK<df64>& RK, int nx, int ny,
+                                            df64* __restrict__ bn, float* __restrict__ rhs,
+                                            float* __restrict__ ulp) {
+  constexpr unsigned F = 0xffffffffu;
+  // x faces left of the lane's two cells, (a - 1 | a) and (a | a + 1), and
+  // the x part of their divergence
+  df2 dx = d2(p_splat(0.0f), p_splat(0.0f));
+  if (out) {
+    const float lph = __shfl_up_sync(F, s.lap.hi.y, 1), lpl = __shfl_up_sync(F, s.lap.lo.y, 1);
+    const float f0h = __shfl_up_sync(F, s.f0.hi.y, 1), f0l = __shfl_up_sync(F, s.f0.lo.y, 1);
+    const float f1h = __shfl_up_sync(F, s.f1.hi.y, 1), f1l = __shfl_up_sync(F, s.f1.lo.y, 1);
+    const df2 f0P = d2(make_float2(f0h, s.f0.hi.x), make_float2(f0l, s.f0.lo.x));
+    const df2 f1P = d2(make_float2(f1h, s.f1.hi.x), make_float2(f1l, s.f1.lo.x));
+    const df2 lP = d2(make_float2(lph, s.lap.hi.x), make_float2(lpl, s.lap.lo.x));
+    const df2 uP = d2(make_float2(s.Lh, s.U0.hi.x), make_float2(s.Ll, s.U0.lo.x));
+    df2 Fx = d2_add_u(d2_mul_u(d2_add_u(f0P, s.f0), d2_sub_u(s.lap, lP)),
+                      d2_mul_u(d2_add_u(f1P, s.f1), hdiff<FAST>(s.U0, uP)));
+    if (!(a - 1 >= 0 && a < nx)) Fx.hi.x = Fx.lo.x = 0.0f;
+    if (!(a >= 0 && a + 1 < nx)) Fx.hi.y = Fx.lo.y = 0.0f;
+    const float nh = __shfl_down_sync(F, Fx.hi.x, 1), nl = __shfl_down_sync(F, Fx.lo.x, 1);
+    dx = d2_sub_u(d2(make_float2(Fx.hi.y, nh), make_float2(Fx.lo.y, nl)), Fx);
   }
-  __syncthreads();
-  // ---- stage 3: face fluxes f0bar dLap + f1bar du (zero on the walls)
-  {
-    constexpr int WX = (kPC + 2) / 2, WY = kPC / 2, NXF = kPR * WX;
-    // x- and y-face pairs in one loop, so that the threads share the work evenly
-    for (int k2 = tid; k2 < NXF + (kPR + 1) * WY; k2 += kPT) {
-      if (k2 >= NXF) {
-        const int k = k2 - NXF;
-        const int q = k / WY, c = 2 * (k - q * WY);  // face between rows j0-1+q and j0+q
-        const df2 f0P = ld2(S.f0h[q], S.f0l[q], c + 2), f0Q = ld2(S.f0h[q + 1], S.f0l[q + 1], c + 2);
-        const df2 f1P = ld2(S.f1h[q], S.f1l[q], c + 2), f1Q = ld2(S.f1h[q + 1], S.f1l[q + 1], c + 2);
-        const df2 lP = ld2(S.laph[q], S.lapl[q], c + 2), lQ = ld2(S.laph[q + 1], S.lapl[q + 1], c + 2);
-        const df2 uP = ld2(S.uh[q + 1], S.ul[q + 1], c + 4), uQ = ld2(S.uh[q + 2], S.ul[q + 2], c + 4);
-        df2 F = d2_add_u(d2_mul_u(d2_add_u(f0P, f0Q), d2_sub_u(lQ, lP)),
-                         d2_mul_u(d2_add_u(f1P, f1Q), hdiff<FAST>(uQ, uP)));
-        const int gp = j0 - 1 + q;
-        if (!(gp >= 0 && gp + 1 < ny)) F = d2(p_splat(0.0f), p_splat(0.0f));
-        st2(S.fyh[q], S.fyl[q], c, F);
-        continue;
-      }
-      const int k = k2;
-      const int r = k / WX, kf = 2 * (k - r * WX);  // faces kf, kf + 1 of row j0 + r
-      const int rs = r + 1, tr = r + 2;
-      const df2 f0P = ld2(S.f0h[rs], S.f0l[rs], kf), f0R = ld2(S.f0h[rs], S.f0l[rs], kf + 2);
-      const df2 f1P = ld2(S.f1h[rs], S.f1l[rs], kf), f1R = ld2(S.f1h[rs], S.f1l[rs], kf + 2);
-      const df2 lP = ld2(S.laph[rs], S.lapl[rs], kf), lR = ld2(S.laph[rs], S.lapl[rs], kf + 2);
-      const df2 uP = ld2(S.uh[tr], S.ul[tr], kf + 2), uR = ld2(S.uh[tr], S.ul[tr], kf + 4);
-      const df2 f0Q = mid2(f0P, f0R), f1Q = mid2(f1P, f1R), lQ = mid2(lP, lR), uQ = mid2(uP, uR);
-      df2 F = d2_add_u(d2_mul_u(d2_add_u(f0P, f0Q), d2_sub_u(lQ, lP)),
-                       d2_mul_u(d2_add_u(f1P, f1Q), hdiff<FAST>(uQ, uP)));
-      const int gp = x0 - 2 + kf;  // left cell of face kf
-      if (!(gp >= 0 && gp + 1 < nx)) F.hi.x = F.lo.x = 0.0f;
-      if (!(gp + 1 >= 0 && gp + 2 < nx)) F.hi.y = F.lo.y = 0.0f;
-      st2(S.fxh[r], S.fxl[r], kf, F);
-    }
-  }
-  __syncthreads();
-  // ---- stage 4: G (or b^n) of the tile's cells, two per thread
-  constexpr int W4 = kPC / 2, N4 = kPR * W4 / kPT;
-  const df2 gscale = d2_splat(RK.gscale);
-  float g = 0.0f;  // max |G| in FP32: a norm for reporting, not a decision
-#pragma unroll
-  for (int e = 0; e < N4; ++e) {
-    const int k = tid + e * kPT, r = k / W4, c = 2 * (k - r * W4);
-    const int gj = j0 + r, gi = x0 + c;
-    if (gj >= ny || gi >= nx) continue;
-    const bool two = gi + 1 < nx;
-    const df2 A = ld2(S.fxh[r], S.fxl[r], c), B = ld2(S.fxh[r], S.fxl[r], c + 2);
-    const df2 dp = d2_add_u(d2_sub_u(B, mid2(A, B)),
-                            d2_sub_u(ld2(S.fyh[r + 1], S.fyl[r + 1], c), ld2(S.fyh[r], S.fyl[r], c)));
-    const df2 uc = ld2(S.uh[r + 2], S.ul[r + 2], c + 4);
-    const size_t idx = (size_t)gj * nx + gi;
+  // cell values of row j + 1
+  const float l1h = __shfl_up_sync(F, s.U1.hi.y, 1), l1l = __shfl_up_sync(F, s.U1.lo.y, 1);
+  const float r1h = __shfl_down_sync(F, s.U1.hi.x, 1), r1l = __shfl_down_sync(F, s.U1.lo.x, 1);
+  df2 lap1, f01, f11;
+  strip_cells<FAST>(RK, s.U1, s.U0, U2, l1h, l1l, r1h, r1l, lap1, f01, f11);
+  // the face between rows j and j + 1 (zero on the walls)
+  df2 FyP = d2_add_u(d2_mul_u(d2_add_u(s.f0, f01), d2_sub_u(lap1, s.lap)),
+                     d2_mul_u(d2_add_u(s.f1, f11), hdiff<FAST>(s.U1, s.U0)));
+  if (!(j >= 0 && j + 1 < ny)) FyP = d2(p_splat(0.0f), p_splat(0.0f));
+  float g = 0.0f;
+  if (out && lane_out && a < nx) {
+    const df2 dp = d2_add_u(dx, d2_sub_u(FyP, s.FyM));
+    const df2 uc = s.U0;
+    const bool two = a + 1 < nx;
+    const size_t idx = (size_t)j * nx + a;
+    const df2 gscale = d2_splat(RK.gscale);
     if constexpr (KIND == kRhsExplicit) {
       const df2 b = d2_norm(d2_sub_u(uc, d2_mul_u(gscale, dp)));
       bn[idx] = df_make(b.hi.x, b.lo.x);
@@ -246,14 +254,13 @@ __device__ __forceinline__ float rhs_stages(RhsPackedSmem& S, const RhsK<df64>& 
         if (two) bn[idx + 1] = df_make(bv.hi.y, bv.lo.y);
         if (!two) bv = d2(make_float2(bv.hi.x, 1.0f), make_float2(bv.lo.x, 0.0f));  // as the loaded pair
       } else {
-        const df64 b0 = bnr[e][0], b1 = bnr[e][1];
-        bv = d2(make_float2(b0.hi, b1.hi), make_float2(b0.lo, b1.lo));
+        bv = B;
       }
       const df2 gs = KIND == kRhsBoth ? d2_splat(RK.gscale2) : gscale;
       const df2 Gv = d2_norm(d2_add_u(d2_sub_u(uc, bv), d2_mul_u(gs, dp)));
       const float2 gl = p_add(Gv.hi, Gv.lo);
       // FP32 film for the sweeps: the leading float of the double-float height
-      if (two && ((nx | gi) & 1) == 0) {
+      if (two && ((nx | a) & 1) == 0) {
         *reinterpret_cast<float2*>(rhs + idx) = make_float2(-gl.x, -gl.y);
         *reinterpret_cast<float2*>(ulp + idx) = uc.hi;
       } else {
@@ -264,121 +271,152 @@ __device__ __forceinline__ float rhs_stages(RhsPackedSmem& S, const RhsK<df64>& 
           ulp[idx + 1] = uc.hi.y;
         }
       }
-      float ag = fabsf(gl.x);
-      if (!(ag <= g)) g = ag;
-      ag = two ? fabsf(gl.y) : 0.0f;
+      g = fabsf(gl.x);
+      const float ag = two ? fabsf(gl.y) : 0.0f;
       if (!(ag <= g)) g = ag;
     }
   }
+  s.U0 = s.U1;
+  s.U1 = U2;
+  s.Lh = l1h;
+  s.Ll = l1l;
+  s.lap = lap1;
+  s.f0 = f01;
+  s.f1 = f11;
+  s.FyM = FyP;
   return g;
+}
+
+// Rows reach the warps through shared memory: each warp has a ring of four
+// rows of heights and four of b^n, filled with asynchronous copies two rows
+// ahead of their use, so no register holds a load in flight.
+struct StripRing {
+  double2 u[4][32];  // the lane's pair of heights
+  float4 b[4][32];   // the lane's pair of b^n (hi, lo, hi, lo)
+};
+
+// queue the copy of row j of heights into dst (reflected at the walls)
+__device__ __forceinline__ void strip_copy_u(double2* dst, const double* __restrict__ u, int nx, int ny, int j,
+                                             int xa, bool inner) {
+  const double* row = u + (size_t)((unsigned)j < (unsigned)ny ? j : reflect_index(j, ny)) * nx;
+  if (inner) {
+    __pipeline_memcpy_async(dst, row + xa, 16);
+  } else {
+    __pipeline_memcpy_async(reinterpret_cast<double*>(dst), row + reflect_index(xa, nx), 8);
+    __pipeline_memcpy_async(reinterpret_cast<double*>(dst) + 1, row + reflect_index(xa + 1, nx), 8);
+  }
+}
+// queue the copy of the lane's b^n of row j (nothing where there is no cell)
+__device__ __forceinline__ void strip_copy_bn(float4* dst, const df64* __restrict__ bn, int nx, int ny, int j,
+                                              int a, bool lane_out) {
+  if (!(lane_out && j < ny && a < nx)) return;
+  const size_t idx = (size_t)j * nx + a;
+  if (a + 1 < nx && ((nx | a) & 1) == 0) {
+    __pipeline_memcpy_async(dst, bn + idx, 16);
+  } else {
+    __pipeline_memcpy_async(reinterpret_cast<df64*>(dst), bn + idx, 8);
+    if (a + 1 < nx) __pipeline_memcpy_async(reinterpret_cast<df64*>(dst) + 1, bn + idx + 1, 8);
+  }
 }
 
 // KIND: kRhsResidual (G from u_k and the stored b^n), kRhsExplicit (b^n from
 // u^n) or kRhsBoth (b^n from u^n, stored, and G of the first iteration,
 // u_0 = u^n, from the same stored b^n -- what kRhsResidual would compute).
+// Warp w of the grid takes strip w % nstrip and rows [seg_rows * (w /
+// nstrip), + seg_rows); one partial result (max|G|) per block.
 template <int KIND>
-__global__ void __launch_bounds__(kPT, 2)  // shared memory allows 2 blocks per SM: up to 64 registers
-    k_rhs_packed(ModelK M, RhsK<df64> RK, const double* __restrict__ u, df64* __restrict__ bn,
-                 float* __restrict__ rhs, float* __restrict__ ulp, PartX* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  RhsPackedSmem& S = *reinterpret_cast<RhsPackedSmem*>(smem_raw);
-  const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * kPC, j0 = blockIdx.y * kPR;
+__global__ void __launch_bounds__(kST, 5)
+    k_rhs_strip(ModelK M, RhsK<df64> RK, const double* __restrict__ u, df64* __restrict__ bn,
+                float* __restrict__ rhs, float* __restrict__ ulp, PartX* __restrict__ part, int nstrip,
+                int seg_rows) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = M.nx, ny = M.ny;
-  // b^n of this thread's stage-4 cells, loaded first so that its latency
-  // overlaps the stencil stages
-  constexpr int W4 = kPC / 2, N4 = kPR * W4 / kPT;
-  static_assert(kPR * W4 == N4 * kPT, "stage 4 gives every thread the same number of pairs");
-  df64 bnr[N4][2];
-  if constexpr (KIND == kRhsResidual) {
-#pragma unroll
-    for (int e = 0; e < N4; ++e) {
-      const int k = tid + e * kPT, r = k / W4, c = 2 * (k - r * W4);
-      const int gj = j0 + r, gi = x0 + c;
-      bnr[e][0] = bnr[e][1] = df_make(1.0f, 0.0f);
-      if (gj < ny && gi < nx) {
-        const size_t idx = (size_t)gj * nx + gi;
-        bnr[e][0] = bn[idx];
-        if (gi + 1 < nx) bnr[e][1] = bn[idx + 1];
+  const int w = blockIdx.x * kSWarps + warp;
+  const int nseg = (ny + seg_rows - 1) / seg_rows;
+  __shared__ StripRing ring[kSWarps];
+  float g = 0.0f;
+  if (w < nstrip * nseg) {
+    const int x0 = (w % nstrip) * kSW, ja = (w / nstrip) * seg_rows;
+    const int jb = min(ja + seg_rows, ny);
+    const int a = x0 - 2 + 2 * lane;  // the lane's first cell
+    const bool lane_out = lane >= 1 && lane <= kSW / 2;
+    const bool inner = x0 - 2 >= 0 && x0 + kSW + 2 <= nx && (nx & 1) == 0 &&
+                       (reinterpret_cast<uintptr_t>(u) & 15) == 0;
+    StripRing& R = ring[warp];
+    // rows ja - 2 .. ja directly; rows ja + 1, ja + 2 (and b^n of rows ja,
+    // ja + 1) queued
+    unsigned lo0, hi0, lo1, hi1, lo2, hi2, lo3, hi3;
+    const df2 Um2 = strip_conv(strip_load(u, nx, ny, ja - 2, a, inner), lo0, hi0);
+    const df2 Um1 = strip_conv(strip_load(u, nx, ny, ja - 1, a, inner), lo1, hi1);
+    const df2 Ua = strip_conv(strip_load(u, nx, ny, ja, a, inner), lo2, hi2);
+    for (int q = 1; q <= 2; ++q) {
+      strip_copy_u(&R.u[(ja + q) & 3][lane], u, nx, ny, ja + q, a, inner);
+      if constexpr (KIND == kRhsResidual) strip_copy_bn(&R.b[(ja + q - 1) & 3][lane], bn, nx, ny, ja + q - 1, a, lane_out);
+      __pipeline_commit();
+    }
+    StripState s;
+    s.U0 = Um1;
+    s.U1 = Ua;
+    s.FyM = d2(p_splat(0.0f), p_splat(0.0f));
+    {  // cell values of row ja - 1
+      constexpr unsigned F = 0xffffffffu;
+      const float lh = __shfl_up_sync(F, Um1.hi.y, 1), ll = __shfl_up_sync(F, Um1.lo.y, 1);
+      const float rh = __shfl_down_sync(F, Um1.hi.x, 1), rl = __shfl_down_sync(F, Um1.lo.x, 1);
+      s.Lh = lh;
+      s.Ll = ll;
+      if (strip_fast(min(lo0, min(lo1, lo2)), max(hi0, max(hi1, hi2))))
+        strip_cells<true>(RK, Um1, Um2, Ua, lh, ll, rh, rl, s.lap, s.f0, s.f1);
+      else
+        strip_cells<false>(RK, Um1, Um2, Ua, lh, ll, rh, rl, s.lap, s.f0, s.f1);
+    }
+    // row steps j = ja - 1 (state only) .. jb - 1; the state's rows j, j + 1
+    // have ranges (lo1, hi1), (lo2, hi2).  Step j queues heights of row
+    // j + 4 and b^n of row j + 3 (slots last read two steps before) and
+    // waits for the copies of step j - 2 (heights j + 2, b^n j + 1).
+    for (int j = ja - 1; j < jb; ++j) {
+      const bool out = j >= ja;
+      strip_copy_u(&R.u[(j + 4) & 3][lane], u, nx, ny, j + 4, a, inner);
+      if constexpr (KIND == kRhsResidual) strip_copy_bn(&R.b[(j + 3) & 3][lane], bn, nx, ny, j + 3, a, lane_out);
+      __pipeline_commit();
+      __pipeline_wait_prior(2);
+      df2 B = d2(p_splat(1.0f), p_splat(0.0f));
+      if constexpr (KIND == kRhsResidual) {
+        if (out) {
+          const float4 v = R.b[j & 3][lane];
+          B = d2(make_float2(v.x, v.z), make_float2(v.y, v.w));
+        }
       }
+      const df2 U2 = strip_conv(R.u[(j + 2) & 3][lane], lo3, hi3);
+      float gj;
+      if (strip_fast(min(lo1, min(lo2, lo3)), max(hi1, max(hi2, hi3))))
+        gj = strip_step<KIND, true>(s, U2, B, out, j, a, lane_out, RK, nx, ny, bn, rhs, ulp);
+      else
+        gj = strip_step<KIND, false>(s, U2, B, out, j, a, lane_out, RK, nx, ny, bn, rhs, ulp);
+      if (!(gj <= g)) g = gj;
+      lo1 = lo2;
+      hi1 = hi2;
+      lo2 = lo3;
+      hi2 = hi3;
     }
+    __pipeline_wait_prior(0);  // no copy outlives the warp
   }
-  // ---- stage 1: film tile (two-cell halo, wall-reflected) as double-float
-  // planes, and the range of its leading floats
-  __shared__ unsigned s_lo, s_hi;
-  if (tid == 0) {
-    s_lo = 0xffffffffu;
-    s_hi = 0u;
-  }
-  __syncthreads();
-  {
-    constexpr int W2 = (kPC + 8) / 2;
-    const bool inner_x = x0 - 4 >= 0 && x0 + kPC + 4 <= nx && (nx & 1) == 0 &&
-                         (reinterpret_cast<uintptr_t>(u) & 15) == 0;
-    // all of a thread's loads are issued before the first conversion
-    constexpr int NP = (kPR + 4) * W2, N1 = (NP + kPT - 1) / kPT;
-    double2 v[N1];
-#pragma unroll
-    for (int i = 0; i < N1; ++i) {
-      const int k = min(tid + i * kPT, NP - 1);
-      const int r = k / W2, c = 2 * (k - r * W2);
-      const int gj = reflect_index(j0 - 2 + r, ny);
-      if (inner_x) {
-        v[i] = __ldg(reinterpret_cast<const double2*>(u + (size_t)gj * nx + (x0 - 4 + c)));
-      } else {
-        v[i].x = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 4 + c, nx));
-        v[i].y = __ldg(u + (size_t)gj * nx + reflect_index(x0 - 3 + c, nx));
-      }
-    }
-    // positive floats order as their bit patterns; anything else (zero,
-    // negative, NaN) makes the range fail the fast-path test below
-    unsigned lo = 0xffffffffu, hi = 0u;
-#pragma unroll
-    for (int i = 0; i < N1; ++i) {
-      const int k = tid + i * kPT;
-      if (k >= NP) break;
-      const int r = k / W2, c = 2 * (k - r * W2);
-      const df64 da = df_of_pos_f64_fast(v[i].x), db = df_of_pos_f64_fast(v[i].y);
-      *reinterpret_cast<float2*>(&S.uh[r][c]) = make_float2(da.hi, db.hi);
-      *reinterpret_cast<float2*>(&S.ul[r][c]) = make_float2(da.lo, db.lo);
-      const unsigned ba = __float_as_uint(da.hi), bb = __float_as_uint(db.hi);
-      lo = min(lo, min(ba, bb));
-      hi = max(hi, max(ba, bb));
-    }
-    lo = __reduce_min_sync(0xffffffffu, lo);
-    hi = __reduce_max_sync(0xffffffffu, hi);
-    if ((tid & 31) == 0) {
-      atomicMin(&s_lo, lo);
-      atomicMax(&s_hi, hi);
-    }
-  }
-  __syncthreads();
-  // the fast path needs every leading float positive, finite and within 25%
-  // of the smallest
-  const float fmn = __uint_as_float(s_lo), fmx = __uint_as_float(s_hi);
-  const bool fast = s_lo > 0u && s_hi < 0x7f800000u && fmx <= 1.25f * fmn;
-  float g;
-  if (fast)
-    g = rhs_stages<KIND, true>(S, RK, x0, j0, nx, ny, bn, rhs, ulp, bnr);
-  else
-    g = rhs_stages<KIND, false>(S, RK, x0, j0, nx, ny, bn, rhs, ulp, bnr);
   if constexpr (KIND == kRhsExplicit) return;
   for (int o = 16; o > 0; o >>= 1) {
     const float g2 = __shfl_xor_sync(0xffffffffu, g, o);
     if (!(g2 <= g)) g = g2;
   }
-  __shared__ float red[kPT / 32];
-  if ((tid & 31) == 0) red[tid >> 5] = g;
+  __shared__ float red[kSWarps];
+  if (lane == 0) red[warp] = g;
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     float mx = red[0];
-    for (int k = 1; k < kPT / 32; ++k)
+    for (int k = 1; k < kSWarps; ++k)
       if (!(red[k] <= mx)) mx = red[k];
     PartX p;
     p.gnorm = (double)mx;
     p.pivot = 0;
     p.pad = 0;
-    part[blockIdx.y * gridDim.x + blockIdx.x] = p;
+    part[blockIdx.x] = p;
   }
 }
 
