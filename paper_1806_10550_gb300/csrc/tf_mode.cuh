@@ -54,7 +54,7 @@ template <class Mode> struct Launch {
     if constexpr (kF32B) {
       if (c.packed_rhs) {
         k_rhs_strip<kRhsExplicit><<<c.grid_pkx, kST, 0, c.stream>>>(
-            c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, nullptr, nullptr, nullptr, c.strip_n, c.strip_rows);
+            c.mk, strip_consts(c.mk, step(c, dt), true), u_old, (HP*)c.bn, nullptr, nullptr, nullptr, c.strip_n, c.strip_rows);
         return cudaGetLastError();
       }
     }
@@ -73,7 +73,7 @@ template <class Mode> struct Launch {
     if constexpr (kF32B) {
       if (c.packed_rhs) {
         k_rhs_strip<kRhsResidual><<<c.grid_pkx, kST, 0, c.stream>>>(
-            c.mk, rhs_consts<HP>(c.mk, step(c, dt)), u_k, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px, c.strip_n, c.strip_rows);
+            c.mk, strip_consts(c.mk, step(c, dt), false), u_k, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px, c.strip_n, c.strip_rows);
         return cudaGetLastError();
       }
     }
@@ -90,7 +90,7 @@ template <class Mode> struct Launch {
     if constexpr (kF32B) {
       if (c.packed_rhs) {
         k_rhs_strip<kRhsBoth><<<c.grid_pkx, kST, 0, c.stream>>>(
-            c.mk, rhs_consts<HP>(c.mk, step(c, dt), true), u_old, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px, c.strip_n, c.strip_rows);
+            c.mk, strip_consts(c.mk, step(c, dt), true), u_old, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px, c.strip_n, c.strip_rows);
         return cudaGetLastError();
       }
     }

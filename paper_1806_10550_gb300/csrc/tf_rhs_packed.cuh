@@ -71,11 +71,11 @@ __device__ __forceinline__ df2 d2_sub_u(df2 a, df2 b) {
   const float2 e = p_sub(p_sub(a.hi, p_sub(s, bb)), p_add(b.hi, bb));
   return d2(s, p_add(e, p_sub(a.lo, b.lo)));
 }
-// -p exactly (0 - p), for the product error fma(a, b, -p)
+// -p exactly (0 - p)
 __device__ __forceinline__ float2 p_negz(float2 p) { return p_sub(make_float2(0.0f, 0.0f), p); }
 __device__ __forceinline__ df2 d2_mul_u(df2 a, df2 b) {
   const float2 p = p_mul(a.hi, b.hi);
-  float2 e = p_fma(a.hi, b.hi, p_negz(p));
+  float2 e = p_fma(a.hi, b.hi, p_neg(p));  // measured cheaper than fma(., ., 0 - p)
   e = p_fma(a.hi, b.lo, e);
   e = p_fma(a.lo, b.hi, e);
   return d2(p, e);
@@ -144,6 +144,28 @@ __device__ __forceinline__ df2 d2_rcp_fast(df2 a) {
 // height differences is made per row step, over the three rows of heights
 // that step reads.
 
+// Constants of a launch.  The Laplacian is carried unscaled (the plain sum
+// of height differences), so the face fluxes are ds^2 times those of the
+// operator: the f1 term takes f1 ds^2 = A1 ds^2 - B1 ds^2 / h, and the
+// divergence is scaled by gscale / ds^2.
+struct StripK {
+  df64 C, A1s, B1s;  // C, A1 ds^2, B1 ds^2
+  df64 gs;           // gscale / ds^2 (theta dt or (1 - theta) dt, / (2 ds^4))
+  df64 gs2;          // the residual's theta dt / (2 ds^4), for kRhsBoth
+  int unitC;         // C == 1
+};
+inline StripK strip_consts(const ModelK& M, const StepK& K, bool expl) {
+  const double ds2 = 1.0 / M.inv_ds2, i4 = 0.5 * M.inv_ds2 * M.inv_ds2;
+  StripK k;
+  k.C = from_f64<df64>(M.C);
+  k.A1s = from_f64<df64>(M.A1 * ds2);
+  k.B1s = from_f64<df64>(M.B1 * ds2);
+  k.gs = from_f64<df64>(i4 * (expl ? K.expl_dt : K.theta_dt));
+  k.gs2 = from_f64<df64>(i4 * K.theta_dt);
+  k.unitC = M.C == 1.0;
+  return k;
+}
+
 constexpr int kSW = 60;  // output columns of a strip
 constexpr int kST = 128;  // threads per block
 constexpr int kSWarps = kST / 32;
@@ -159,22 +181,29 @@ __device__ __forceinline__ double2 strip_load(const double* __restrict__ u, int 
   v.y = __ldg(u + row + reflect_index(xa + 1, nx));
   return v;
 }
-// the pair as double-float, and the warp's range of leading-float bits
+// the pair as double-float (the leading 24 bits, and the next 29 rounded to
+// a float scaled by 2^(e - 1075): the split of df_of_pos_f64_fast, with the
+// scaling as a multiply by a power of two), and the warp's range of
+// leading-float bits
 __device__ __forceinline__ df2 strip_conv(double2 v, unsigned& lo, unsigned& hi) {
-  const df64 a = df_of_pos_f64_fast(v.x), b = df_of_pos_f64_fast(v.y);
-  const unsigned ba = __float_as_uint(a.hi), bb = __float_as_uint(b.hi);
+  const float ha = f32_of_pos_f64_fast(v.x), hb = f32_of_pos_f64_fast(v.y);
+  const unsigned ba = __float_as_uint(ha), bb = __float_as_uint(hb);
+  const float ra = __uint2float_rn((unsigned)__double_as_longlong(v.x) & 0x1fffffffu);
+  const float rb = __uint2float_rn((unsigned)__double_as_longlong(v.y) & 0x1fffffffu);
+  const float2 sc = make_float2(__uint_as_float((ba & 0x7f800000u) - (52u << 23)),
+                                __uint_as_float((bb & 0x7f800000u) - (52u << 23)));
   lo = __reduce_min_sync(0xffffffffu, min(ba, bb));
   hi = __reduce_max_sync(0xffffffffu, max(ba, bb));
-  return d2(make_float2(a.hi, b.hi), make_float2(a.lo, b.lo));
+  return d2(make_float2(ha, hb), p_mul(make_float2(ra, rb), sc));
 }
 __device__ __forceinline__ bool strip_fast(unsigned lo, unsigned hi) {
   return lo > 0u && hi < 0x7f800000u && __uint_as_float(hi) <= 1.25f * __uint_as_float(lo);
 }
 
-// Laplacian, f0 and f1 of the pair U with the rows above (Um) and below
-// (Up); (lh, ll) is the left neighbour's height, (rh, rl) the right one's
+// Laplacian (unscaled), f0 and f1 ds^2 of the pair U with the rows above
+// (Um) and below (Up); (lh, ll) is the left neighbour's height, (rh, rl) the right one's
 template <bool FAST>
-__device__ __forceinline__ void strip_cells(const RhsK<df64>& K, const df2& U, const df2& Um, const df2& Up, float lh,
+__device__ __forceinline__ void strip_cells(const StripK& K, const df2& U, const df2& Um, const df2& Up, float lh,
                                             float ll, float rh, float rl, df2& lap, df2& f0, df2& f1) {
   const df2 E = d2(make_float2(U.hi.y, rh), make_float2(U.lo.y, rl));
   const df2 Wn = d2(make_float2(lh, U.hi.x), make_float2(ll, U.lo.x));
@@ -186,10 +215,10 @@ __device__ __forceinline__ void strip_cells(const RhsK<df64>& K, const df2& U, c
   } else {
     l = d2_add_u(d2_add_u(d2_sub_u(E, U), d2_sub_u(Wn, U)), d2_add_u(d2_sub_u(Up, U), d2_sub_u(Um, U)));
   }
-  lap = d2_mul_u(l, d2_splat(K.inv_ds2));
+  lap = l;
   const df2 h2 = d2_mul_u(U, U);
-  f0 = K.mc.unitC ? d2_mul_u(h2, U) : d2_mul_u(d2_mul_u(d2_splat(K.mc.C), h2), U);
-  f1 = d2_sub_u(d2_splat(K.mc.A1), d2_mul_u(d2_splat(K.mc.B1), d2_rcp_fast(U)));
+  f0 = K.unitC ? d2_mul_u(h2, U) : d2_mul_u(d2_mul_u(d2_splat(K.C), h2), U);
+  f1 = d2_sub_u(d2_splat(K.A1s), d2_mul_u(d2_splat(K.B1s), d2_rcp_fast(U)));
 }
 
 struct StripState {
@@ -204,7 +233,7 @@ struct StripState {
 // of the lane's cells.
 template <int KIND, bool FAST>
 __device__ __forceinline__ float strip_step(StripState& s, const df2& U2, const df2& B, bool out, int j, int a,
-                                            bool lane_out, const RhsK<df64>& RK, int nx, int ny,
+                                            bool lane_out, const StripK& RK, int nx, int ny,
                                             df64* __restrict__ bn, float* __restrict__ rhs,
                                             float* __restrict__ ulp) {
   constexpr unsigned F = 0xffffffffu;
@@ -241,7 +270,7 @@ __device__ __forceinline__ float strip_step(StripState& s, const df2& U2, const 
     const df2 uc = s.U0;
     const bool two = a + 1 < nx;
     const size_t idx = (size_t)j * nx + a;
-    const df2 gscale = d2_splat(RK.gscale);
+    const df2 gscale = d2_splat(RK.gs);
     if constexpr (KIND == kRhsExplicit) {
       const df2 b = d2_norm(d2_sub_u(uc, d2_mul_u(gscale, dp)));
       bn[idx] = df_make(b.hi.x, b.lo.x);
@@ -256,18 +285,19 @@ __device__ __forceinline__ float strip_step(StripState& s, const df2& U2, const 
       } else {
         bv = B;
       }
-      const df2 gs = KIND == kRhsBoth ? d2_splat(RK.gscale2) : gscale;
-      const df2 Gv = d2_norm(d2_add_u(d2_sub_u(uc, bv), d2_mul_u(gs, dp)));
-      const float2 gl = p_add(Gv.hi, Gv.lo);
+      const df2 gs = KIND == kRhsBoth ? d2_splat(RK.gs2) : gscale;
+      // -G = (b^n - u) - gs dp: the negation of G's operations, exactly
+      const df2 Gn = d2_norm(d2_sub_u(d2_sub_u(bv, uc), d2_mul_u(gs, dp)));
+      const float2 gl = p_add(Gn.hi, Gn.lo);
       // FP32 film for the sweeps: the leading float of the double-float height
       if (two && ((nx | a) & 1) == 0) {
-        *reinterpret_cast<float2*>(rhs + idx) = make_float2(-gl.x, -gl.y);
+        *reinterpret_cast<float2*>(rhs + idx) = gl;
         *reinterpret_cast<float2*>(ulp + idx) = uc.hi;
       } else {
-        rhs[idx] = -gl.x;
+        rhs[idx] = gl.x;
         ulp[idx] = uc.hi.x;
         if (two) {
-          rhs[idx + 1] = -gl.y;
+          rhs[idx + 1] = gl.y;
           ulp[idx + 1] = uc.hi.y;
         }
       }
@@ -326,7 +356,7 @@ __device__ __forceinline__ void strip_copy_bn(float4* dst, const df64* __restric
 // nstrip), + seg_rows); one partial result (max|G|) per block.
 template <int KIND>
 __global__ void __launch_bounds__(kST, 5)
-    k_rhs_strip(ModelK M, RhsK<df64> RK, const double* __restrict__ u, df64* __restrict__ bn,
+    k_rhs_strip(ModelK M, StripK RK, const double* __restrict__ u, df64* __restrict__ bn,
                 float* __restrict__ rhs, float* __restrict__ ulp, PartX* __restrict__ part, int nstrip,
                 int seg_rows) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
