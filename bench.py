@@ -258,7 +258,7 @@ def kernel_table(res, N, lp):
 # from an ncu capture of the FP32-bulk kernels at 4096^2 (traffic scales
 # with the cells).  Valid for the kernels as captured; set an entry to None
 # when that kernel changes.
-TRAFFIC_PER_CELL_F32B = {"rhs": None, "x_sweep": 31.42, "y_sweep": 44.57, "explicit": None}
+TRAFFIC_PER_CELL_F32B = {"rhs": 24.44, "x_sweep": 31.42, "y_sweep": 44.57, "explicit": None}
 
 
 def ncu_counters_apply(w) -> bool:
