@@ -53,11 +53,47 @@ def peaks() -> dict:
 # 8 blocks of 256 threads per SM); no measured FP64 figure comes with the
 # HBM and bf16 peaks.
 
+# ncu counters per cell, each stored with a digest of the device sources of
+# the kernel it was counted on: a counter is reported only while those
+# sources are unchanged (current_counters), so an edited kernel reads null
+# until it is counted again.
+CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1806_10550_gb300", "csrc")
+_SWEEP_SOURCES = ["tf_line_sweeps.cuh", "tf_sweeps.cuh", "tf_kernels.cuh", "tf_numeric.cuh"]
+KERNEL_SOURCES = {
+    ("f32b", "rhs"): ["tf_rhs_packed.cuh", "tf_kernels.cuh", "tf_numeric.cuh"],
+    ("f32b", "explicit"): ["tf_rhs_packed.cuh", "tf_kernels.cuh", "tf_numeric.cuh"],
+    ("f32b", "x_sweep"): _SWEEP_SOURCES,
+    ("f32b", "y_sweep"): _SWEEP_SOURCES,
+    ("fp64", "rhs"): ["tf_sweeps.cuh", "tf_kernels.cuh", "tf_numeric.cuh"],
+    ("fp64", "x_sweep"): _SWEEP_SOURCES,
+    ("fp64", "y_sweep"): _SWEEP_SOURCES,
+}
+
+
+def sources_digest(files, root=CSRC) -> str:
+    """First 16 hex digits of the SHA-256 of the named files (name and
+    contents, in the order given)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def current_counters(table, mode, root=CSRC) -> dict:
+    """{kernel: value} from a table of (value, digest) entries, with None for
+    a kernel whose sources no longer have the digest it was counted on."""
+    return {k: (v if v is not None and d == sources_digest(KERNEL_SOURCES[(mode, k)], root) else None)
+            for k, (v, d) in table.items()}
+
+
 # FP64 operations executed per cell by each FP64-mode kernel (DFMA counted
 # as 2, DADD and DMUL as 1), from an ncu capture of the FP64-mode kernels at
-# 4096^2 (per cell they do not depend on the grid size).  Valid for the
-# kernels as captured.
-FP64_FLOPS_PER_CELL = {"rhs": 46.14, "x_sweep": 86.90, "y_sweep": 103.90}
+# 4096^2 (per cell they do not depend on the grid size).
+FP64_FLOPS_PER_CELL = {"rhs": (46.14, "3909518efbba1249"), "x_sweep": (86.90, "d5fca69cac3007bf"),
+                       "y_sweep": (103.90, "d5fca69cac3007bf")}
 
 
 class ClockSampler:
@@ -256,13 +292,13 @@ def kernel_table(res, N, lp):
 
 # DRAM bytes (read + write) per cell per launch of each FP32-bulk kernel,
 # from an ncu capture of the FP32-bulk kernels at 4096^2 (traffic scales
-# with the cells).  Valid for the kernels as captured; set an entry to None
-# when that kernel changes.
-TRAFFIC_PER_CELL_F32B = {"rhs": 24.44, "x_sweep": 31.42, "y_sweep": 44.57, "explicit": None}
+# with the cells).
+TRAFFIC_PER_CELL_F32B = {"rhs": (24.27, "ca82a515e69f5934"), "x_sweep": (31.23, "d5fca69cac3007bf"),
+                         "y_sweep": (44.38, "d5fca69cac3007bf"), "explicit": (21.66, "ca82a515e69f5934")}
 
 
 def ncu_counters_apply(w) -> bool:
-    """True when workload w runs the kernels that the ncu counters behind
+    """True when workload w runs the kernels that the ncu counters of
     TRAFFIC_PER_CELL_F32B and FP64_FLOPS_PER_CELL were taken on: those of the
     (3, 2) power law.  The other models evaluate their mobilities in other
     code (an out-of-line call per cell, Pi in FP64 inside the residual)."""
@@ -948,7 +984,8 @@ def main():
         accepted_steps=acc_local, attempts=R["info"]["attempts"],
         newton_iterations=R["info"]["newton_iterations"],
         cell_iterations_per_s=N * N * R["info"]["newton_iterations"] * world / (R["ms"] * 1e-3),
-        roofline=roofline_hbm(R, N, lp, pk, TRAFFIC_PER_CELL_F32B if head == "f32b" and profiled else None),
+        roofline=roofline_hbm(R, N, lp, pk,
+                              current_counters(TRAFFIC_PER_CELL_F32B, "f32b") if head == "f32b" and profiled else None),
         gpu_launches=R["timing"]["launches"],
         kernel_ms=dict(explicit=R["timing"]["explicit_ms"], rhs=R["timing"]["rhs_ms"],
                        x_sweep=R["timing"]["x_ms"], y_sweep=R["timing"]["y_ms"]),
@@ -973,8 +1010,10 @@ def main():
               "y_sweep": (t["y_launches"], t["y_ms"])}
         dom64 = max(kt, key=lambda k: kt[k][1])
         n64, ms64 = kt[dom64]
-        ach64 = FP64_FLOPS_PER_CELL[dom64] * N * N * n64 / (ms64 * 1e-3) / 1e12
-        it_fl = sum(FP64_FLOPS_PER_CELL[k] * kt[k][0] for k in kt) * N * N
+        fl64 = current_counters(FP64_FLOPS_PER_CELL, "fp64")
+        profiled = profiled and all(v is not None for v in fl64.values())
+        ach64 = fl64[dom64] * N * N * n64 / (ms64 * 1e-3) / 1e12 if profiled else None
+        it_fl = sum(fl64[k] * kt[k][0] for k in kt) * N * N if profiled else None
         it_ms = sum(kt[k][1] for k in kt)
         line["fp64"] = dict(value=v64, ms_per_step=F["ms"] / max(1, F["info"]["attempts"]),
                             accepted_steps=F["info"]["accepted"],
@@ -982,7 +1021,7 @@ def main():
                             ms_per_iteration=per,
                             roofline=None if not profiled else dict(bound="alu", unit="TFLOP/s", peak=round(FP64_TFLOPS, 4),
                                           peak_source="measured live by tf_probe_fma",
-                                          kernel=dom64, flops_per_cell=FP64_FLOPS_PER_CELL[dom64],
+                                          kernel=dom64, flops_per_cell=fl64[dom64],
                                           ms_per_launch=round(ms64 / max(1, n64), 4),
                                           achieved=round(ach64, 4), frac=round(ach64 / FP64_TFLOPS, 4),
                                           flops="executed FP64 operations per cell counted by ncu (DFMA = 2)",

@@ -38,12 +38,13 @@ def test_algorithmic_bytes_per_launch():
 
 
 def test_roofline_of_the_dominant_kernel_and_the_iteration():
-    r = bench.roofline_hbm(dict(timing=TIMING), N, 4, PEAK, bench.TRAFFIC_PER_CELL_F32B)
+    traffic = {k: v for k, (v, _) in bench.TRAFFIC_PER_CELL_F32B.items()}
+    r = bench.roofline_hbm(dict(timing=TIMING), N, 4, PEAK, traffic)
     assert r["kernel"] == "y_sweep" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     per_ms = 911.80 / 1073
     gbs = 20 * N * N / (per_ms * 1e-3) / 1e9
     assert abs(r["achieved"] - gbs) <= 0.05 and abs(r["frac"] - gbs / 6798.2) <= 5e-5
-    assert r["traffic"] == round(bench.TRAFFIC_PER_CELL_F32B["y_sweep"] * N * N)
+    assert r["traffic"] == round(traffic["y_sweep"] * N * N)
     # every launch of the Newton loop over the iterations: 16 B/cell per
     # explicit part and per residual, 4 per x sweep, 20 per y sweep
     it_bytes = (200 * 16 + 873 * 16 + 1073 * (4 + 20)) * N * N / 1073
@@ -57,5 +58,27 @@ def test_traffic_is_null_without_a_capture():
     r = bench.roofline_hbm(dict(timing=TIMING), N, 4, PEAK, None)
     assert r["traffic"] is None
     t = dict(TIMING, y_ms=100.0)  # another dominant kernel: the residual
-    r = bench.roofline_hbm(dict(timing=t), N, 4, PEAK, dict(bench.TRAFFIC_PER_CELL_F32B, rhs=None))
+    traffic = {k: v for k, (v, _) in bench.TRAFFIC_PER_CELL_F32B.items()}
+    r = bench.roofline_hbm(dict(timing=t), N, 4, PEAK, dict(traffic, rhs=None))
     assert r["kernel"] == "rhs" and r["traffic"] is None
+
+
+def test_counters_follow_the_kernel_sources(tmp_path):
+    """A stored ncu counter is reported only while the device sources of its
+    kernel still have the digest it was taken on: editing the residual's
+    header nulls the residual's counters and leaves the sweeps' alone."""
+    import shutil
+    files = sorted({f for v in bench.KERNEL_SOURCES.values() for f in v})
+    for f in files:
+        shutil.copy(os.path.join(bench.CSRC, f), tmp_path / f)
+    table = {k: (1.0 + i, bench.sources_digest(bench.KERNEL_SOURCES[("f32b", k)], str(tmp_path)))
+             for i, k in enumerate(("rhs", "explicit", "x_sweep", "y_sweep"))}
+    before = bench.current_counters(table, "f32b", str(tmp_path))
+    assert before == {"rhs": 1.0, "explicit": 2.0, "x_sweep": 3.0, "y_sweep": 4.0}
+    with open(tmp_path / "tf_rhs_packed.cuh", "a") as fh:
+        fh.write("// edited\n")
+    after = bench.current_counters(table, "f32b", str(tmp_path))
+    assert after == {"rhs": None, "explicit": None, "x_sweep": 3.0, "y_sweep": 4.0}
+    # a kernel counted on other sources, or never counted, reads null
+    assert bench.current_counters({"x_sweep": (5.0, "0" * 16), "y_sweep": (None, None)}, "f32b") == \
+        {"x_sweep": None, "y_sweep": None}
