@@ -530,10 +530,10 @@ def run_ensemble(args, w):
             g.copy_(h)
         torch.cuda.synchronize()
 
-    def timed(ctxs, clocks=None):
+    def timed(ctxs, clocks=None, engine=tf.TF_ENSEMBLE_AUTO):
         # warm-up: W attempts per film, then the timed run from the initial films
         reset()
-        tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, dt0, args.warmup)
+        tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, dt0, args.warmup, engine=engine)
         for c in ctxs:
             tf.tf_timing_enable(c, True)
         reset()
@@ -542,7 +542,7 @@ def run_ensemble(args, w):
         if clocks:
             clocks.__enter__()
         e0.record()
-        infos = tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, dt0, A)
+        infos = tf.tf_ensemble_advance(ctxs, grids, 0.0, 1e30, dt0, A, engine=engine)
         e1.record()
         torch.cuda.synchronize()
         if clocks:
@@ -561,6 +561,10 @@ def run_ensemble(args, w):
     infos, ms = timed(ctxs, clocks)
     launches = sum(tf.tf_timing_get(c)["launches"] for c in ctxs)
     cells = sum(f["N"] ** 2 * i["accepted"] for f, i in zip(films, infos))
+    # the same films and contexts on the host engine (the controller on the
+    # host, four threads polling the films' events): the same decisions
+    infos_h, ms_h = timed(ctxs, engine=tf.TF_ENSEMBLE_HOST)
+    assert infos_h == infos
     iters = sum(i["newton_iterations"] for i in infos)
     value = job_rate(dist, cells, ms)
     # the same films, one after another
@@ -582,6 +586,8 @@ def run_ensemble(args, w):
         accepted_steps=sum(i["accepted"] for i in infos), newton_iterations=iters,
         sequential_value=job_rate(dist, cells, ms_seq), speedup_vs_sequential=ms_seq / ms,
         fixed_shape_value=job_rate(dist, cells_fixed, ms_fixed),
+        engine="graph: each film's whole run one CUDA graph launch, Newton and step control on the device",
+        host_engine_value=job_rate(dist, cells, ms_h),
         line_solver_by_size={str(k): v for k, v in sorted(tuned.items())},
         gpu_launches=launches,
         clocks=dict(sm_mhz=cs["sm_mhz"], sm_max_mhz=cs["sm_max_mhz"], reasons=cs["reasons"]),

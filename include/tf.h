@@ -227,25 +227,43 @@ int tf_advance(tf_ctx* ctx, double* h, double t0, double t_end, double dt0,
                int max_attempts, const double* dt_replay, const int* iter_replay,
                tf_step_record* records, tf_advance_info* info, int* streak);
 
+/* Engines of tf_ensemble_advance. */
+#define TF_ENSEMBLE_AUTO 0  /* the graph engine for every film it serves, else the host engine */
+#define TF_ENSEMBLE_HOST 1  /* the host engine for every film                                   */
+
 /* Advance n independent films together.  Film i is advanced exactly as
  * tf_advance(ctx[i], h[i], t0[i], t_end[i], dt0[i], max_attempts[i], NULL,
  * NULL, NULL, &info[i]) would advance it -- the same kernels in the same
- * order, the same decisions, bit-identical grids -- but one host thread
- * keeps the work of all films queued on their contexts' streams at once,
- * so that the kernels of small films run side by side on the GPU (the
- * many-film statistics runs of Sec. Results; no counterpart in the paper's
- * implementation).  Give each context its own stream: contexts that share a
- * stream are correct but serialised.  ctx: n distinct contexts; h: n device
- * grids, each of its context's shape (advanced in place); t0, t_end, dt0,
+ * order, the same decisions, bit-identical grids -- with the work of all
+ * films queued on their contexts' streams at once, so that the kernels of
+ * small films run side by side on the GPU (the many-film statistics runs of
+ * Sec. Results; no counterpart in the paper's implementation).  Two
+ * engines:
+ *   graph engine (TF_ENSEMBLE_AUTO, for FP32-bulk contexts of the (3, 2)
+ *     power law on the twisted sweeps): each film's whole run is one launch
+ *     of a CUDA graph held by its context -- conditional WHILE nodes over
+ *     attempts and Newton iterations whose conditions one-thread controller
+ *     kernels set from the iteration's reductions, with the film's Δt and
+ *     Newton state in device memory.  The host waits once per film per
+ *     call.  The graph is built on the context's first such call (a few
+ *     milliseconds); that first call should come before any stream capture.
+ *     With timing enabled only tf_timing.launches is counted for these
+ *     films.
+ *   host engine (TF_ENSEMBLE_HOST, and every other context): the state
+ *     machine of tf_advance on the host, its waits on the GPU resumable, four
+ *     host threads polling the films' events.
+ * Give each context its own stream: contexts that share a stream are
+ * correct but serialised.  ctx: n distinct contexts; h: n device grids,
+ * each of its context's shape (advanced in place); t0, t_end, dt0,
  * max_attempts: n host values each; info: n host records, required;
  * streak: n host values (each film's accept streak, in and out, as in
- * tf_advance) or NULL.
+ * tf_advance) or NULL; engine: TF_ENSEMBLE_AUTO or TF_ENSEMBLE_HOST.
  * Returns TF_OK, or a negative error at the first failing call (work of
  * other films may then still be queued: synchronise or destroy the
  * contexts).                                                             */
 int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const double* t0,
                         const double* t_end, const double* dt0, const int* max_attempts,
-                        tf_advance_info* info, int* streak);
+                        tf_advance_info* info, int* streak, int engine);
 
 /* ---- line-solver tuning ---------------------------------------------------
  * The paper has no counterpart to this: it picks, per grid shape, the

@@ -139,7 +139,7 @@ def library(build_if_missing: bool = True):
                              C.POINTER(TfAdvanceInfo), C.POINTER(C.c_int)]
     L.tf_ensemble_advance.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(dp),
                                       C.POINTER(dp), C.POINTER(dp), C.POINTER(C.c_int),
-                                      C.POINTER(TfAdvanceInfo), C.POINTER(C.c_int)]
+                                      C.POINTER(TfAdvanceInfo), C.POINTER(C.c_int), C.c_int]
     L.tf_tune_line_solver.argtypes = [C.POINTER(TfParams), vp, vp, dp, C.c_int, C.c_int,
                                       C.POINTER(C.c_int), C.POINTER(dp)]
     L.tf_tuned_line_solver.argtypes = [C.POINTER(TfParams)]
@@ -362,12 +362,18 @@ def tf_tuned_line_solver(params: TfParams) -> int:
     return library().tf_tuned_line_solver(C.byref(params))
 
 
-def tf_ensemble_advance(ctxs, hs, t0, t_end, dt0, max_attempts, streak=0):
+TF_ENSEMBLE_AUTO = 0
+TF_ENSEMBLE_HOST = 1
+
+
+def tf_ensemble_advance(ctxs, hs, t0, t_end, dt0, max_attempts, streak=0, engine=TF_ENSEMBLE_AUTO):
     """Advance independent films together (``tf_advance`` on each, their
     work interleaved on the contexts' streams).  ``ctxs``: contexts, one per
     film, each best on its own stream; ``hs``: their grids (advanced in
     place); ``t0``, ``t_end``, ``dt0``, ``max_attempts``, ``streak``: one
-    value or one per film.  Returns one info dict per film (with its
+    value or one per film; ``engine``: TF_ENSEMBLE_AUTO (each film's run as
+    one CUDA graph with its controller on the device, where the context
+    allows it) or TF_ENSEMBLE_HOST.  Returns one info dict per film (with its
     ``streak`` at the end)."""
     n = len(ctxs)
     if len(hs) != n:
@@ -384,7 +390,8 @@ def tf_ensemble_advance(ctxs, hs, t0, t_end, dt0, max_attempts, streak=0):
     infos = (TfAdvanceInfo * max(1, n))()
     st = arr(streak, C.c_int)
     _check(library().tf_ensemble_advance(n, ctx_a, h_a, arr(t0, C.c_double), arr(t_end, C.c_double),
-                                         arr(dt0, C.c_double), arr(max_attempts, C.c_int), infos, st),
+                                         arr(dt0, C.c_double), arr(max_attempts, C.c_int), infos, st,
+                                         int(engine)),
            "tf_ensemble_advance")
     return [dict(status=i.status, attempts=i.attempts, accepted=i.accepted,
                  newton_iterations=i.newton_iterations, t=i.t, dt=i.dt, streak=st[k])

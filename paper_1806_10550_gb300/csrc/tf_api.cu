@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "tf_internal.h"
+#include "tf_ensemble_dev.cuh"
 
 using tf::Scalars;
 
@@ -435,6 +436,9 @@ void tf_destroy(tf_ctx* c) {
   cudaFree(c->py);
   cudaFree(c->dsc);
   if (c->hsc) cudaFreeHost(c->hsc);
+  if (c->ens_exec) cudaGraphExecDestroy(c->ens_exec);
+  cudaFree(c->ens_dev);
+  if (c->ens_host) cudaFreeHost(c->ens_host);
   for (int k = 0; k < 8; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   free(c);
@@ -705,16 +709,90 @@ int tf_advance(tf_ctx* c, double* h, double t0, double t_end, double dt0, int ma
   return TF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Graph engine: a film's whole run as one launch of its context's graph
+// (tf_ensemble_dev.cuh), with the controller state staged through pinned
+// memory before and after it.
+
+bool graph_capable(const tf_ctx& c) { return c.ops->ens_graph && c.packed_rhs && !c.part; }
+
+int film_graph_start(tf_ctx& c, double* h, double t0, double t_end, double dt0, int max_att, int streak) {
+  if (!c.ens_exec) {
+    int r = dalloc((void**)&c.ens_dev, sizeof(tf::EnsDev));
+    if (r) return r;
+    if (!c.ens_host) TF_CK(cudaMallocHost((void**)&c.ens_host, sizeof(tf::EnsDev)));
+    TF_CK(c.ops->ens_graph(c, c.ens_dev, &c.ens_exec));
+  }
+  tf::EnsDev& e = *c.ens_host;
+  memset(&e, 0, sizeof(e));
+  const tf_params& P = c.p;
+  e.p.cur = h;
+  e.p.nxt = c.ubuf2;
+  e.ubuf = c.ubuf;
+  e.M = c.mk;
+  e.theta = P.theta;
+  e.tol = P.newton_tol;
+  e.dt_max = P.dt_max;
+  e.dt_min = P.dt_min;
+  e.dt_grow = P.dt_grow;
+  e.dt_shrink = P.dt_shrink;
+  e.rupture_h = P.rupture_h;
+  e.grow_after = P.grow_after;
+  e.max_iter = P.newton_max_iter;
+  e.fixed_iter = P.newton_fixed_iter;
+  e.t = t0;
+  e.t_end = t_end;
+  e.dt = dt0;
+  e.max_att = max_att;
+  e.streak = streak;
+  e.status = TF_ADV_MAX_ATTEMPTS;
+  TF_CK(cudaMemcpyAsync(c.ens_dev, &e, sizeof(e), cudaMemcpyHostToDevice, c.stream));
+  TF_CK(cudaGraphLaunch(c.ens_exec, c.stream));
+  TF_CK(cudaMemcpyAsync(c.ens_host, c.ens_dev, sizeof(e), cudaMemcpyDeviceToHost, c.stream));
+  return TF_OK;
+}
+
+// After the graph: what film_finish does, from the staged state.
+int film_graph_finish(tf_ctx& c, double* h, tf_advance_info* info, int* streak_io) {
+  TF_CK(cudaStreamSynchronize(c.stream));
+  const tf::EnsDev& e = *c.ens_host;
+  int status = e.status;
+  if (status == TF_ADV_MAX_ATTEMPTS && e.t >= e.t_end) status = TF_ADV_DONE;
+  if (e.p.cur != h) {
+    TF_CK(cudaMemcpyAsync(h, e.p.cur, c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    TF_CK(cudaStreamSynchronize(c.stream));
+  }
+  memset(info, 0, sizeof(*info));
+  info->status = status;
+  info->attempts = e.a;
+  info->accepted = e.accepted;
+  info->newton_iterations = e.newton_iterations;
+  info->t = e.t;
+  info->dt = e.dt;
+  if (streak_io) *streak_io = e.streak;
+  if (c.timing.enabled) c.timing.launches += (int)e.kernels;
+  return TF_OK;
+}
+
 int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const double* t0,
                         const double* t_end, const double* dt0, const int* max_attempts,
-                        tf_advance_info* info, int* streak) {
+                        tf_advance_info* info, int* streak, int engine) {
   if (n < 0 || (n > 0 && (!ctx || !h || !t0 || !t_end || !dt0 || !max_attempts || !info)))
     return TF_ERR_ARG;
+  if (engine != TF_ENSEMBLE_AUTO && engine != TF_ENSEMBLE_HOST) return TF_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     if (!ctx[i] || !h[i] || max_attempts[i] < 0 || !(dt0[i] > 0.0) || !isfinite(t0[i])) return TF_ERR_ARG;
     if (streak && streak[i] < 0) return TF_ERR_ARG;
     for (int j = 0; j < i; ++j)
       if (ctx[j] == ctx[i]) return TF_ERR_ARG;  // one context per film
+  }
+  // films on the graph engine: launched first, collected at the end
+  std::vector<char> on_graph((size_t)n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (engine != TF_ENSEMBLE_AUTO || !graph_capable(*ctx[i])) continue;
+    on_graph[(size_t)i] = 1;
+    int r = film_graph_start(*ctx[i], h[i], t0[i], t_end[i], dt0[i], max_attempts[i], streak ? streak[i] : 0);
+    if (r) return r;
   }
   std::vector<FilmRun> F((size_t)n);
   int active = 0;
@@ -722,6 +800,10 @@ int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const doubl
     FilmRun& f = F[(size_t)i];
     memset(&f, 0, sizeof(f));
     f.c = ctx[i];
+    if (on_graph[(size_t)i]) {
+      f.done = true;
+      continue;
+    }
     f.h = h[i];
     f.t = t0[i];
     f.t_end = t_end[i];
@@ -780,6 +862,11 @@ int tf_ensemble_advance(int n, tf_ctx* const* ctx, double* const* h, const doubl
   for (int e : err)
     if (e) return e;
   for (FilmRun& f : F) TF_CK(cudaStreamSynchronize(f.c->stream));
+  for (int i = 0; i < n; ++i) {
+    if (!on_graph[(size_t)i]) continue;
+    int r = film_graph_finish(*ctx[i], h[i], &info[i], streak ? &streak[i] : nullptr);
+    if (r) return r;
+  }
   return TF_OK;
 }
 

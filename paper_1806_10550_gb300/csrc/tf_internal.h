@@ -20,6 +20,8 @@ struct tf_ctx;
 
 namespace tf {
 
+struct EnsDev;
+
 struct Ops {
   size_t hp_bytes, lp_bytes;
   cudaError_t (*prepare)();
@@ -31,6 +33,9 @@ struct Ops {
   cudaError_t (*xsweep)(tf_ctx& c, double dt, const double* u_k);
   cudaError_t (*ysweep)(tf_ctx& c, const double* u_k, double dt, double* u_next, double* v_out);
   cudaError_t (*w_to_f64)(tf_ctx& c, double* out);
+  // The graph of a whole ensemble film run (tf_ensemble_dev.cuh) for
+  // contexts on the FP32-bulk power-law twisted path; NULL for the others.
+  cudaError_t (*ens_graph)(tf_ctx& c, EnsDev* e, cudaGraphExec_t* out);
 };
 
 extern const Ops ops_fp64;
@@ -117,4 +122,8 @@ struct tf_ctx {
   int expl_kernels;   // kernels the last explicit-part launch queued
   void* adj_ws;       // workspace of tf_adjoint_step (grown on demand)
   size_t adj_bytes;
+  // graph engine of tf_ensemble_advance (built on first use)
+  tf::EnsDev* ens_dev;        // the film's device-resident controller state
+  tf::EnsDev* ens_host;       // pinned staging copy of it
+  cudaGraphExec_t ens_exec;   // the instantiated graph of a whole run
 };

@@ -196,7 +196,7 @@ template <class T> struct LineK {
   // Laplacian left unscaled), D1 = k1 B1 / h^2
   T pF0, pF1a, pF1b, pD0, pD1;
 };
-template <class T> inline LineK<T> line_consts(const ModelK& M, const StepK& K) {
+template <class T> TF_HD LineK<T> line_consts(const ModelK& M, const StepK& K) {
   LineK<T> L;
   L.ml = mob_consts<T>(M);
   L.inv_ds2 = (T)M.inv_ds2;
@@ -662,7 +662,9 @@ static __global__ void __launch_bounds__(256)
 
 // Mass and minimum of a grid (for tf_residual's norms).
 static __global__ void __launch_bounds__(256)
-    k_grid_stats(const double* __restrict__ u, size_t N, PartY* __restrict__ part) {
+    k_grid_stats(const double* __restrict__ u, size_t N, PartY* __restrict__ part,
+                 const double* const* __restrict__ up = nullptr) {
+  if (up) u = *up;  // the grid named by a device-resident pointer (ensemble graphs)
   // min over positive values through their bit patterns (integer compares)
   unsigned long long hb = 0x7ff0000000000000ull;
   Mass128 m = {0ull, 0ull};

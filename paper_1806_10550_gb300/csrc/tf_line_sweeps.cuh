@@ -133,6 +133,10 @@ __device__ __forceinline__ void copy_span(T* dst, const T* __restrict__ src, int
   }
 }
 
+// a * b rounded on its own: never contracted with a following add
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Per-cell film values, pre-scaled for the band: with k3 = theta dt/(2 ds^4)
 // and k1 = theta dt/(2 ds^2),
 //   F0 = k3 f0, F1 = k1 f1, D0 = k1 f0', D1 = k1 f1',
@@ -170,8 +174,11 @@ __device__ __forceinline__ CellS<LP> cell_pl32(const LineK<LP>& L, Acc U) {
   X.u = uc;
   X.lap = ((U(0, 1) - uc) + (U(0, -1) - uc)) + ((U(1, 0) - uc) + (U(-1, 0) - uc));
   const LP s = rcp(uc), h2 = uc * uc;
-  X.F0 = L.pF0 * (h2 * uc);
-  X.F1 = L.pF1a - L.pF1b * s;
+  // F0 rounded as a product of its own (never fused into the face sums
+  // F0_p + F0_q) and F1 as one written-out fma: every instantiation of the
+  // sweeps then rounds the band alike
+  X.F0 = mul_rn(L.pF0, h2 * uc);
+  X.F1 = fma(-L.pF1b, s, L.pF1a);
   X.D0 = L.pD0 * h2;
   X.D1 = L.pD1 * (s * s);
   return X;
@@ -182,7 +189,9 @@ __device__ __forceinline__ void face_scaled(const CellS<LP>& P, const CellS<LP>&
                                             LP dF[4]) {
   const LP dl = Q.lap - P.lap, du = Q.u - P.u;
   const LP c3 = P.F0 + Q.F0, Bd = P.F1 + Q.F1;
-  const LP tp = P.D0 * dl + P.D1 * du, tq = Q.D0 * dl + Q.D1 * du;
+  // one fused form, written out, so that every instantiation of the sweeps
+  // rounds these alike (a * b + c * d may otherwise fuse either product)
+  const LP tp = fma(P.D0, dl, P.D1 * du), tq = fma(Q.D0, dl, Q.D1 * du);
   if (pl && qr) {
     dF[0] = -c3;
     dF[1] = LP(3) * c3 + (tp - Bd);
@@ -330,13 +339,19 @@ template <class LP> struct YSmem {
   PartY part[kSweepThreads / 32];
 };
 
-template <class Mode>
+// DEV (the ensemble graphs): the step's band constants *Ld and the
+// iterates {u_k, u_k+1} = uio[0], uio[1] come from device memory.
+template <class Mode, bool DEV = false>
 __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
-    k_ysweep(ModelK M, LineK<typename Mode::LP> L, const double* __restrict__ u,
+    k_ysweep(ModelK M, LineK<typename Mode::LP> Lp, const double* __restrict__ up,
              const typename Mode::LP* __restrict__ ul, const typename Mode::LP* __restrict__ w,
-             typename Mode::LP* __restrict__ fac, double* __restrict__ unew, double* __restrict__ vout,
-             PartY* __restrict__ part) {
+             typename Mode::LP* __restrict__ fac, double* __restrict__ unp, double* __restrict__ vout,
+             PartY* __restrict__ part, const LineK<typename Mode::LP>* __restrict__ Ld = nullptr,
+             const double* const* __restrict__ uio = nullptr) {
   typedef typename Mode::LP LP;
+  const LineK<LP>& L = DEV ? *Ld : Lp;
+  const double* __restrict__ u = DEV ? uio[0] : up;
+  double* __restrict__ unew = DEV ? const_cast<double*>(uio[1]) : unp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   YSmem<LP>& S = *reinterpret_cast<YSmem<LP>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -608,12 +623,15 @@ template <class LP> struct XSmem {
   int piv[kSweepThreads / 32];
 };
 
-template <class Mode>
+// DEV (the ensemble graphs): the step's band constants *Ld come from device
+// memory.
+template <class Mode, bool DEV = false>
 __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
-    k_xsweep(ModelK M, LineK<typename Mode::LP> L, const typename Mode::LP* __restrict__ ul,
+    k_xsweep(ModelK M, LineK<typename Mode::LP> Lp, const typename Mode::LP* __restrict__ ul,
              typename Mode::LP* __restrict__ rw, typename Mode::LP* __restrict__ fac,
-             PartX* __restrict__ part) {
+             PartX* __restrict__ part, const LineK<typename Mode::LP>* __restrict__ Ld = nullptr) {
   typedef typename Mode::LP LP;
+  const LineK<LP>& L = DEV ? *Ld : Lp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   XSmem<LP>& S = *reinterpret_cast<XSmem<LP>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

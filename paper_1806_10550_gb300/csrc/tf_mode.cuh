@@ -6,6 +6,7 @@
 
 #include "tf_internal.h"
 #include "tf_rhs_packed.cuh"
+#include "tf_ensemble_dev.cuh"
 
 static_assert(tf::kRhsStripCols == tf::kSW && tf::kRhsStripWarps == tf::kSWarps, "residual strips of the launch grid");
 
@@ -45,6 +46,11 @@ template <class Mode> struct Launch {
     if ((e = cudaFuncSetAttribute(k_rhs<Mode, kRhsBoth>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     if constexpr (kF32B) {
       if ((e = part::prepare())) return e;
+      // the sweeps of the ensemble graphs (constants from device memory)
+      if ((e = cudaFuncSetAttribute(k_xsweep<Mode, true>, A, (int)smem_x))) return e;
+      if ((e = cudaFuncSetAttribute(k_ysweep<Mode, true>, A, (int)smem_y))) return e;
+      if ((e = cudaFuncSetAttribute(k_xsweep<Mode, true>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
+      if ((e = cudaFuncSetAttribute(k_ysweep<Mode, true>, C, (int)cudaSharedmemCarveoutMaxShared))) return e;
     }
     return cudaFuncSetAttribute(k_rhs<Mode, kRhsResidual>, C, (int)cudaSharedmemCarveoutMaxShared);
   }
@@ -125,6 +131,87 @@ template <class Mode> struct Launch {
                                                        (LP*)c.fac_y, u_next, v_out, c.py);
     return cudaGetLastError();
   }
+  // The whole run of an ensemble film as one graph (FP32-bulk, (3, 2) power
+  // law, twisted sweeps): k_ens_begin, then WHILE (attempts) { explicit part
+  // with the first residual; WHILE (iterations) { residual, x sweep, y sweep,
+  // reductions, k_ens_iter }; copy of the result, film statistics,
+  // reductions, k_ens_step }.  The kernels are those of a tf_advance step,
+  // with their constants and grids read from e.
+  static cudaError_t ens_graph_c(tf_ctx& c, EnsDev* e, cudaGraphExec_t* out) {
+    if constexpr (!kF32B) {
+      return cudaErrorNotSupported;
+    } else {
+      if (!c.packed_rhs || c.part) return cudaErrorNotSupported;
+      cudaStream_t s = nullptr;
+      cudaGraph_t g = nullptr, B = nullptr, I = nullptr;
+      cudaError_t err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      if (err) return err;
+      const cudaStreamCaptureMode md = cudaStreamCaptureModeRelaxed;
+      const StripK rk0 = strip_consts(c.mk, step(c, 1.0), false);  // placeholders: read from e
+      const LineK<LP> l0 = line_consts<LP>(c.mk, step(c, 1.0));
+      cudaGraphConditionalHandle ho, hi;
+      cudaGraphNode_t nb = nullptr, no = nullptr, nx = nullptr, ni = nullptr;
+      size_t one = 1;
+      auto fail = [&](cudaError_t x) {
+        cudaStreamDestroy(s);
+        if (g) cudaGraphDestroy(g);
+        return x;
+      };
+      if ((err = cudaGraphCreate(&g, 0))) return fail(err);
+      if ((err = cudaGraphConditionalHandleCreate(&ho, g, 0, cudaGraphCondAssignDefault))) return fail(err);
+      // top level: the first attempt
+      if ((err = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, md))) return fail(err);
+      k_ens_begin<<<1, 1, 0, s>>>(e, ho);
+      if ((err = cudaStreamEndCapture(s, &g))) return fail(err);
+      if ((err = cudaGraphGetNodes(g, &nb, &one)) || one != 1) return fail(err ? err : cudaErrorUnknown);
+      cudaGraphNodeParams po = {};
+      po.type = cudaGraphNodeTypeConditional;
+      po.conditional.handle = ho;
+      po.conditional.type = cudaGraphCondTypeWhile;
+      po.conditional.size = 1;
+      if ((err = cudaGraphAddNode(&no, g, &nb, nullptr, 1, &po))) return fail(err);
+      B = po.conditional.phGraph_out[0];
+      // attempt: the explicit part with the first iteration's residual
+      if ((err = cudaGraphConditionalHandleCreate(&hi, B, 1, cudaGraphCondAssignDefault))) return fail(err);
+      if ((err = cudaStreamBeginCaptureToGraph(s, B, nullptr, nullptr, 0, md))) return fail(err);
+      k_rhs_strip<kRhsBoth, true><<<c.grid_pkx, kST, 0, s>>>(c.mk, rk0, nullptr, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px,
+                                                       c.strip_n, c.strip_rows, &e->rk_both, &e->p.cur, nullptr);
+      if ((err = cudaStreamEndCapture(s, &B))) return fail(err);
+      one = 1;
+      if ((err = cudaGraphGetNodes(B, &nx, &one)) || one != 1) return fail(err ? err : cudaErrorUnknown);
+      cudaGraphNodeParams pi = {};
+      pi.type = cudaGraphNodeTypeConditional;
+      pi.conditional.handle = hi;
+      pi.conditional.type = cudaGraphCondTypeWhile;
+      pi.conditional.size = 1;
+      if ((err = cudaGraphAddNode(&ni, B, &nx, nullptr, 1, &pi))) return fail(err);
+      I = pi.conditional.phGraph_out[0];
+      // Newton iteration
+      if ((err = cudaStreamBeginCaptureToGraph(s, I, nullptr, nullptr, 0, md))) return fail(err);
+      k_rhs_strip<kRhsResidual, true><<<c.grid_pkx, kST, 0, s>>>(c.mk, rk0, nullptr, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp,
+                                                           c.px, c.strip_n, c.strip_rows, &e->rk_res, &e->p.uk,
+                                                           &e->k);
+      k_xsweep<Mode, true><<<c.grid_x, kSweepThreads, smem_x, s>>>(c.mk, l0, (const LP*)c.ulp, (LP*)c.w, (LP*)c.fac_x,
+                                                           c.px + c.n_rhs_parts, &e->line);
+      k_ysweep<Mode, true><<<c.grid_y, kSweepThreads, smem_y, s>>>(c.mk, l0, nullptr, (const LP*)c.ulp, (const LP*)c.w,
+                                                           (LP*)c.fac_y, nullptr, nullptr, c.py, &e->line,
+                                                           &e->p.uk);
+      k_finalize<<<1, 256, 0, s>>>(c.px, c.n_rhs_parts + c.grid_x, c.py, c.grid_y, c.dsc);
+      k_ens_iter<<<1, 1, 0, s>>>(e, c.dsc, hi);
+      if ((err = cudaStreamEndCapture(s, &I))) return fail(err);
+      // end of the attempt: the result into nxt, its statistics, the controller
+      if ((err = cudaStreamBeginCaptureToGraph(s, B, &ni, nullptr, 1, md))) return fail(err);
+      k_ens_copy<<<1024, 256, 0, s>>>(e, c.N);
+      k_grid_stats<<<c.grid_stats, 256, 0, s>>>(nullptr, c.N, c.py, &e->p.nxt);
+      k_finalize<<<1, 256, 0, s>>>(c.px, 0, c.py, c.grid_stats, c.dsc);
+      k_ens_step<<<1, 1, 0, s>>>(e, c.dsc, ho, hi);
+      if ((err = cudaStreamEndCapture(s, &B))) return fail(err);
+      if ((err = cudaGraphInstantiate(out, g, 0))) return fail(err);
+      cudaGraphDestroy(g);
+      cudaStreamDestroy(s);
+      return cudaSuccess;
+    }
+  }
   static cudaError_t w_to_f64_c(tf_ctx& c, double* out) {
     if (sizeof(LP) == sizeof(double))
       return cudaMemcpyAsync(out, c.w, c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
@@ -146,6 +233,7 @@ template <class Mode> Ops make_ops() {
   o.xsweep = &L::xsweep_c;
   o.ysweep = &L::ysweep_c;
   o.w_to_f64 = &L::w_to_f64_c;
+  o.ens_graph = L::kF32B ? &L::ens_graph_c : nullptr;
   return o;
 }
 

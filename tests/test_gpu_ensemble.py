@@ -84,6 +84,44 @@ def test_ensemble_matches_per_film_advance(torch, mode, mixed):
     assert infos[6]["attempts"] == 0
 
 
+def test_graph_engine_matches_host_engine(torch):
+    """The graph engine (each film's run one CUDA graph, its controller on
+    the device) against the host engine on the same FP32-bulk films: the
+    same infos and bit-identical grids, over a first call and a second call
+    on the same contexts (the graphs reused) that continues from the first
+    call's t, dt and streak."""
+    runs = {}
+    for engine in (tf.TF_ENSEMBLE_HOST, tf.TF_ENSEMBLE_AUTO):
+        ctxs, grids, t_end, dt0, att = [], [], [], [], []
+        for nx, ny, th, seed, fdt, fend, na in FILMS:
+            p, sm, _, _ = film_params(nx, ny, th, tf.TF_FP32_BULK)
+            ctxs.append(tf.Context(p, stream=torch.cuda.Stream()))
+            grids.append(dev(torch, S.spinodal_film(nx, ny, 1.0, 0.01, seed=seed)))
+            t_end.append(fend / sm)
+            dt0.append(fdt / sm)
+            att.append(na)
+        for c in ctxs:
+            tf.tf_timing_enable(c, True)
+        first = tf.tf_ensemble_advance(ctxs, grids, 0.0, t_end, dt0, att, engine=engine)
+        g1 = [host(g).copy() for g in grids]
+        timing = [tf.tf_timing_get(c) for c in ctxs]
+        second = tf.tf_ensemble_advance(ctxs, grids, [i["t"] for i in first], t_end, [i["dt"] for i in first],
+                                        [max(1, a // 2) for a in att], streak=[i["streak"] for i in first],
+                                        engine=engine)
+        runs[engine] = (first, g1, second, [host(g) for g in grids], timing)
+    h1, hg1, h2, hg2, ht = runs[tf.TF_ENSEMBLE_HOST]
+    a1, ag1, a2, ag2, at = runs[tf.TF_ENSEMBLE_AUTO]
+    assert a1 == h1 and a2 == h2
+    for i in range(len(FILMS)):
+        assert np.array_equal(ag1[i], hg1[i]), i
+        assert np.array_equal(ag2[i], hg2[i]), i
+        # which engine ran: the graph engine counts launches but times no kernel
+        if FILMS[i][6] > 0:
+            assert at[i]["launches"] > 0 and at[i]["x_launches"] == 0, (i, at[i])
+            assert ht[i]["x_launches"] > 0, (i, ht[i])
+    assert sum(i["attempts"] for i in a2) > 0
+
+
 def test_ensemble_film_matches_oracle(torch):
     nx, ny, th, seed, fdt, fend, na = FILMS[2]
     p, sm, kappa, ds = film_params(nx, ny, th, tf.TF_FP64)
