@@ -122,6 +122,41 @@ def test_graph_engine_matches_host_engine(torch):
     assert sum(i["attempts"] for i in a2) > 0
 
 
+def test_graph_engine_stops_as_tf_advance(torch):
+    """The graph engine's other exits, each against the host engine: a film
+    that ruptures (min h below rupture_h after its first accepted step), one
+    whose step size falls below dt_min after rejections, and one on a fixed
+    iteration count."""
+    def film(engine, mutate, fdt):
+        p, sm, _, _ = film_params(40, 32, 25.0, tf.TF_FP32_BULK)
+        mutate(p, sm)
+        ctx = tf.Context(p, stream=torch.cuda.Stream())
+        g = dev(torch, S.spinodal_film(40, 32, 1.0, 0.01, seed=11))
+        info = tf.tf_ensemble_advance([ctx], [g], 0.0, 1e30, fdt / sm, 30, engine=engine)[0]
+        return info, host(g)
+
+    def rupture(p, sm):
+        p.rupture_h = 0.999
+
+    def dt_floor(p, sm):  # one iteration never meets the tolerance: 5, 2.5, 1.25, then 0.625 < dt_min
+        p.newton_max_iter = 1
+        p.dt_min = 1.0 / sm
+
+    def fixed(p, sm):
+        p.newton_fixed_iter = 3
+
+    for mutate, fdt, status in ((rupture, 1e-3, tf.TF_ADV_RUPTURE), (dt_floor, 5.0, tf.TF_ADV_DT_MIN),
+                                (fixed, 1e-3, None)):
+        ih, gh = film(tf.TF_ENSEMBLE_HOST, mutate, fdt)
+        ia, ga = film(tf.TF_ENSEMBLE_AUTO, mutate, fdt)
+        assert ia == ih, (mutate.__name__, ia, ih)
+        assert np.array_equal(ga, gh), mutate.__name__
+        if status is not None:
+            assert ia["status"] == status, (mutate.__name__, ia)
+        else:
+            assert ia["newton_iterations"] == 3 * ia["attempts"] > 0
+
+
 def test_ensemble_film_matches_oracle(torch):
     nx, ny, th, seed, fdt, fend, na = FILMS[2]
     p, sm, kappa, ds = film_params(nx, ny, th, tf.TF_FP64)
