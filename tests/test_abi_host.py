@@ -128,6 +128,9 @@ def test_null_arguments_rejected():
     assert L.tf_tape_backward(None, None, None, None, None) == tf.TF_ERR_ARG
     assert L.tf_tape_timing(None, None, 0) == tf.TF_ERR_ARG
     L.tf_tape_destroy(None)
+    # the ensemble call: a negative count, and an engine that does not exist
+    assert L.tf_ensemble_advance(-1, None, None, None, None, None, None, None, None, tf.TF_ENSEMBLE_AUTO) == tf.TF_ERR_ARG
+    assert L.tf_ensemble_advance(0, None, None, None, None, None, None, None, None, 7) == tf.TF_ERR_ARG
 
 
 def test_no_cpu_fallback_without_gpu():
