@@ -3,10 +3,11 @@
 //
 // tf_advance's controller and the Newton loop of a time step (Sec. Adaptive
 // Time Stepping, Fig. FlowChartTime; the pseudo-Newton iteration of eqs.
-// JacobianSystem1-3) move into device memory and three one-thread kernels,
-// so that a film's whole run is one CUDA graph: an outer conditional WHILE
-// over attempts and an inner one over Newton iterations, whose conditions
-// these kernels set.  Every decision is the host's, made with the same
+// JacobianSystem1-3) move into device memory and into k_ens_begin and the
+// two reduction kernels k_ens_iter and k_ens_step, which finish with the
+// controller in their thread 0, so that a film's whole run is one CUDA graph:
+// an outer conditional WHILE over attempts and an inner one over the Newton
+// iterations after the first, whose conditions these kernels set.  Every decision is the host's, made with the same
 // double arithmetic on the same scalars (the reductions' Scalars in device
 // memory), so a film advanced here takes the steps, iteration counts and
 // bits that tf_advance gives it.  The kernels of the path read the step's
@@ -87,22 +88,28 @@ __device__ __forceinline__ bool ens_start_attempt(EnsDev& e) {
   return true;
 }
 
-// Before the outer loop: the first attempt.
+// Before the outer loop: the first attempt.  (The kernel counts below are
+// the graph's launches for this film: this kernel; per iteration the x and
+// y sweeps and the reductions, and the residual from the second on; per
+// attempt the explicit part, the copy, the statistics and their reductions.)
 static __global__ void k_ens_begin(EnsDev* __restrict__ e, cudaGraphConditionalHandle outer) {
   e->kernels += 1;
   cudaGraphSetConditional(outer, ens_start_attempt(*e) ? 1u : 0u);
 }
 
-// After a Newton iteration's reductions: classify it as step() does, and
-// either run the next iteration (into the other iterate buffer) or end the
-// step.
-static __global__ void k_ens_iter(EnsDev* __restrict__ e, const Scalars* __restrict__ s,
-                                  cudaGraphConditionalHandle inner) {
+// A Newton iteration's reductions (k_finalize's), then in thread 0: classify
+// the iteration as step() does, and either run the next iteration (into the
+// other iterate buffer) or end the step.
+static __global__ void __launch_bounds__(256)
+    k_ens_iter(const PartX* __restrict__ px, int nx_part, const PartY* __restrict__ py, int ny_part,
+               Scalars* __restrict__ out, EnsDev* __restrict__ e, cudaGraphConditionalHandle inner) {
+  if (!finalize_block(px, nx_part, py, ny_part, out)) return;
   EnsDev& E = *e;
-  E.kernels += 5;  // residual (returns at once in iteration 0), x sweep, y sweep, reductions, this
+  const Scalars s = *out;
+  E.kernels += E.k == 0 ? 3 : 4;
   E.it = E.k + 1;
   E.p.uk = E.p.un;
-  E.sstatus = ens_classify(*s, E.it, E.fixed_iter, E.tol);
+  E.sstatus = ens_classify(s, E.it, E.fixed_iter, E.tol);
   ++E.k;
   const bool more = E.sstatus == TF_STEP_NOT_CONVERGED && E.k < E.kmax;
   if (more) E.p.un = (E.k & 1) ? E.ubuf : E.p.nxt;
@@ -118,13 +125,17 @@ static __global__ void __launch_bounds__(256) k_ens_copy(const EnsDev* __restric
     dst[k] = src[k];
 }
 
-// After the step's film statistics: tf_advance's controller (accept or
-// reject, Δt growth after grow_after accepted steps in a row, rupture, Δt
-// floor), then the next attempt.  Re-arms the inner loop.
-static __global__ void k_ens_step(EnsDev* __restrict__ e, const Scalars* __restrict__ s,
-                                  cudaGraphConditionalHandle outer, cudaGraphConditionalHandle inner) {
+// The step's film statistics (k_finalize's reduction of k_grid_stats), then
+// in thread 0 tf_advance's controller (accept or reject, Δt growth after
+// grow_after accepted steps in a row, rupture, Δt floor) and the next
+// attempt.
+static __global__ void __launch_bounds__(256)
+    k_ens_step(const PartY* __restrict__ py, int ny_part, Scalars* __restrict__ out, EnsDev* __restrict__ e,
+               cudaGraphConditionalHandle outer) {
+  if (!finalize_block(nullptr, 0, py, ny_part, out)) return;
   EnsDev& E = *e;
-  E.kernels += 5;  // explicit part, copy, statistics, reductions, this
+  const Scalars* s = out;
+  E.kernels += 4;
   ++E.a;
   E.newton_iterations += E.it;
   bool go = false;
@@ -154,7 +165,6 @@ static __global__ void k_ens_step(EnsDev* __restrict__ e, const Scalars* __restr
       go = ens_start_attempt(E);
     }
   }
-  cudaGraphSetConditional(inner, 1u);
   cudaGraphSetConditional(outer, go ? 1u : 0u);
 }
 

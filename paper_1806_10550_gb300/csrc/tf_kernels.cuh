@@ -609,9 +609,11 @@ __device__ __forceinline__ bool positive_finite_bits(double u) {
 // ---------------------------------------------------------------------------
 // Reductions over the per-block partials (one block, fixed order).
 
-static __global__ void __launch_bounds__(256)
-    k_finalize(const PartX* __restrict__ px, int nx_part, const PartY* __restrict__ py, int ny_part,
-               Scalars* __restrict__ out) {
+// The reduction of the per-block partials into the iteration's scalars by
+// one block of 256 threads: thread 0 writes *out and returns true.
+__device__ __forceinline__ bool finalize_block(const PartX* __restrict__ px, int nx_part,
+                                               const PartY* __restrict__ py, int ny_part,
+                                               Scalars* __restrict__ out) {
   __shared__ double s_err[256], s_g[256], s_h[256];
   __shared__ Mass128 s_m[256];
   __shared__ int s_nf[256], s_pv[256];
@@ -657,7 +659,15 @@ static __global__ void __launch_bounds__(256)
     s.nonfinite = s_nf[0];
     s.pivot = s_pv[0];
     *out = s;
+    return true;
   }
+  return false;
+}
+
+static __global__ void __launch_bounds__(256)
+    k_finalize(const PartX* __restrict__ px, int nx_part, const PartY* __restrict__ py, int ny_part,
+               Scalars* __restrict__ out) {
+  finalize_block(px, nx_part, py, ny_part, out);
 }
 
 // Mass and minimum of a grid (for tf_residual's norms).

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <type_traits>
+#include <vector>
 
 #include "tf_internal.h"
 #include "tf_rhs_packed.cuh"
@@ -133,10 +134,12 @@ template <class Mode> struct Launch {
   }
   // The whole run of an ensemble film as one graph (FP32-bulk, (3, 2) power
   // law, twisted sweeps): k_ens_begin, then WHILE (attempts) { explicit part
-  // with the first residual; WHILE (iterations) { residual, x sweep, y sweep,
-  // reductions, k_ens_iter }; copy of the result, film statistics,
-  // reductions, k_ens_step }.  The kernels are those of a tf_advance step,
-  // with their constants and grids read from e.
+  // with the first residual, x sweep, y sweep, k_ens_iter (reductions and
+  // the iteration's classification); WHILE (further iterations) { residual,
+  // x sweep, y sweep, k_ens_iter }; copy of the result, film statistics,
+  // k_ens_step (their reductions and the step controller) }.  The kernels
+  // and their order are those of a tf_advance step, with their constants and
+  // grids read from e.
   static cudaError_t ens_graph_c(tf_ctx& c, EnsDev* e, cudaGraphExec_t* out) {
     if constexpr (!kF32B) {
       return cudaErrorNotSupported;
@@ -157,6 +160,15 @@ template <class Mode> struct Launch {
         if (g) cudaGraphDestroy(g);
         return x;
       };
+      // one Newton iteration's sweeps and reductions
+      auto sweeps = [&]() {
+        k_xsweep<Mode, true><<<c.grid_x, kSweepThreads, smem_x, s>>>(c.mk, l0, (const LP*)c.ulp, (LP*)c.w,
+                                                                     (LP*)c.fac_x, c.px + c.n_rhs_parts, &e->line);
+        k_ysweep<Mode, true><<<c.grid_y, kSweepThreads, smem_y, s>>>(c.mk, l0, nullptr, (const LP*)c.ulp,
+                                                                     (const LP*)c.w, (LP*)c.fac_y, nullptr, nullptr,
+                                                                     c.py, &e->line, &e->p.uk);
+        k_ens_iter<<<1, 256, 0, s>>>(c.px, c.n_rhs_parts + c.grid_x, c.py, c.grid_y, c.dsc, e, hi);
+      };
       if ((err = cudaGraphCreate(&g, 0))) return fail(err);
       if ((err = cudaGraphConditionalHandleCreate(&ho, g, 0, cudaGraphCondAssignDefault))) return fail(err);
       // top level: the first attempt
@@ -171,14 +183,25 @@ template <class Mode> struct Launch {
       po.conditional.size = 1;
       if ((err = cudaGraphAddNode(&no, g, &nb, nullptr, 1, &po))) return fail(err);
       B = po.conditional.phGraph_out[0];
-      // attempt: the explicit part with the first iteration's residual
-      if ((err = cudaGraphConditionalHandleCreate(&hi, B, 1, cudaGraphCondAssignDefault))) return fail(err);
+      // attempt: the explicit part with the first iteration's residual, and
+      // the first iteration
+      if ((err = cudaGraphConditionalHandleCreate(&hi, B, 0, cudaGraphCondAssignDefault))) return fail(err);
       if ((err = cudaStreamBeginCaptureToGraph(s, B, nullptr, nullptr, 0, md))) return fail(err);
       k_rhs_strip<kRhsBoth, true><<<c.grid_pkx, kST, 0, s>>>(c.mk, rk0, nullptr, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp, c.px,
-                                                       c.strip_n, c.strip_rows, &e->rk_both, &e->p.cur, nullptr);
+                                                             c.strip_n, c.strip_rows, &e->rk_both, &e->p.cur);
+      sweeps();
       if ((err = cudaStreamEndCapture(s, &B))) return fail(err);
-      one = 1;
-      if ((err = cudaGraphGetNodes(B, &nx, &one)) || one != 1) return fail(err ? err : cudaErrorUnknown);
+      {  // the last node of the chain: the one no other node depends on
+        size_t nn = 0, ne = 0;
+        if ((err = cudaGraphGetNodes(B, nullptr, &nn))) return fail(err);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if ((err = cudaGraphGetNodes(B, nodes.data(), &nn))) return fail(err);
+        for (cudaGraphNode_t n : nodes) {
+          if ((err = cudaGraphNodeGetDependentNodes(n, nullptr, nullptr, &ne))) return fail(err);
+          if (ne == 0) nx = n;
+        }
+        if (!nx) return fail(cudaErrorUnknown);
+      }
       cudaGraphNodeParams pi = {};
       pi.type = cudaGraphNodeTypeConditional;
       pi.conditional.handle = hi;
@@ -186,25 +209,17 @@ template <class Mode> struct Launch {
       pi.conditional.size = 1;
       if ((err = cudaGraphAddNode(&ni, B, &nx, nullptr, 1, &pi))) return fail(err);
       I = pi.conditional.phGraph_out[0];
-      // Newton iteration
+      // the iterations after the first
       if ((err = cudaStreamBeginCaptureToGraph(s, I, nullptr, nullptr, 0, md))) return fail(err);
       k_rhs_strip<kRhsResidual, true><<<c.grid_pkx, kST, 0, s>>>(c.mk, rk0, nullptr, (HP*)c.bn, (LP*)c.w, (LP*)c.ulp,
-                                                           c.px, c.strip_n, c.strip_rows, &e->rk_res, &e->p.uk,
-                                                           &e->k);
-      k_xsweep<Mode, true><<<c.grid_x, kSweepThreads, smem_x, s>>>(c.mk, l0, (const LP*)c.ulp, (LP*)c.w, (LP*)c.fac_x,
-                                                           c.px + c.n_rhs_parts, &e->line);
-      k_ysweep<Mode, true><<<c.grid_y, kSweepThreads, smem_y, s>>>(c.mk, l0, nullptr, (const LP*)c.ulp, (const LP*)c.w,
-                                                           (LP*)c.fac_y, nullptr, nullptr, c.py, &e->line,
-                                                           &e->p.uk);
-      k_finalize<<<1, 256, 0, s>>>(c.px, c.n_rhs_parts + c.grid_x, c.py, c.grid_y, c.dsc);
-      k_ens_iter<<<1, 1, 0, s>>>(e, c.dsc, hi);
+                                                                 c.px, c.strip_n, c.strip_rows, &e->rk_res, &e->p.uk);
+      sweeps();
       if ((err = cudaStreamEndCapture(s, &I))) return fail(err);
       // end of the attempt: the result into nxt, its statistics, the controller
       if ((err = cudaStreamBeginCaptureToGraph(s, B, &ni, nullptr, 1, md))) return fail(err);
       k_ens_copy<<<1024, 256, 0, s>>>(e, c.N);
       k_grid_stats<<<c.grid_stats, 256, 0, s>>>(nullptr, c.N, c.py, &e->p.nxt);
-      k_finalize<<<1, 256, 0, s>>>(c.px, 0, c.py, c.grid_stats, c.dsc);
-      k_ens_step<<<1, 1, 0, s>>>(e, c.dsc, ho, hi);
+      k_ens_step<<<1, 256, 0, s>>>(c.py, c.grid_stats, c.dsc, e, ho);
       if ((err = cudaStreamEndCapture(s, &B))) return fail(err);
       if ((err = cudaGraphInstantiate(out, g, 0))) return fail(err);
       cudaGraphDestroy(g);

@@ -354,19 +354,13 @@ __device__ __forceinline__ void strip_copy_bn(float4* dst, const df64* __restric
 // u_0 = u^n, from the same stored b^n -- what kRhsResidual would compute).
 // Warp w of the grid takes strip w % nstrip and rows [seg_rows * (w /
 // nstrip), + seg_rows); one partial result (max|G|) per block.
-// DEV (the ensemble graphs): the step's constants RKd, the grid *ud and the
-// Newton iteration in flight *iter come from device memory -- a residual
-// launch of iteration 0 returns at once, since the explicit part formed that
-// residual; otherwise RKp and up.
+// DEV (the ensemble graphs): the step's constants *RKd and the grid *ud come
+// from device memory; otherwise RKp and up.
 template <int KIND, bool DEV = false>
 __global__ void __launch_bounds__(kST, 5)
     k_rhs_strip(ModelK M, StripK RKp, const double* __restrict__ up, df64* __restrict__ bn,
                 float* __restrict__ rhs, float* __restrict__ ulp, PartX* __restrict__ part, int nstrip,
-                int seg_rows, const StripK* __restrict__ RKd = nullptr, const double* const* __restrict__ ud = nullptr,
-                const int* __restrict__ iter = nullptr) {
-  if constexpr (DEV) {
-    if (iter && *iter == 0) return;
-  }
+                int seg_rows, const StripK* __restrict__ RKd = nullptr, const double* const* __restrict__ ud = nullptr) {
   const StripK& RK = DEV ? *RKd : RKp;
   const double* __restrict__ u = DEV ? *ud : up;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
