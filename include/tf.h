@@ -242,9 +242,9 @@ int tf_advance(tf_ctx* ctx, double* h, double t0, double t_end, double dt0,
  *   graph engine (TF_ENSEMBLE_AUTO, for FP32-bulk contexts of the (3, 2)
  *     power law on the twisted sweeps): each film's whole run is one launch
  *     of a CUDA graph held by its context -- conditional WHILE nodes over
- *     attempts and Newton iterations whose conditions one-thread controller
- *     kernels set from the iteration's reductions, with the film's Δt and
- *     Newton state in device memory.  The host waits once per film per
+ *     attempts and Newton iterations whose conditions the reduction kernels
+ *     set (their thread 0 runs tf_advance's decisions on the reduced
+ *     scalars), with the film's Δt and Newton state in device memory.  The host waits once per film per
  *     call.  The graph is built on the context's first such call (a few
  *     milliseconds); that first call should come before any stream capture.
  *     With timing enabled only tf_timing.launches is counted for these
