@@ -92,8 +92,8 @@ def current_counters(table, mode, root=CSRC) -> dict:
 # FP64 operations executed per cell by each FP64-mode kernel (DFMA counted
 # as 2, DADD and DMUL as 1), from an ncu capture of the FP64-mode kernels at
 # 4096^2 (per cell they do not depend on the grid size).
-FP64_FLOPS_PER_CELL = {"rhs": (46.14, "42a3bea84856f1b6"), "x_sweep": (85.91, "5a5b8ec6c5fd8521"),
-                       "y_sweep": (102.91, "5a5b8ec6c5fd8521")}
+FP64_FLOPS_PER_CELL = {"rhs": (46.14, "b7f77f9a109008d3"), "x_sweep": (85.91, "1453e94b4cd1b98b"),
+                       "y_sweep": (102.91, "1453e94b4cd1b98b")}
 
 
 class ClockSampler:
@@ -293,8 +293,8 @@ def kernel_table(res, N, lp):
 # DRAM bytes (read + write) per cell per launch of each FP32-bulk kernel,
 # from an ncu capture of the FP32-bulk kernels at 4096^2 (traffic scales
 # with the cells).
-TRAFFIC_PER_CELL_F32B = {"rhs": (24.25, "7a7eaa79b8506481"), "x_sweep": (31.24, "5a5b8ec6c5fd8521"),
-                         "y_sweep": (44.37, "5a5b8ec6c5fd8521"), "explicit": (21.66, "7a7eaa79b8506481")}
+TRAFFIC_PER_CELL_F32B = {"rhs": (24.27, "7980ad0cf0226350"), "x_sweep": (31.23, "1453e94b4cd1b98b"),
+                         "y_sweep": (44.37, "1453e94b4cd1b98b"), "explicit": (21.68, "7980ad0cf0226350")}
 
 
 def ncu_counters_apply(w) -> bool:

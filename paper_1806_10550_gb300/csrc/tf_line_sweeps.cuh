@@ -133,6 +133,12 @@ __device__ __forceinline__ void copy_span(T* dst, const T* __restrict__ src, int
   }
 }
 
+// The Newton update's correction as a double, exactly: integer operations
+// for an FP32 correction (f64_of_f32_exact), so that the update's one FP64
+// add per cell is the backward ticks' only FP64-pipe work
+__device__ __forceinline__ double widen_exact(float x) { return f64_of_f32_exact(x); }
+__device__ __forceinline__ double widen_exact(double x) { return x; }
+
 // a * b rounded on its own: never contracted with a following add
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
@@ -544,10 +550,10 @@ __global__ void __launch_bounds__(kSweepThreads, Mode::kSweepBlocks)
               if (r >= nr) break;
               const LP x = S.s.b.xb[bq & 1][h][r][c];
               const double uk = S.s.b.ukt[slot][h][r][c];
-              // one native FP64 add per cell, correctly rounded (with the
-              // float widened exactly on the FP64 pipe: fewer instructions
-              // than the integer add of tf_numeric.cuh, measured)
-              const double un = uk + (double)x;
+              // one native FP64 add per cell, correctly rounded (fewer
+              // instructions than the integer add of tf_numeric.cuh,
+              // measured); the float widened exactly off the FP64 pipe
+              const double un = uk + widen_exact(x);
               const size_t idx = base + i * step8;
               unew[idx] = un;
               if (vout) vout[idx] = to_f64(x);

@@ -116,6 +116,19 @@ TF_HD double f64_of_f32(float f) {
   return double_of(sign | ((uint64_t)(e - 127 + 1023) << 52) | ((uint64_t)(b & 0x7fffffu) << 29));
 }
 
+// float -> double, exactly what the native conversion gives: normal floats
+// and zeros with integer operations (the exponent rebiased by 1023 - 127 in
+// the high word, the significand's last three bits in the low word);
+// subnormal, infinite and NaN floats, which the Newton update all but never
+// meets, take the native conversion.
+TF_HD double f64_of_f32_exact(float f) {
+  const uint32_t b = bits_of(f), a = b & 0x7fffffffu;
+  if (a - 0x00800000u < 0x7f000000u)
+    return double_of(((uint64_t)((b & 0x80000000u) | ((a >> 3) + 0x38000000u)) << 32) | (uint64_t)(b << 29));
+  if (a == 0u) return double_of((uint64_t)b << 32);
+  return (double)f;
+}
+
 // ---------------------------------------------------------------------------
 // double-float numbers
 struct df64 {

@@ -32,6 +32,20 @@ void tfh_fast_conv(const double* x, float* f, float* hi, float* lo, long n) {
     lo[i] = d.lo;
   }
 }
+// bit patterns b in [lo, hi) whose float f64_of_f32_exact widens to other
+// bits than the host's own float -> double conversion
+long tfh_f64_of_f32_exact_mismatches(unsigned long long lo, unsigned long long hi) {
+  long bad = 0;
+  for (unsigned long long b = lo; b < hi; ++b) {
+    const float f = tf::float_of((uint32_t)b);
+    const double w = tf::f64_of_f32_exact(f), r = (double)f;
+    if (tf::bits_of(w) != tf::bits_of(r)) ++bad;
+  }
+  return bad;
+}
+void tfh_f64_of_f32_exact(const float* x, double* y, long n) {
+  for (long i = 0; i < n; ++i) y[i] = tf::f64_of_f32_exact(x[i]);
+}
 void tfh_fixed36(const double* u, long long* q, long n) {
   for (long i = 0; i < n; ++i) q[i] = (long long)tf::fixed36_of_f64(u[i]);
 }

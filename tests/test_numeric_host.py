@@ -56,6 +56,21 @@ def test_df_of_f64_is_48_bit_accurate(lib):
     assert np.all(np.abs(lo) <= np.spacing(np.abs(hi)))
 
 
+def test_f64_of_f32_exact_is_the_conversion(lib):
+    """The integer widening of the y sweep's Newton update gives the bits of
+    the native float -> double conversion for every one of the 2^32 float
+    bit patterns, and NumPy's widening on named values."""
+    f = lib.tfh_f64_of_f32_exact_mismatches
+    f.restype = C.c_long
+    f.argtypes = [C.c_ulonglong, C.c_ulonglong]
+    assert f(0, 1 << 32) == 0
+    x = np.array([0.0, -0.0, 1.0, -1.0, 1.5, 3.4028235e38, -1.1754944e-38, 1.1754942e-38, 1e-45,
+                  np.inf, -np.inf, 0.1, -2.5e-7], np.float32)
+    y = np.empty(x.size)
+    lib.tfh_f64_of_f32_exact(_p(x), _p(y), C.c_long(x.size))
+    assert y.view(np.uint64).tolist() == x.astype(np.float64).view(np.uint64).tolist()
+
+
 def test_f64_add_f32_rounds_to_nearest(lib):
     rng = np.random.default_rng(2)
     n = 20000
