@@ -717,9 +717,11 @@ int tf_advance(tf_ctx* c, double* h, double t0, double t_end, double dt0, int ma
 bool graph_capable(const tf_ctx& c) { return c.ops->ens_graph && c.packed_rhs && !c.part; }
 
 int film_graph_start(tf_ctx& c, double* h, double t0, double t_end, double dt0, int max_att, int streak) {
-  if (!c.ens_exec) {
-    int r = dalloc((void**)&c.ens_dev, sizeof(tf::EnsDev));
-    if (r) return r;
+  if (!c.ens_exec) {  // first use; a failed earlier build keeps its buffers
+    if (!c.ens_dev) {
+      int r = dalloc((void**)&c.ens_dev, sizeof(tf::EnsDev));
+      if (r) return r;
+    }
     if (!c.ens_host) TF_CK(cudaMallocHost((void**)&c.ens_host, sizeof(tf::EnsDev)));
     TF_CK(c.ops->ens_graph(c, c.ens_dev, &c.ens_exec));
   }

@@ -221,7 +221,9 @@ template <class Mode> struct Launch {
       k_grid_stats<<<c.grid_stats, 256, 0, s>>>(nullptr, c.N, c.py, &e->p.nxt);
       k_ens_step<<<1, 256, 0, s>>>(c.py, c.grid_stats, c.dsc, e, ho);
       if ((err = cudaStreamEndCapture(s, &B))) return fail(err);
-      if ((err = cudaGraphInstantiate(out, g, 0))) return fail(err);
+      cudaGraphExec_t x = nullptr;  // *out only ever holds an instantiated graph
+      if ((err = cudaGraphInstantiate(&x, g, 0))) return fail(err);
+      *out = x;
       cudaGraphDestroy(g);
       cudaStreamDestroy(s);
       return cudaSuccess;
