@@ -133,6 +133,34 @@ def test_null_arguments_rejected():
     assert L.tf_ensemble_advance(0, None, None, None, None, None, None, None, None, 7) == tf.TF_ERR_ARG
 
 
+def test_tuner_and_probe_refuse_bad_arguments():
+    """The line-solver tuner, its table and the FMA probe refuse their bad
+    arguments on the host, before any device work."""
+    L = tf.library()
+    p = tf.tf_params_default(nx=64, ny=64, ds=1.0)
+    best, ms = C.c_int(-7), (C.c_double * 2)(-3.0, -3.0)
+    fake = C.c_void_p(16)  # never dereferenced: every call below is refused first
+    for args in ((None, None, fake, 0.1, 1, 1),     # no parameters
+                 (C.byref(p), None, None, 0.1, 1, 1),  # no film
+                 (C.byref(p), None, fake, 0.1, 0, 1),  # no timed round
+                 (C.byref(p), None, fake, 0.1, 1, 0),  # no copy
+                 (C.byref(p), None, fake, 0.1, 1, 257),  # too many copies
+                 (C.byref(p), None, fake, 0.0, 1, 1),  # dt not positive
+                 (C.byref(p), None, fake, float("nan"), 1, 1),
+                 (C.byref(p), None, fake, float("inf"), 1, 1)):
+        assert L.tf_tune_line_solver(*args, C.byref(best), ms) == tf.TF_ERR_ARG, args
+    assert L.tf_tune_line_solver(C.byref(p), None, fake, 0.1, 1, 1, None, ms) == tf.TF_ERR_ARG
+    assert best.value == -7 and list(ms) == [-3.0, -3.0]
+    # nothing tuned for this shape in this process; NULLs read as "none"
+    assert L.tf_tuned_line_solver(C.byref(p)) == -1
+    assert L.tf_tuned_line_solver(None) == -1
+    assert L.tf_line_solver(None) == -1
+    out = C.c_double(-1.0)
+    assert L.tf_probe_fma(tf.TF_FP64, None, None) == tf.TF_ERR_ARG
+    assert L.tf_probe_fma(5, None, C.byref(out)) == tf.TF_ERR_ARG
+    assert out.value == -1.0
+
+
 def test_no_cpu_fallback_without_gpu():
     import torch
     if torch.cuda.is_available():
